@@ -1,0 +1,197 @@
+"""O1: restarted, diagonally scaled PDHG in plain FP64 numpy.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+The paper's GPU arm solves the LP relaxation with PDHG (Sec. II-C, Alg. 1
+"Solver 1"; Sec. III-C) with an iteration limit of 100,000, an absolute
+feasibility tolerance of 1e-5 and a convergence tolerance of 1e-4 (Sec. II-D),
+but does not state the method.  This follows the published PDLP scheme
+(Applegate et al., NeurIPS 2021) with a constant step:
+
+  start:  x = clip(0, l, u), y = 0, omega = omega0, tau = eta/omega,
+          sigma = eta*omega, anchor = (x, y), KKT_anchor = KKT_omega(x, y)
+  step k: x+ = clip(x - tau (c - A^T y), l, u)
+          y+ = y + sigma (q - A (2 x+ - x)),  y+_I = max(y+_I, 0)
+          running sums of x+, y+ since the last restart (uniform average)
+  every n_eval steps (after step k with (k+1) % n_eval == 0):
+          relative KKT (unscaled presolved LP) of the current point, then of
+          the average: stop at the first one <= tol (current checked first);
+          candidate = average if KKT_omega(avg) < KKT_omega(cur) else current;
+          restart when KKT_c <= 0.2 KKT_anchor, or KKT_c <= 0.8 KKT_anchor and
+          KKT_c > KKT_c at the previous evaluation, or j >= 0.36 (k+1)
+          (j = steps since the last restart);
+          on restart: dx = ||x_c - x_anchor||, dy = ||y_c - y_anchor||;
+          if both > 1e-10, omega = exp(0.5 ln(dy/dx) + 0.5 ln omega);
+          (x, y) = anchor = candidate; KKT_anchor = KKT_omega(candidate) with
+          the new omega; sums and j reset; tau, sigma recomputed.
+All arithmetic is on the scaled problem except the stopping test.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import kkt
+
+BETA_SUFFICIENT = 0.2
+BETA_NECESSARY = 0.8
+BETA_ARTIFICIAL = 0.36
+N_EVAL = 64
+
+
+@dataclasses.dataclass
+class State:
+    x: np.ndarray
+    y: np.ndarray
+    x_sum: np.ndarray
+    y_sum: np.ndarray
+    x_anchor: np.ndarray
+    y_anchor: np.ndarray
+    omega: float
+    tau: float
+    sigma: float
+    kkt_anchor: float
+    kkt_prev: float
+    j: int
+    k: int
+    restarts: int = 0
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray          # scaled presolved primal (returned point)
+    y: np.ndarray          # scaled presolved dual
+    iters: int
+    status: str            # "optimal" | "iteration_limit"
+    rel: tuple             # (rel_p, rel_d, rel_gap) of the returned point
+    restarts: int
+    omega: float
+    state: State
+    which: str             # "current" | "average"
+
+
+def _unscaled_lp(S):
+    """The unscaled presolved LP, rebuilt from the scaled one and D_r, D_c."""
+    class _U:
+        pass
+    U = _U()
+    U.A = S.A.multiply(1.0 / S.Dr[:, None]).multiply(1.0 / S.Dc[None, :]).tocsr()
+    U.q = S.q / S.Dr
+    U.c = S.c / S.Dc
+    with np.errstate(invalid="ignore"):
+        U.l = S.l * S.Dc
+        U.u = S.u * S.Dc
+    U.m_eq = S.m_eq
+    return U
+
+
+def weighted(S, x, y, omega):
+    r = kkt.residuals(S.A, S.q, S.c, S.l, S.u, S.m_eq, x, y)
+    rp2 = float(np.dot(r.rp, r.rp))
+    rd2 = float(np.dot(r.rd, r.rd))
+    return kkt.weighted_kkt(rp2, rd2, r.gap, omega), (rp2, rd2, r.gap)
+
+
+def initial_state(S, x0=None, y0=None) -> State:
+    x = np.clip(np.zeros(S.A.shape[1]), S.l, S.u) if x0 is None else np.clip(x0.copy(), S.l, S.u)
+    y = np.zeros(S.A.shape[0]) if y0 is None else y0.copy()
+    if y0 is not None:
+        y[S.m_eq:] = np.maximum(y[S.m_eq:], 0.0)
+    omega = S.omega0
+    ka, _ = weighted(S, x, y, omega)
+    return State(x=x, y=y, x_sum=np.zeros_like(x), y_sum=np.zeros_like(y),
+                 x_anchor=x.copy(), y_anchor=y.copy(), omega=omega,
+                 tau=S.eta / omega, sigma=S.eta * omega, kkt_anchor=ka,
+                 kkt_prev=math.inf, j=0, k=0)
+
+
+def step(S, st: State, AT=None):
+    """One PDHG iteration in place."""
+    AT = S.A.T.tocsr() if AT is None else AT
+    x_new = np.clip(st.x - st.tau * (S.c - AT @ st.y), S.l, S.u)
+    xbar = 2.0 * x_new - st.x
+    y_new = st.y + st.sigma * (S.q - S.A @ xbar)
+    y_new[S.m_eq:] = np.maximum(y_new[S.m_eq:], 0.0)
+    st.x = x_new
+    st.y = y_new
+    st.x_sum += x_new
+    st.y_sum += y_new
+    st.j += 1
+    st.k += 1
+
+
+def restart_decision(kkt_cand, kkt_anchor, kkt_prev, j, k_plus_1) -> bool:
+    """The restart test applied at an evaluation (k_plus_1 = steps taken)."""
+    if kkt_cand <= BETA_SUFFICIENT * kkt_anchor:
+        return True
+    if kkt_cand <= BETA_NECESSARY * kkt_anchor and kkt_cand > kkt_prev:
+        return True
+    if j >= BETA_ARTIFICIAL * k_plus_1:
+        return True
+    return False
+
+
+def primal_weight_update(omega, dx, dy) -> float:
+    if dx > 1e-10 and dy > 1e-10:
+        return math.exp(0.5 * math.log(dy / dx) + 0.5 * math.log(omega))
+    return omega
+
+
+def evaluate(S, st: State, U, tol: float):
+    """Evaluation after an n_eval block; returns (done, which, point) and
+    applies a restart to ``st`` when the test fires."""
+    x_avg = st.x_sum / st.j
+    y_avg = st.y_sum / st.j
+    for which, (xx, yy) in (("current", (st.x, st.y)), ("average", (x_avg, y_avg))):
+        rel = kkt.relative_kkt(U, S.Dc * xx, S.Dr * yy)
+        if max(rel) <= tol:
+            return True, which, (xx.copy(), yy.copy()), rel
+    k_cur, parts_cur = weighted(S, st.x, st.y, st.omega)
+    k_avg, parts_avg = weighted(S, x_avg, y_avg, st.omega)
+    if k_avg < k_cur:
+        xc, yc, kc, parts = x_avg, y_avg, k_avg, parts_avg
+    else:
+        xc, yc, kc, parts = st.x, st.y, k_cur, parts_cur
+    if restart_decision(kc, st.kkt_anchor, st.kkt_prev, st.j, st.k):
+        dx = float(np.linalg.norm(xc - st.x_anchor))
+        dy = float(np.linalg.norm(yc - st.y_anchor))
+        st.omega = primal_weight_update(st.omega, dx, dy)
+        st.x = xc.copy()
+        st.y = yc.copy()
+        st.x_anchor = st.x.copy()
+        st.y_anchor = st.y.copy()
+        st.kkt_anchor = kkt.weighted_kkt(parts[0], parts[1], parts[2], st.omega)
+        st.kkt_prev = math.inf
+        st.x_sum[:] = 0.0
+        st.y_sum[:] = 0.0
+        st.j = 0
+        st.tau = S.eta / st.omega
+        st.sigma = S.eta * st.omega
+        st.restarts += 1
+    else:
+        st.kkt_prev = kc
+    return False, None, None, None
+
+
+def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
+          x0=None, y0=None, trace=None, trace_iters=()) -> Result:
+    """Run O1 on a ``presolve.Scaled`` problem.  ``trace(k, state)`` is called
+    after every step k in ``trace_iters`` (k counts steps taken)."""
+    st = initial_state(S, x0, y0)
+    AT = S.A.T.tocsr()
+    U = _unscaled_lp(S)
+    trace_iters = set(trace_iters)
+    while st.k < max_iter:
+        step(S, st, AT)
+        if st.k % n_eval == 0:
+            done, which, pt, rel = evaluate(S, st, U, tol)
+            if done:
+                return Result(x=pt[0], y=pt[1], iters=st.k, status="optimal", rel=rel,
+                              restarts=st.restarts, omega=st.omega, state=st, which=which)
+        if trace is not None and st.k in trace_iters:
+            trace(st.k, st)
+    rel = kkt.relative_kkt(U, S.Dc * st.x, S.Dr * st.y)
+    return Result(x=st.x.copy(), y=st.y.copy(), iters=st.k, status="iteration_limit",
+                  rel=rel, restarts=st.restarts, omega=st.omega, state=st, which="current")

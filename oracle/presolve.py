@@ -1,0 +1,300 @@
+"""Presolve, diagonal scaling, ||A||_2 estimate and postsolve, written plainly.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+The paper's presolve is Gurobi's (Sec. II-D: fewer rows/columns before the
+relaxation); this is the reduced form the GPU arm needs, applied identically
+to every load so that the reduced structure does not depend on the load:
+
+  repeat until a pass changes nothing:
+    1. every active column with l == u is fixed: its value moves into the row
+       right-hand sides and the objective constant;
+    2. rows are swept in order, counting entries in active columns:
+         0 entries: equality needs q == 0, ">=" needs q <= 0 (else infeasible);
+                    the row is dropped;
+         1 entry a x_j:  equality fixes l_j = u_j = q / a;  ">=" tightens
+                    l_j (a > 0) or u_j (a < 0) to q / a; the row is dropped;
+    3. every active column with no entry in an active row is fixed at the bound
+       its cost prefers (l if c > 0, u if c < 0, else l, u or 0 when finite).
+  Surviving rows and columns keep their original order.
+
+Scaling (the PDLP preconditioner, Applegate et al. 2021): 10 Ruiz passes
+(divide row i by sqrt(max_j |a_ij|) and column j by sqrt(max_i |a_ij|), both
+taken from the matrix at the start of the pass), then one Pock-Chambolle pass
+with alpha = 1 (divide by sqrt of row / column absolute sums).  With the
+accumulated factors D_r, D_c:  A_s = D_r A D_c,  c_s = D_c c,  q_s = D_r q,
+l_s = l / D_c,  u_s = u / D_c.
+
+Step size: eta = 0.998 / ||A_s||_2 with ||A_s||_2^2 from power iteration on
+A_s^T A_s started at 1/sqrt(n), stopped when the estimate changes by at most
+1e-10 relative or after 500 products.  Initial primal weight
+omega0 = ||c_s|| / ||q_s|| when both exceed 1e-10, else 1.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+from .lp import LP
+
+RUIZ_ITERS = 10
+PC_ALPHA = 1.0
+POWER_TOL = 1e-10
+POWER_MAX = 500
+ETA_FACTOR = 0.998
+
+
+class Infeasible(Exception):
+    pass
+
+
+@dataclasses.dataclass
+class Presolved:
+    lp: LP                    # reduced, unscaled
+    col_map: np.ndarray       # reduced column -> raw column
+    row_map: np.ndarray       # reduced row -> raw row
+    raw_n: int
+    raw_m: int
+    fixed: list               # (raw col, value) in the order fixed
+    removed_rows: list        # (raw row, raw col or -1, coef, kind 'E'/'I', tightened)
+    raw: LP
+
+
+def presolve(raw: LP) -> Presolved:
+    A = raw.A.tocsr()
+    n, m = raw.n, raw.m
+    l = raw.l.copy()
+    u = raw.u.copy()
+    q = raw.q.copy()
+    obj_const = raw.obj_const
+    col_on = np.ones(n, bool)
+    row_on = np.ones(m, bool)
+    fixed = []
+    removed = []
+    xfix = np.zeros(n)
+    Acsc = A.tocsc()
+
+    changed = True
+    while changed:
+        changed = False
+        # 1. fixed columns
+        for j in range(n):
+            if col_on[j] and l[j] == u[j]:
+                v = l[j]
+                for k in range(Acsc.indptr[j], Acsc.indptr[j + 1]):
+                    i = Acsc.indices[k]
+                    if row_on[i]:
+                        q[i] -= Acsc.data[k] * v
+                obj_const += raw.c[j] * v
+                xfix[j] = v
+                col_on[j] = False
+                fixed.append((j, v))
+                changed = True
+        # 2. empty and singleton rows
+        for i in range(m):
+            if not row_on[i]:
+                continue
+            ents = [(A.indices[k], A.data[k]) for k in range(A.indptr[i], A.indptr[i + 1])
+                    if col_on[A.indices[k]]]
+            is_eq = i < raw.m_eq
+            if len(ents) == 0:
+                if (is_eq and abs(q[i]) > 1e-9) or ((not is_eq) and q[i] > 1e-9):
+                    raise Infeasible(f"empty row {i} with rhs {q[i]}")
+                row_on[i] = False
+                removed.append((i, -1, 0.0, "E" if is_eq else "I", False))
+                changed = True
+            elif len(ents) == 1:
+                j, a = ents[0]
+                bnd = q[i] / a
+                tightened = False
+                if is_eq:
+                    if bnd < l[j] - 1e-9 or bnd > u[j] + 1e-9:
+                        raise Infeasible(f"singleton equality row {i}")
+                    l[j] = bnd
+                    u[j] = bnd
+                    tightened = True
+                elif a > 0:
+                    if bnd > l[j]:
+                        l[j] = bnd
+                        tightened = True
+                else:
+                    if bnd < u[j]:
+                        u[j] = bnd
+                        tightened = True
+                if l[j] > u[j] + 1e-9:
+                    raise Infeasible(f"bounds crossed on column {j}")
+                if l[j] > u[j]:
+                    u[j] = l[j]
+                row_on[i] = False
+                removed.append((i, j, a, "E" if is_eq else "I", tightened))
+                changed = True
+        # 3. empty columns
+        for j in range(n):
+            if not col_on[j]:
+                continue
+            used = False
+            for k in range(Acsc.indptr[j], Acsc.indptr[j + 1]):
+                if row_on[Acsc.indices[k]]:
+                    used = True
+                    break
+            if used:
+                continue
+            cj = raw.c[j]
+            if cj > 0:
+                v = l[j]
+            elif cj < 0:
+                v = u[j]
+            else:
+                v = l[j] if np.isfinite(l[j]) else (u[j] if np.isfinite(u[j]) else 0.0)
+            if not np.isfinite(v):
+                raise Infeasible(f"unbounded empty column {j}")
+            obj_const += cj * v
+            xfix[j] = v
+            col_on[j] = False
+            fixed.append((j, v))
+            changed = True
+
+    col_map = np.flatnonzero(col_on)
+    row_map = np.flatnonzero(row_on)
+    Ared = A[row_map][:, col_map].tocsr()
+    Ared.sort_indices()
+    m_eq = int(np.count_nonzero(row_map < raw.m_eq))
+    red = LP(A=Ared, q=q[row_map].copy(), c=raw.c[col_map].copy(),
+             l=l[col_map].copy(), u=u[col_map].copy(), m_eq=m_eq, obj_const=obj_const)
+    ps = Presolved(lp=red, col_map=col_map, row_map=row_map, raw_n=n, raw_m=m,
+                   fixed=fixed, removed_rows=removed, raw=raw)
+    ps._xfix = xfix
+    ps._tight_l = l
+    ps._tight_u = u
+    return ps
+
+
+def postsolve(ps: Presolved, x: np.ndarray, y: np.ndarray | None = None):
+    """Map a reduced (unscaled) primal/dual pair back to the raw LP.
+
+    Primal: fixed columns take their fixed value.  Dual: removed rows get 0,
+    except a singleton row whose bound is active in the reduced solution and
+    was tightened by that row: it takes the column's reduced cost / a.
+    """
+    raw = ps.raw
+    xr = ps._xfix.copy()
+    xr[ps.col_map] = x
+    if y is None:
+        return xr, None
+    yr = np.zeros(ps.raw_m)
+    yr[ps.row_map] = y
+    # reduced costs in the raw LP with the rows known so far
+    lam = raw.c - raw.A.T @ yr
+    for (i, j, a, kind, tightened) in reversed(ps.removed_rows):
+        if j < 0 or not tightened:
+            continue
+        if kind == "E":
+            yr[i] = lam[j] / a
+        else:
+            at_bound = abs(xr[j] - (ps._tight_l[j] if a > 0 else ps._tight_u[j])) <= 1e-9 * (1 + abs(xr[j]))
+            if at_bound and lam[j] / a > 0:
+                yr[i] = lam[j] / a
+        lam = raw.c - raw.A.T @ yr
+    return xr, yr
+
+
+@dataclasses.dataclass
+class Scaled:
+    A: sp.csr_matrix
+    q: np.ndarray
+    c: np.ndarray
+    l: np.ndarray
+    u: np.ndarray
+    m_eq: int
+    Dr: np.ndarray
+    Dc: np.ndarray
+    eta: float
+    omega0: float
+    norm_A: float
+    q_inf_unscaled: float
+    c_inf_unscaled: float
+
+
+def _row_absmax(A):
+    """max_j |a_ij| per row (0 for an empty row)."""
+    out = np.zeros(A.shape[0])
+    nz = np.diff(A.indptr) > 0
+    if A.data.size:
+        red = np.maximum.reduceat(np.abs(A.data), A.indptr[:-1][nz])
+        out[nz] = red
+    return out
+
+
+def _scale_matrix(A: sp.csr_matrix, rf: np.ndarray, cf: np.ndarray) -> sp.csr_matrix:
+    """A_ij / rf_i / cf_j."""
+    B = A.copy()
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    B.data = B.data / rf[rows] / cf[B.indices]
+    return B
+
+
+def ruiz_pass(A: sp.csr_matrix):
+    absA = abs(A)
+    rmax = _row_absmax(absA)
+    cmax = _row_absmax(absA.T.tocsr())
+    rf = np.where(rmax > 0, np.sqrt(rmax), 1.0)
+    cf = np.where(cmax > 0, np.sqrt(cmax), 1.0)
+    return _scale_matrix(A, rf, cf), rf, cf
+
+
+def pock_chambolle_pass(A: sp.csr_matrix, alpha: float = PC_ALPHA):
+    absA = abs(A)
+    rs = np.asarray((absA.power(2.0 - alpha)).sum(axis=1)).ravel()
+    cs = np.asarray((absA.power(alpha)).sum(axis=0)).ravel()
+    rf = np.where(rs > 0, np.sqrt(rs), 1.0)
+    cf = np.where(cs > 0, np.sqrt(cs), 1.0)
+    return _scale_matrix(A, rf, cf), rf, cf
+
+
+def power_norm(A: sp.csr_matrix, tol: float = POWER_TOL, max_iter: int = POWER_MAX) -> float:
+    """||A||_2 by power iteration on A^T A (start 1/sqrt(n))."""
+    n = A.shape[1]
+    v = np.full(n, 1.0 / np.sqrt(n))
+    AT = A.T.tocsr()
+    lam_prev = 0.0
+    lam = 0.0
+    for _ in range(max_iter):
+        w = AT @ (A @ v)
+        lam = float(np.sqrt(np.dot(w, w)))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+        if abs(lam - lam_prev) <= tol * lam:
+            break
+        lam_prev = lam
+    return float(np.sqrt(lam))
+
+
+def scale(lp: LP, ruiz_iters: int = RUIZ_ITERS, pock_chambolle: bool = True) -> Scaled:
+    A = lp.A.tocsr().astype(np.float64)
+    Dr = np.ones(lp.m)
+    Dc = np.ones(lp.n)
+    for _ in range(ruiz_iters):
+        A, rf, cf = ruiz_pass(A)
+        Dr = Dr / rf
+        Dc = Dc / cf
+    if pock_chambolle:
+        A, rf, cf = pock_chambolle_pass(A)
+        Dr = Dr / rf
+        Dc = Dc / cf
+    c = Dc * lp.c
+    q = Dr * lp.q
+    with np.errstate(invalid="ignore"):
+        l = lp.l / Dc
+        u = lp.u / Dc
+    nrm = power_norm(A)
+    eta = ETA_FACTOR / nrm if nrm > 0 else 1.0
+    cn = float(np.linalg.norm(c))
+    qn = float(np.linalg.norm(q))
+    omega0 = cn / qn if (cn > 1e-10 and qn > 1e-10) else 1.0
+    return Scaled(A=A, q=q, c=c, l=l, u=u, m_eq=lp.m_eq, Dr=Dr, Dc=Dc, eta=eta,
+                  omega0=omega0, norm_A=nrm,
+                  q_inf_unscaled=float(np.max(np.abs(lp.q), initial=0.0)),
+                  c_inf_unscaled=float(np.max(np.abs(lp.c), initial=0.0)))

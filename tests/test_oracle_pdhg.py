@@ -1,0 +1,129 @@
+"""Pins for O1 (FP64 restarted PDHG): convergence to the simplex optimum,
+closed-form fixed points, step invariants and the restart rules."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ucgen
+from oracle import kkt, lp as olp, pdhg, presolve as ops, simplex
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pipeline(P):
+    raw = olp.build_lp(P)
+    ps = ops.presolve(raw)
+    S = ops.scale(ps.lp)
+    return raw, ps, S
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pdhg_reaches_simplex_objective(seed):
+    P = ucgen.make_problem(seed, B=12, L=16, G=4, T=6, lo=0.4, hi=0.8, noise=0.05,
+                           zero_pmin_frac=0.25)
+    raw, ps, S = _pipeline(P)
+    r = pdhg.solve(S, tol=1e-4, max_iter=100_000)
+    assert r.status == "optimal"
+    x = S.Dc * r.x
+    y = S.Dr * r.y
+    assert max(kkt.relative_kkt(ps.lp, x, y)) <= 1e-4       # independent KKT evaluation
+    ref = simplex.solve_lp(raw)
+    xr, _ = ops.postsolve(ps, x)
+    obj = float(raw.c @ xr)
+    assert abs(obj - ref.obj) / max(1.0, abs(ref.obj)) <= 1e-4
+
+
+def test_pdhg_tiny_objective_matches_golden():
+    with open(os.path.join(GOLDEN, "tiny_lp.json")) as f:
+        g = json.load(f)
+    P = ucgen.tiny(g["seed"])
+    raw, ps, S = _pipeline(P)
+    r = pdhg.solve(S, tol=1e-4, max_iter=100_000)
+    assert r.status == "optimal"
+    xr, _ = ops.postsolve(ps, S.Dc * r.x)
+    obj = float(raw.c @ xr)
+    assert abs(obj - g["objective"]) / abs(g["objective"]) <= 1e-4
+
+
+def test_pdhg_iterates_stay_in_their_sets():
+    P = ucgen.micro(0, B=10, L=13, G=4, T=6)
+    raw, ps, S = _pipeline(P)
+    st = pdhg.initial_state(S)
+    U = pdhg._unscaled_lp(S)
+    AT = S.A.T.tocsr()
+    for _ in range(300):
+        pdhg.step(S, st, AT)
+        assert np.all(st.x >= S.l) and np.all(st.x <= S.u)
+        assert np.all(st.y[S.m_eq:] >= 0.0)
+        if st.k % pdhg.N_EVAL == 0:
+            pdhg.evaluate(S, st, U, 0.0)
+            assert np.all(st.x >= S.l) and np.all(st.x <= S.u)
+
+
+def test_pdhg_box_minimiser_in_one_step():
+    # the only row is slack everywhere in the box, so the LP optimum is the
+    # box-clipped minimiser of c.x, reached by the first primal step
+    lp = olp.LP(A=sp.csr_matrix(np.array([[1.0, 1.0, 1.0]])), q=np.array([-100.0]),
+                c=np.array([1.0, -1.0, 2.0]), l=np.zeros(3), u=np.array([1.0, 1.0, 5.0]), m_eq=0)
+    S = ops.scale(lp, ruiz_iters=0, pock_chambolle=False)
+    st = pdhg.initial_state(S)
+    assert st.tau * np.min(np.abs(S.c)) >= np.max(S.u - S.l)
+    pdhg.step(S, st)
+    np.testing.assert_array_equal(st.x, [0.0, 1.0, 0.0])
+    np.testing.assert_array_equal(st.y, [0.0])
+    r = pdhg.solve(S, tol=1e-12, max_iter=1000)
+    assert r.status == "optimal" and r.iters == pdhg.N_EVAL
+
+
+def test_pdhg_single_equality_row_fixed_point():
+    # min c.x s.t. a.x = b, 0 <= x <= 1: fill columns in increasing c_j / a_j
+    a = np.array([1.0, 2.0, 0.5, 1.5, 1.0])
+    c = np.array([3.0, 2.0, 4.0, 1.0, 6.0])
+    b = 2.7
+    order = np.argsort(c / a)
+    xs = np.zeros(5)
+    left = b
+    for j in order:
+        xs[j] = min(1.0, left / a[j])
+        left -= a[j] * xs[j]
+        if left <= 0:
+            break
+    lp = olp.LP(A=sp.csr_matrix(a[None, :]), q=np.array([b]), c=c, l=np.zeros(5),
+                u=np.ones(5), m_eq=1)
+    S = ops.scale(lp)
+    r = pdhg.solve(S, tol=1e-9, max_iter=200_000)
+    assert r.status == "optimal"
+    np.testing.assert_allclose(S.Dc * r.x, xs, atol=1e-6)
+    mu = c[order][np.searchsorted(np.cumsum(a[order]), b)] / a[order][np.searchsorted(np.cumsum(a[order]), b)]
+    assert abs(S.Dr[0] * r.y[0] - mu) <= 1e-6 * mu          # the row's price is the marginal ratio
+
+
+def test_restart_rules_scripted():
+    inf = math.inf
+    assert pdhg.restart_decision(0.19, 1.0, inf, 10, 1000)        # sufficient decay
+    assert not pdhg.restart_decision(0.21, 1.0, inf, 10, 1000)
+    assert pdhg.restart_decision(0.5, 1.0, 0.4, 10, 1000)         # necessary decay, no progress
+    assert not pdhg.restart_decision(0.5, 1.0, 0.6, 10, 1000)     # still improving
+    assert not pdhg.restart_decision(0.9, 1.0, 0.6, 10, 1000)     # not decayed enough
+    assert pdhg.restart_decision(0.9, 1.0, 0.6, 360, 1000)        # long epoch (artificial)
+    assert not pdhg.restart_decision(0.9, 1.0, 0.6, 359, 1000)
+
+
+def test_primal_weight_rule_scripted():
+    assert pdhg.primal_weight_update(1.0, 1.0, 4.0) == pytest.approx(2.0, rel=1e-15)
+    assert pdhg.primal_weight_update(4.0, 2.0, 2.0) == pytest.approx(2.0, rel=1e-15)
+    assert pdhg.primal_weight_update(3.0, 0.0, 1.0) == 3.0         # movement too small: keep
+    assert pdhg.primal_weight_update(3.0, 1.0, 1e-11) == 3.0
+
+
+def test_first_evaluation_restarts():
+    P = ucgen.micro(1, B=6, L=8, G=3, T=4)
+    raw, ps, S = _pipeline(P)
+    seen = {}
+    pdhg.solve(S, tol=0.0, max_iter=pdhg.N_EVAL,
+               trace=lambda k, st: seen.setdefault(k, (st.restarts, st.j)), trace_iters=[pdhg.N_EVAL])
+    assert seen[pdhg.N_EVAL] == (1, 0)       # j = 64 >= 0.36 * 64 always fires
