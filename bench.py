@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: restarted PDHG on the 6,049-bus / 700-unit / 48-period UC LP relaxation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config ...]
+
+One step = one solve of the whole hot path on the device-resident presolved LP:
+reset to the cold start, PDHG iterations in CUDA-graph replays of 64, KKT /
+restart evaluation every 64 iterations, until relative KKT <= 1e-4.  `value`
+is PDHG iterations per second summed over ranks (weak scaling: every rank
+solves its own copy; no collective on the data path).  Time-to-1e-4 per LP,
+the algorithmic HBM bandwidth and the kernel roofline are reported beside it.
+`e2e` repeats the step through the public C ABI from host arrays (LP build,
+presolve, upload, solve, download, postsolve).  `--impl reference` times the
+CPU oracle (the same algorithm, plain numpy) on a bounded sample.
+"""
+import os
+
+# the CPU oracle legs use exactly one core; set before numpy is imported
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-4 KKT per UC LP; PDHG iters/s and HBM GB/s; p50/p99 served latency"
+UNIT = "PDHG iter/s"
+TOL = 1e-4
+MAX_ITER = 100_000
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid
+# only for the device source it was taken on (sha256 of uc_device.cu).
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _src_hash():
+    with open(os.path.join(ROOT, "paper_2607_03627_gb300", "csrc", "uc_device.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def bytes_per_iter(n, m, nnz, vs):
+    """Algorithmic bytes of the fused primal (A^T y) and dual (A x-bar) kernels."""
+    primal = nnz * (vs + 4) + 4 * (n + 1) + 8 * m + 56 * n
+    dual = nnz * (vs + 4) + 4 * (m + 1) + 16 * n + 40 * m
+    return primal, dual
+
+
+def make_workload(name, rank):
+    import ucgen
+    if name in ("paper", "paper-fp32"):
+        P = ucgen.paper_scale(0)
+        desc = dict(workload="UC LP relaxation, 6049 buses / 8000 lines / 700 units / 48 periods",
+                    buses=P.B, lines=P.L, units=P.G, periods=P.T, seed=0)
+    elif name == "tiny":
+        P = ucgen.tiny(0)
+        desc = dict(workload="UC LP relaxation, 30 buses / 41 lines / 6 units / 24 periods",
+                    buses=P.B, lines=P.L, units=P.G, periods=P.T, seed=0)
+    else:
+        raise SystemExit(f"unknown config {name}")
+    return P, desc, (32 if name == "paper-fp32" else 64)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding as B
+
+    P, desc, vbits = make_workload(args.config, rank)
+    t0 = time.perf_counter()
+    lp = B.uc_build_lp(P)
+    ps = B.uc_presolve(lp, value_bits=vbits)
+    presolve_s = time.perf_counter() - t0
+    n, m, m_eq, nnz = B.uc_presolved_dims(ps)
+    vs = 4 if vbits == 32 else 8
+    sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True)
+
+    def solve_once():
+        sess.reset(-1)
+        sess.run()
+
+    def read_stats():
+        res, rc = sess.result(0)
+        st = B.uc_get_stats(res)
+        return res, st
+
+    for _ in range(args.warmup):
+        solve_once()
+    _, st_w = read_stats()
+    tp0, td0, nt0 = st_w["primal_kernel_ms"] * st_w["timed_launches"], st_w["dual_kernel_ms"] * st_w["timed_launches"], st_w["timed_launches"]
+    launches0 = st_w["kernel_launches"]
+
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            solve_once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res, st = read_stats()
+    # every timed solve starts cold from the same point and takes the same path
+    iters = [st["iters"]] * args.steps
+    if world > 1:
+        t = torch.tensor([ms, float(sum(iters))], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max, total_iters = tmax[0].item(), tsum[1].item()
+    else:
+        ms_max, total_iters = ms, float(sum(iters))
+    value = total_iters / (ms_max / 1e3)
+    n_timed = st["timed_launches"] - nt0
+    tp = (st["primal_kernel_ms"] * st["timed_launches"] - tp0) / max(n_timed, 1)
+    td = (st["dual_kernel_ms"] * st["timed_launches"] - td0) / max(n_timed, 1)
+    bp, bd = bytes_per_iter(n, m, nnz, vs)
+    peak, peak_kind = _peaks()
+    dom = ("k_primal", bp, tp) if tp * 1 >= td else ("k_dual", bd, td)
+    achieved = dom[1] / (dom[2] / 1e3) / 1e9 if dom[2] > 0 else 0.0
+    traffic = None
+    rec = NCU_TRAFFIC.get((args.config, dom[0]))
+    if rec and rec["src"] == _src_hash():
+        traffic = rec["bytes"]
+    per_iter_ms = ms_max / max(total_iters / world, 1)
+    alg_gbs = (bp + bd) / (per_iter_ms / 1e3) / 1e9
+
+    # end to end through the public API from host arrays
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        tot_it = 0
+        h2d = d2h = 0
+        for _ in range(args.e2e_steps):
+            lp2 = B.uc_build_lp(P)
+            ps2 = B.uc_presolve(lp2, value_bits=vbits)
+            r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter)
+            sol = B.uc_get_solution(r2, P.T, P.B, P.L, P.G)
+            tot_it += sol["stats"]["iters"]
+            h2d += sol["stats"]["h2d_bytes"]
+            d2h += sol["stats"]["d2h_bytes"]
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s, float(tot_it)], device="cuda", dtype=torch.float64)
+            tm = t.clone(); dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            ts = t.clone(); dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+            e2e_s, tot_it = tm[0].item(), ts[1].item()
+        e2e = {"value": tot_it / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // args.e2e_steps),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps),
+               "seconds_per_lp": e2e_s / args.e2e_steps,
+               "includes": "uc_build_lp + uc_presolve + uc_solve (upload, solve, download) + uc_get_solution"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(P, args.cpu_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if vbits == 64 else "f32-values/f64",
+            "data": "synthetic (seeded generator standing in for the GO3 6,049-bus cases)",
+            "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
+                           tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
+                           l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
+                           parallelism=f"replicas x{world}"),
+            "time_to_1e-4_ms": ms_max / args.steps,
+            "iters_per_solve": st["iters"], "status": st["status_name"],
+            "rel_kkt": max(st["rel_primal"], st["rel_dual"], st["rel_gap"]),
+            "objective": st["objective"], "restarts": st["restarts"],
+            "pdhg_iters_per_s_per_gpu": total_iters / world / (ms_max / 1e3),
+            "algorithmic_GBps": alg_gbs, "bytes_per_iter": bp + bd,
+            "presolve_s": presolve_s,
+            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": dom[1],
+                         "mean_launch_us": dom[2] * 1e3, "timed_launches": n_timed,
+                         "other_kernel": {"name": "k_dual" if dom[0] == "k_primal" else "k_primal",
+                                          "mean_launch_us": (td if dom[0] == "k_primal" else tp) * 1e3,
+                                          "algorithmic_bytes_per_launch": bd if dom[0] == "k_primal" else bp}},
+            "clocks": clk.summary(),
+            "gpu_launches": st["kernel_launches"] - launches0,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, iters):
+    """The oracle PDHG as it stands, single core, on a bounded sample of the
+    workload: `iters` iterations (evaluations every 64 included) on the same LP
+    the oracle builds, presolves and scales itself (that set-up is not timed)."""
+    from oracle import lp as olp, pdhg, presolve as ops
+    raw = olp.build_lp(P)
+    ps = ops.presolve(raw)
+    S = ops.scale(ps.lp)
+    st = pdhg.initial_state(S)
+    AT = S.A.T.tocsr()
+    U = pdhg._unscaled_lp(S)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        pdhg.step(S, st, AT)
+        if st.k % pdhg.N_EVAL == 0:
+            pdhg.evaluate(S, st, U, TOL)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} PDHG iterations (with {iters // 64} KKT/restart evaluations) of the oracle "
+                      f"on the same 6049-bus LP; oracle build/presolve/scaling not timed",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step is one 64-iteration
+    block (PDHG steps + one KKT/restart evaluation) of the paper-scale LP."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import ucgen  # noqa: F401
+    from oracle import lp as olp, pdhg, presolve as ops
+    P, desc, vbits = make_workload(args.config if args.config != "paper-fp32" else "paper", rank)
+    raw = olp.build_lp(P)
+    ps = ops.presolve(raw)
+    S = ops.scale(ps.lp)
+    st = pdhg.initial_state(S)
+    AT = S.A.T.tocsr()
+    U = pdhg._unscaled_lp(S)
+
+    def block():
+        for _ in range(pdhg.N_EVAL):
+            pdhg.step(S, st, AT)
+        pdhg.evaluate(S, st, U, TOL)
+
+    for _ in range(args.warmup):
+        block()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        block()
+    dt = time.perf_counter() - t0
+    value = args.steps * pdhg.N_EVAL / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator standing in for the GO3 6,049-bus cases)",
+            "config": dict(desc, n=S.A.shape[1], m=S.A.shape[0], nnz=int(S.A.nnz),
+                           step="64 oracle PDHG iterations + 1 KKT/restart evaluation"),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} x 64 iterations after {args.warmup} warm-up blocks"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="paper", choices=["paper", "paper-fp32", "tiny"])
+    ap.add_argument("--max-iter", type=int, default=MAX_ITER)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

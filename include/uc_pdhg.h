@@ -1,0 +1,231 @@
+/*
+ * uc_pdhg.h -- C ABI of the GB300 unit-commitment LP solver (restarted PDHG).
+ *
+ * The paper ("Rapid Concurrent GPU-CPU Solvers for Scalable Unit Commitment in
+ * Large Power Grids") runs PDHG on the GPU on the LP relaxation of a
+ * multi-period unit-commitment problem (Sec. II-C, Alg. 1 "Solver 1"), after a
+ * presolve (Sec. II-D) and with an iteration limit of 100,000, an absolute
+ * feasibility tolerance of 1e-5 and a convergence tolerance of 1e-4
+ * (Sec. II-D).  This library implements that relaxation solve:
+ *
+ *   uc_build_lp     problem data -> raw DC-UC LP (host)
+ *   uc_presolve     raw LP -> reduced, Ruiz/Pock-Chambolle scaled LP with
+ *                   A and A^T, step size from ||A||_2 (host)
+ *   uc_solve        restarted PDHG on the device (hand-written sm_103a kernels)
+ *   uc_solve_batch  several LPs in one block-diagonal device solve
+ *   uc_get_solution unscale + postsolve into p, u, v, theta, f, shed, LMPs
+ *
+ * Conventions for every call:
+ *   - return value: UC_OK (0) or a negative UC_E* code; the message of the
+ *     last failure on the calling thread is uc_last_error();
+ *   - no C++ exception crosses this boundary;
+ *   - handles (uc_lp, uc_presolved, uc_result) are owned by the library from
+ *     creation until the matching uc_free_*; input arrays are copied, so the
+ *     caller keeps ownership of everything it passes in;
+ *   - output arrays are caller-allocated host memory of the stated size;
+ *   - arrays are C-contiguous; "time-major" means index [t * K + k].
+ */
+#ifndef UC_PDHG_H
+#define UC_PDHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UC_OK 0
+#define UC_EINVAL (-1)       /* bad sizes or indices, non-positive reactance, self loop */
+#define UC_ENOMEM (-2)       /* host or device allocation failed / budget exceeded */
+#define UC_EINFEASIBLE (-3)  /* presolve proved the LP infeasible */
+#define UC_EUNBOUNDED (-4)   /* presolve proved the LP unbounded */
+#define UC_EITERLIMIT (-5)   /* max_iter reached before the tolerance (result valid) */
+#define UC_ETIMEOUT (-6)     /* timeout_ms elapsed (result valid, last iterate) */
+#define UC_ENUMERIC (-7)     /* NaN/Inf in the iterates */
+#define UC_ECANCELLED (-8)   /* opts.cancel was set (result valid, last iterate) */
+#define UC_ECUDA (-9)        /* a CUDA runtime call failed */
+
+typedef struct uc_lp uc_lp;
+typedef struct uc_presolved uc_presolved;
+typedef struct uc_result uc_result;
+typedef struct uc_session uc_session;
+
+/* Multi-period DC unit-commitment data (model: DC relaxation of the UC
+ * problem of Sec. II-A; the full GO Challenge 3 AC model is out of scope).
+ * Buses 0..B-1, lines 0..L-1 (from != to), units 0..G-1, periods 0..T-1. */
+typedef struct {
+    int B, L, G, T;
+    int ref_bus;                 /* angle reference, theta_ref = 0 */
+    const int32_t *line_from;    /* [L] */
+    const int32_t *line_to;      /* [L] */
+    const double *x_pu;          /* [L] reactance (p.u., > 0) */
+    const double *fmax;          /* [L] flow limit (MW, >= 0) */
+    const int32_t *gen_bus;      /* [G] */
+    const double *pmax;          /* [G] MW */
+    const double *pmin;          /* [G] MW, 0 <= pmin <= pmax */
+    const double *ramp;          /* [G] MW per period */
+    const double *c_lin;         /* [G] $/MWh */
+    const double *c_nl;          /* [G] $ per committed period */
+    const double *c_su;          /* [G] $ per startup */
+    const double *u0;            /* [G] commitment before period 0 (0 or 1) */
+    const double *load;          /* [T*B] time-major MW, >= 0 */
+    double voll;                 /* shed price $/MWh; <= 0: no shed columns (strict balance) */
+} uc_problem;
+
+typedef struct {
+    int ruiz_iters;              /* Ruiz equilibration passes (default 10) */
+    int pock_chambolle;          /* 1: one Pock-Chambolle pass, alpha = 1 (default 1) */
+    int power_max_iter;          /* power-iteration products for ||A||_2 (default 500) */
+    double power_tol;            /* relative change that stops it (default 1e-10) */
+    int value_bits;              /* 64: FP64 matrix values on device; 32: FP32 (default 64) */
+    int threads;                 /* host threads for presolve (0 = hardware concurrency) */
+} uc_presolve_opts;
+
+/* Device memory callback: return `bytes` bytes of device memory usable on
+ * `stream` (aligned to 256 B), or NULL.  Used for every device allocation
+ * when set; otherwise cudaMallocAsync/cudaFreeAsync on the solve's stream. */
+typedef void *(*uc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*uc_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct {
+    double tol_rel_kkt;          /* relative KKT tolerance (default 1e-4, Sec. II-D) */
+    double tol_abs_feas;         /* reported absolute feasibility threshold (default 1e-5) */
+    int max_iter;                /* iteration limit (default 100000, Sec. II-D) */
+    int n_eval;                  /* iterations between KKT / restart evaluations (default 64, even) */
+    int use_graph;               /* 1: replay CUDA graphs of n_eval iterations (default 1) */
+    int kernel_timing;           /* 1: time one primal and one dual kernel per replay with events */
+    double timeout_ms;           /* 0: none */
+    const double *warm_x;        /* nullable [n] presolved-space primal start (scaled) */
+    const double *warm_y;        /* nullable [m] presolved-space dual start (scaled) */
+    uc_alloc_fn alloc;           /* nullable device allocator */
+    uc_free_fn free;
+    void *alloc_ctx;
+    int spmv_rows_per_block;     /* 0: automatic (tuned); else threads per CTA for the row kernels */
+    const volatile int *cancel;  /* nullable; a nonzero value (set from another thread) stops the
+                                    solve at its next replay boundary with UC_ECANCELLED -- the
+                                    "terminate the other solver" step of Alg. 1 */
+} uc_solve_opts;
+
+typedef struct {
+    int status;                  /* UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ENUMERIC, UC_ECANCELLED */
+    int iters;                   /* PDHG iterations taken */
+    int restarts;
+    int evals;
+    int returned_average;        /* 1 if the returned point is the iterate average */
+    double rel_primal, rel_dual, rel_gap;  /* infinity-norm relative KKT parts (presolved LP) */
+    double abs_primal;           /* max |primal violation| of the presolved LP (reported only) */
+    double objective;            /* raw-LP objective of the returned point ($) */
+    double dual_objective;       /* presolved dual objective + presolve constant */
+    double omega;                /* final primal weight */
+    double solve_ms;             /* device solve wall time (upload excluded) */
+    double upload_ms;            /* host -> device copy and set-up */
+    double primal_kernel_ms;     /* mean duration of the timed primal kernels (kernel_timing) */
+    double dual_kernel_ms;       /* mean duration of the timed dual kernels (kernel_timing) */
+    int timed_launches;          /* number of kernels each mean is over */
+    int kernel_launches;         /* kernels launched by the session so far */
+    int64_t h2d_bytes;           /* host -> device bytes of the session upload */
+    int64_t d2h_bytes;           /* device -> host bytes of this result (+ status polls) */
+} uc_stats;
+
+void uc_default_presolve_opts(uc_presolve_opts *o);
+void uc_default_solve_opts(uc_solve_opts *o);
+
+/* Build the raw LP (model of Sec. II-A in DC form).  Columns per period t
+ * (offset t*nc, nc = 3G+B+L(+B if voll>0)): p, u, v (G each), theta (B),
+ * f (L), shed (B).  Rows: equality rows (bus balance, flow definition) for all
+ * periods first, then ">=" rows (Pmax u - p, p - Pmin u, startup, ramp up,
+ * ramp down).  Returns UC_EINVAL on bad data. */
+int uc_build_lp(const uc_problem *prob, uc_lp **out);
+int uc_lp_dims(const uc_lp *lp, int *n, int *m, int *m_eq, int64_t *nnz);
+/* Copy the raw LP out (CSR, rows in order, columns ascending): rowptr [m+1],
+ * colidx [nnz], val [nnz], q [m], c [n], l [n], u [n] (+-inf for free). */
+int uc_lp_export(const uc_lp *lp, int32_t *rowptr, int32_t *colidx, double *val,
+                 double *q, double *c, double *l, double *u);
+
+/* Presolve (Sec. II-D, reduced form: fixed columns, singleton rows to bounds,
+ * empty rows / columns; surviving rows and columns keep their order), then
+ * scaling and the step size.  Host only.  UC_EINFEASIBLE / UC_EUNBOUNDED
+ * when presolve proves it. */
+int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **out);
+int uc_presolved_dims(const uc_presolved *ps, int *n, int *m, int *m_eq, int64_t *nnz);
+/* Copy out the scaled reduced LP and its scaling: rowptr [m+1], colidx [nnz],
+ * val [nnz] (FP64 scaled values), q, Dr [m], c, l, u, Dc [n], col_map [n] and
+ * row_map [m] (raw indices), scalars [6] = {eta, omega0, ||A_s||_2, objective
+ * constant, ||q||_inf, ||c||_inf} (the last two unscaled).  Any pointer may be
+ * NULL to skip that array. */
+int uc_presolved_export(const uc_presolved *ps, int32_t *rowptr, int32_t *colidx, double *val,
+                        double *q, double *c, double *l, double *u, double *Dr, double *Dc,
+                        int32_t *col_map, int32_t *row_map, double *scalars);
+
+/* Restarted, diagonally scaled PDHG on the device (Sec. II-C "PDHG (GPU)"),
+ * stopping at relative KKT <= tol_rel_kkt (infinity norm, unscaled presolved
+ * LP) or at max_iter.  `stream` is a cudaStream_t (NULL: legacy default).
+ * The solve is synchronous: it returns when the device work has finished.
+ * Returns the solve status; *out is set (and must be freed) whenever the
+ * status is UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ECANCELLED or UC_ENUMERIC. */
+int uc_solve(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc_result **out);
+
+/* Solve k presolved LPs at once: their matrices are packed block-diagonally
+ * and every iteration launches one primal and one dual kernel for all of
+ * them; each LP keeps its own step sizes, restarts and stopping test and
+ * freezes when it converges.  outs[i] receives LP i's result.  Returns UC_OK
+ * if every LP reached the tolerance, else the first non-OK status. */
+int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
+                   uc_result **outs);
+
+/* Device-resident sessions.  A session uploads k presolved LPs once (matrices
+ * block-diagonal, per-LP vectors, start points, CUDA graph of n_eval
+ * iterations) and then solves them any number of times; it is what uc_solve
+ * and uc_solve_batch use internally, and what a server uses to keep
+ * instances resident, warm-start re-solves and refill finished slots while
+ * the other LPs keep iterating (continuous batching).  A session is used by
+ * one host thread at a time; its device work runs on `stream`.
+ *
+ *   uc_session_create     upload; no LP runs until it is reset
+ *   uc_session_reset      LP i (all if i < 0) back to its start point; the
+ *                         initial KKT anchor is computed on the device
+ *   uc_session_run        replay until every reset LP has stopped, or after
+ *                         max_replays replays (<= 0: enough for max_iter);
+ *                         *n_running = LPs still iterating; returns UC_OK,
+ *                         UC_ECANCELLED or UC_ETIMEOUT (host-side stops)
+ *   uc_session_status     1 idle, 2 iterating, else the LP's final status
+ *   uc_session_result     copy LP i's state out as a uc_result (LP becomes idle)
+ *   uc_session_set_start  warm start of LP i (scaled presolved space, [n], [m];
+ *                         NULL = zeros), used by the next reset
+ *   uc_session_update_lp  replace slot i by an LP with the same scaled matrix
+ *                         (e.g. the same grid and units with another load):
+ *                         new q, c, l, u and scalars; the start point becomes
+ *                         clip(0, l, u), y = 0.  UC_EINVAL if the matrix differs.
+ *   uc_session_device_bytes  bytes of device memory the session holds */
+int uc_session_create(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
+                      uc_session **out);
+int uc_session_reset(uc_session *s, int i);
+int uc_session_run(uc_session *s, int max_replays, int *n_running);
+int uc_session_status(const uc_session *s, int i);
+int uc_session_result(uc_session *s, int i, uc_result **out);
+int uc_session_set_start(uc_session *s, int i, const double *x, const double *y);
+int uc_session_update_lp(uc_session *s, int i, const uc_presolved *ps);
+size_t uc_session_device_bytes(const uc_session *s);
+void uc_session_free(uc_session *s);
+
+/* Unscale and postsolve the returned point and split it: p, u, v [T*G];
+ * theta, shed, lmp [T*B] (lmp = balance-row duals, $/MWh); f [T*L].  Any
+ * array may be NULL.  stats may be NULL. */
+int uc_get_solution(const uc_result *res, double *p, double *u, double *v, double *theta,
+                    double *f, double *shed, double *lmp, uc_stats *stats);
+/* Raw-LP primal [raw n] and dual [raw m] of the returned point. */
+int uc_get_raw_solution(const uc_result *res, double *x, double *y);
+/* Presolved-space, SCALED iterates: which = 0 current, 1 average since the
+ * last restart, 2 returned point; x [n], y [m]. */
+int uc_get_iterate(const uc_result *res, int which, double *x, double *y);
+
+void uc_free_lp(uc_lp *lp);
+void uc_free_presolved(uc_presolved *ps);
+void uc_free_result(uc_result *res);
+const char *uc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UC_PDHG_H */

@@ -1,0 +1,1018 @@
+// Device side: restarted, diagonally scaled PDHG for one or several
+// (block-diagonally packed) presolved unit-commitment LPs on sm_103a.
+//
+// The paper's GPU arm solves the LP relaxation with PDHG (Sec. II-C, Alg. 1
+// "Solver 1"; Sec. III-C), with an iteration limit of 100,000 and a
+// convergence tolerance of 1e-4 (Sec. II-D).  The method is the PDLP scheme
+// with a constant step (eta = 0.998 / ||A_s||_2, tau = eta / omega,
+// sigma = eta * omega):
+//
+//   x+ = clip(x - tau (c - A^T y), l, u)            k_primal  (A^T row = column of A)
+//   y+ = y + sigma (q - A (2 x+ - x)),  y+_I >= 0   k_dual
+//   every n_eval iterations: KKT of the current point and of the average
+//   since the last restart (k_eval, FP64, deterministic block partials),
+//   then the stopping test, restart test and primal-weight update on the
+//   device (k_control) and the restart itself (k_apply).
+//
+// The path is a sparse, bandwidth-bound contraction (about 0.25 flop/byte),
+// so no tensor cores are used: every row of A and A^T is owned by one thread,
+// vectors are FP64, matrix values FP64 or FP32 (accumulation in FP64).
+// n_eval iterations plus the evaluation are captured once in a CUDA graph and
+// replayed; the host only polls the LPs' 4-byte statuses in pinned memory per
+// replay.  A session keeps the matrices and iterates resident on the device:
+// LPs are reset, re-solved, warm-started or replaced (same matrix, new
+// right-hand side and bounds) without another upload of the matrix.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "uc_internal.h"
+
+namespace uc {
+namespace dev {
+
+constexpr int kThreads = 256;      // threads per CTA of the row kernels (8 warps)
+constexpr int kEvalRows = 1024;    // rows handled by one CTA of the evaluation kernel
+constexpr int kSlots = 9;          // reduction slots per candidate
+constexpr int kPart = 2 * kSlots;  // per-block partial record (current, average)
+
+enum Slot { RP2 = 0, RPU, QY, DY2, RD2, RDU, CX, BND, DX2 };
+enum Status { RUNNING = 0, OPTIMAL = 1, ITER_LIMIT = 2, NUMERIC = 3, NEEDS_INIT = 4 };
+enum Action { ACT_NONE = 0, ACT_RESTART = 1, ACT_FINISH = 2 };
+
+// Per-LP solver state, resident in device memory and only changed by k_control.
+struct Scalars {
+    double omega, tau, sigma, eta;
+    double kkt_anchor, kkt_prev;
+    double tol, q_inf, c_inf;
+    double rel_p, rel_d, rel_g, abs_p, pobj, dobj;   // of the last evaluated / returned point
+    int k_base, j_base, max_iter, n_eval;
+    int status, which, action, cand;
+    double inv_j;                                    // 1 / iterations averaged at the last evaluation
+    int restarts, evals, pad0, pad1;
+};
+
+// One CTA's slice of rows (or columns) of one LP.
+struct Seg {
+    int inst;    // LP index
+    int begin;   // first global row / column
+    int end;     // one past the last
+    int aux;     // dual kernel: first ">=" row of this LP; evaluation kernel: 1 for a
+                 // column slice, (first ">=" row) << 1 for a row slice
+};
+
+struct Bufs {
+    // matrices (block-diagonal when batched, global indices)
+    const int *A_rp, *A_ci, *AT_rp, *AT_ci;
+    const void *A_v, *AT_v;
+    // constant vectors
+    const double *c, *l, *u, *q, *Dr, *Dc;
+    // state: x, y double-buffered
+    double *x[2], *y[2];
+    double *xsum, *ysum, *xa, *ya, *xret, *yret;
+    double *part;
+    Scalars *S;
+    int *status;       // [k] copy of each LP's status, read by the host after every replay
+};
+
+// ---------------------------------------------------------------------------
+// iteration kernels
+// ---------------------------------------------------------------------------
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+    const Seg sg = segs[blockIdx.x];
+    const Scalars *S = b.S + sg.inst;
+    if (S->status != RUNNING || S->k_base + it >= S->max_iter) return;
+    const int j = sg.begin + threadIdx.x;
+    if (j >= sg.end) return;
+    const double tau = S->tau;
+    const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+    const double *__restrict__ y = b.y[src];
+    double acc = 0.0;
+    const int k1 = b.AT_rp[j + 1];
+    for (int k = b.AT_rp[j]; k < k1; k++) acc += (double)v[k] * y[b.AT_ci[k]];
+    double xv = b.x[src][j] - tau * (b.c[j] - acc);
+    xv = fmin(fmax(xv, b.l[j]), b.u[j]);
+    b.x[src ^ 1][j] = xv;
+    b.xsum[j] += xv;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+    const Seg sg = segs[blockIdx.x];
+    const Scalars *S = b.S + sg.inst;
+    if (S->status != RUNNING || S->k_base + it >= S->max_iter) return;
+    const int i = sg.begin + threadIdx.x;
+    if (i >= sg.end) return;
+    const double sigma = S->sigma;
+    const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    const double *__restrict__ xn = b.x[src ^ 1];
+    const double *__restrict__ xo = b.x[src];
+    double acc = 0.0;
+    const int k1 = b.A_rp[i + 1];
+    for (int k = b.A_rp[i]; k < k1; k++) {
+        const int j = b.A_ci[k];
+        acc += (double)v[k] * (2.0 * xn[j] - xo[j]);
+    }
+    double yv = b.y[src][i] + sigma * (b.q[i] - acc);
+    if (i >= sg.aux) yv = fmax(yv, 0.0);
+    b.y[src ^ 1][i] = yv;
+    b.ysum[i] += yv;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation: per-CTA FP64 partials of both candidates (fixed reduction order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_reduce_store(double (&acc)[kPart], double *out) {
+    __shared__ double sh[kThreads / 32][kPart];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < kPart; s++) {
+        double v = acc[s];
+        const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = is_max ? fmax(v, w) : v + w;
+        }
+        if (lane == 0) sh[warp][s] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPart) {
+        const int s = threadIdx.x;
+        const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
+        double v = sh[0][s];
+        for (int w = 1; w < kThreads / 32; w++) v = is_max ? fmax(v, sh[w][s]) : v + sh[w][s];
+        out[s] = v;
+    }
+}
+
+// mode 0: initial point (current only, no average); mode 1: regular evaluation
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs, Bufs b, int mode) {
+    const Seg sg = segs[blockIdx.x];
+    const Scalars *S = b.S + sg.inst;
+    double acc[kPart];
+#pragma unroll
+    for (int s = 0; s < kPart; s++) acc[s] = 0.0;
+    const bool live = (mode == 0) ? (S->status == NEEDS_INIT)
+                                  : (S->status == RUNNING && S->k_base + S->n_eval <= S->max_iter);
+    if (live) {
+        const double inv_j = (mode == 0) ? 0.0 : 1.0 / (double)(S->j_base + S->n_eval);
+        const double *x = b.x[0], *y = b.y[0];
+        const bool rows = (sg.aux & 1) == 0;
+        const int eq_end = sg.aux >> 1;   // rows: first ">=" row
+        if (rows) {
+            const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+            for (int i = sg.begin + threadIdx.x; i < sg.end; i += kThreads) {
+                double ax0 = 0.0, ax1 = 0.0;
+                for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
+                    const int j = b.A_ci[k];
+                    const double a = (double)v[k];
+                    ax0 += a * x[j];
+                    ax1 += a * (b.xsum[j] * inv_j);
+                }
+                const double qi = b.q[i], dri = b.Dr[i], yh = b.ya[i];
+                const bool ineq = i >= eq_end;
+                double r0 = ax0 - qi, r1 = ax1 - qi;
+                if (ineq) { r0 = fmin(r0, 0.0); r1 = fmin(r1, 0.0); }
+                const double y0 = y[i], y1 = b.ysum[i] * inv_j;
+                acc[RP2] += r0 * r0;
+                acc[RPU] = fmax(acc[RPU], fabs(r0) / dri);
+                acc[QY] += qi * y0;
+                acc[DY2] += (y0 - yh) * (y0 - yh);
+                acc[kSlots + RP2] += r1 * r1;
+                acc[kSlots + RPU] = fmax(acc[kSlots + RPU], fabs(r1) / dri);
+                acc[kSlots + QY] += qi * y1;
+                acc[kSlots + DY2] += (y1 - yh) * (y1 - yh);
+            }
+        } else {
+            const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+            for (int j = sg.begin + threadIdx.x; j < sg.end; j += kThreads) {
+                double t0 = 0.0, t1 = 0.0;
+                for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) {
+                    const int i = b.AT_ci[k];
+                    const double a = (double)v[k];
+                    t0 += a * y[i];
+                    t1 += a * (b.ysum[i] * inv_j);
+                }
+                const double cj = b.c[j], lj = b.l[j], uj = b.u[j], dcj = b.Dc[j], xh = b.xa[j];
+                const bool lf = isfinite(lj), uf = isfinite(uj);
+                const double x0 = x[j], x1 = b.xsum[j] * inv_j;
+                const double lam[2] = {cj - t0, cj - t1};
+                const double xs[2] = {x0, x1};
+#pragma unroll
+                for (int cnd = 0; cnd < 2; cnd++) {
+                    const double lm = lam[cnd];
+                    const double lp = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
+                    const double rd = lm - lp;
+                    double bnd = 0.0;
+                    if (lf) bnd += lj * fmax(lp, 0.0);
+                    if (uf) bnd += uj * fmin(lp, 0.0);
+                    double *a = acc + cnd * kSlots;
+                    a[RD2] += rd * rd;
+                    a[RDU] = fmax(a[RDU], fabs(rd) / dcj);
+                    a[CX] += cj * xs[cnd];
+                    a[BND] += bnd;
+                    a[DX2] += (xs[cnd] - xh) * (xs[cnd] - xh);
+                }
+            }
+        }
+    }
+    block_reduce_store(acc, b.part + (size_t)blockIdx.x * kPart);
+}
+
+// ---------------------------------------------------------------------------
+// scalar controller: one CTA per LP
+// ---------------------------------------------------------------------------
+struct InstRange { int eval_begin, eval_end; };
+
+__device__ double kkt_w(double rp2, double rd2, double gap, double w) {
+    return sqrt(w * w * rp2 + rd2 / (w * w) + gap * gap);
+}
+
+__global__ void __launch_bounds__(kThreads) k_control(const InstRange *__restrict__ ranges, Bufs b, int mode) {
+    const int inst = blockIdx.x;
+    Scalars *S = b.S + inst;
+    __shared__ double red[kThreads][kPart];
+    __shared__ int live;
+    if (threadIdx.x == 0) {
+        S->action = ACT_NONE;
+        live = (mode == 0) ? (S->status == NEEDS_INIT) : (S->status == RUNNING);
+    }
+    __syncthreads();
+    if (!live) return;
+    const InstRange r = ranges[inst];
+    double acc[kPart];
+#pragma unroll
+    for (int s = 0; s < kPart; s++) acc[s] = 0.0;
+    for (int blk = r.eval_begin + threadIdx.x; blk < r.eval_end; blk += kThreads) {
+        const double *p = b.part + (size_t)blk * kPart;
+#pragma unroll
+        for (int s = 0; s < kPart; s++) {
+            const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
+            acc[s] = is_max ? fmax(acc[s], p[s]) : acc[s] + p[s];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kPart; s++) red[threadIdx.x][s] = acc[s];
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            for (int s = 0; s < kPart; s++) {
+                const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
+                const double a = red[threadIdx.x][s], c = red[threadIdx.x + h][s];
+                red[threadIdx.x][s] = is_max ? fmax(a, c) : a + c;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double *T = red[0];
+    const double w = S->omega;
+    double K[2], rel[2][3], gap[2], pobj[2], dobj[2];
+    for (int cnd = 0; cnd < 2; cnd++) {
+        const double *a = T + cnd * kSlots;
+        pobj[cnd] = a[CX];
+        dobj[cnd] = a[QY] + a[BND];
+        gap[cnd] = pobj[cnd] - dobj[cnd];
+        K[cnd] = kkt_w(a[RP2], a[RD2], gap[cnd], w);
+        rel[cnd][0] = a[RPU] / (1.0 + S->q_inf);
+        rel[cnd][1] = a[RDU] / (1.0 + S->c_inf);
+        rel[cnd][2] = fabs(gap[cnd]) / (1.0 + fabs(pobj[cnd]) + fabs(dobj[cnd]));
+    }
+    if (mode == 0) {                     // initial anchor
+        S->kkt_anchor = K[0];
+        S->kkt_prev = INFINITY;
+        S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
+        S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
+        S->status = isfinite(K[0]) ? RUNNING : NUMERIC;
+        b.status[inst] = S->status;
+        return;
+    }
+    const int n_eval = S->n_eval;
+    if (S->k_base + n_eval > S->max_iter) {   // partial block: limit reached inside it
+        S->status = ITER_LIMIT;
+        b.status[inst] = S->status;
+        return;
+    }
+    const int k = S->k_base + n_eval;
+    const int j = S->j_base + n_eval;
+    S->evals += 1;
+    S->inv_j = 1.0 / (double)j;
+    S->k_base = k;
+    if (!isfinite(K[0]) || !isfinite(K[1])) {
+        S->status = NUMERIC;
+        b.status[inst] = S->status;
+        return;
+    }
+    for (int cnd = 0; cnd < 2; cnd++) {
+        const double mx = fmax(rel[cnd][0], fmax(rel[cnd][1], rel[cnd][2]));
+        if (mx <= S->tol) {
+            S->status = OPTIMAL;
+            S->which = cnd;
+            S->action = ACT_FINISH;
+            S->rel_p = rel[cnd][0]; S->rel_d = rel[cnd][1]; S->rel_g = rel[cnd][2];
+            S->abs_p = T[cnd * kSlots + RPU]; S->pobj = pobj[cnd]; S->dobj = dobj[cnd];
+            b.status[inst] = S->status;
+            return;
+        }
+    }
+    S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
+    S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
+    const int cand = (K[1] < K[0]) ? 1 : 0;
+    const double kc = K[cand];
+    const bool restart = (kc <= 0.2 * S->kkt_anchor) ||
+                         (kc <= 0.8 * S->kkt_anchor && kc > S->kkt_prev) ||
+                         ((double)j >= 0.36 * (double)k);
+    if (restart) {
+        const double *a = T + cand * kSlots;
+        const double dx = sqrt(a[DX2]), dy = sqrt(a[DY2]);
+        double wn = w;
+        if (dx > 1e-10 && dy > 1e-10) wn = exp(0.5 * log(dy / dx) + 0.5 * log(w));
+        S->omega = wn;
+        S->kkt_anchor = kkt_w(a[RP2], a[RD2], gap[cand], wn);
+        S->kkt_prev = INFINITY;
+        S->j_base = 0;
+        S->restarts += 1;
+        S->tau = S->eta / wn;
+        S->sigma = S->eta * wn;
+        S->cand = cand;
+        S->action = ACT_RESTART;
+    } else {
+        S->kkt_prev = kc;
+        S->j_base = j;
+    }
+    if (k >= S->max_iter) {
+        S->status = ITER_LIMIT;
+        b.status[inst] = S->status;
+    }
+}
+
+// restart (current <- candidate, anchor <- candidate, sums <- 0) or finish (ret <- chosen)
+__global__ void __launch_bounds__(kThreads) k_apply(const Seg *__restrict__ segs, int ncol_blocks, Bufs b) {
+    const Seg sg = segs[blockIdx.x];
+    const Scalars *S = b.S + sg.inst;
+    const int act = S->action;
+    if (act == ACT_NONE) return;
+    const int idx = sg.begin + threadIdx.x;
+    if (idx >= sg.end) return;
+    const bool col = blockIdx.x < (unsigned)ncol_blocks;
+    double *cur = col ? b.x[0] : b.y[0];
+    double *sum = col ? b.xsum : b.ysum;
+    double *anc = col ? b.xa : b.ya;
+    double *ret = col ? b.xret : b.yret;
+    const double avg = sum[idx] * S->inv_j;
+    if (act == ACT_FINISH) {
+        ret[idx] = S->which ? avg : cur[idx];
+        return;
+    }
+    const double v = S->cand ? avg : cur[idx];
+    cur[idx] = v;
+    anc[idx] = v;
+    sum[idx] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration: a device-resident session of k LPs
+// ---------------------------------------------------------------------------
+#define UC_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                       \
+            return UC_ECUDA;                                                           \
+        }                                                                              \
+    } while (0)
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    // uploaded once
+    size_t A_rp, A_ci, A_v, AT_rp, AT_ci, AT_v, segs_p, segs_d, segs_e, segs_a, ranges;
+    // per-LP data (replaced by update_lp)
+    size_t c, l, u, Dc, q, Dr, x_init, y_init, S_init;
+    // working state
+    size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, S, status;
+    size_t upload_end, total;
+};
+
+}  // namespace dev
+}  // namespace uc
+
+struct uc_session {
+    int k = 0, vb = 64;
+    size_t vs = 8;
+    uc_solve_opts o{};
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    std::vector<std::shared_ptr<const uc::PsData>> P;
+    std::vector<int64_t> roff, coff, zoff;
+    int64_t M = 0, N = 0, Z = 0;
+    int n_sp = 0, n_sd = 0, n_se = 0, n_sa = 0;
+    uc::dev::Layout L{};
+    char *D = nullptr;
+    size_t bytes = 0;
+    uc::dev::Bufs b{};
+    const uc::dev::Seg *dsp = nullptr, *dsd = nullptr, *dse = nullptr, *dsa = nullptr;
+    const uc::dev::InstRange *drg = nullptr;
+    std::vector<uc::dev::Scalars> S_init;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t tev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int *h_status = nullptr;      // pinned [k]
+    std::vector<char> active;     // LPs reset since their last result
+    double tp_sum = 0.0, td_sum = 0.0;
+    int timed = 0;
+    long long launches = 0;
+    double upload_ms = 0.0, last_run_ms = 0.0;
+    int host_status = UC_OK;      // UC_ECANCELLED / UC_ETIMEOUT of the last run
+    long long h2d = 0;            // bytes uploaded (create, update_lp, set_start)
+    long long polls = 0;          // replays whose status was copied back
+
+    ~uc_session() {
+        if (s) cudaStreamSynchronize(s);
+        for (auto e : exec) if (e) cudaGraphExecDestroy(e);
+        for (auto g : graph) if (g) cudaGraphDestroy(g);
+        for (auto e : ev) if (e) cudaEventDestroy(e);
+        for (auto &row : tev) for (auto e : row) if (e) cudaEventDestroy(e);
+        if (h_status) cudaFreeHost(h_status);
+        if (D) {
+            if (o.free) o.free(D, bytes, (void *)s, o.alloc_ctx);
+            else cudaFreeAsync(D, s);
+        }
+        if (own_stream && s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    }
+};
+
+namespace uc {
+namespace dev {
+
+template <typename T>
+static void put(std::vector<char> &st, size_t off, const T *src, size_t count) {
+    if (count) std::memcpy(st.data() + off, src, count * sizeof(T));
+}
+
+static Scalars make_scalars(const uc_session &X, const PsData &p) {
+    Scalars s{};
+    s.eta = p.eta;
+    s.omega = p.omega0;
+    s.tau = p.eta / p.omega0;
+    s.sigma = p.eta * p.omega0;
+    s.tol = X.o.tol_rel_kkt;
+    s.q_inf = p.q_inf;
+    s.c_inf = p.c_inf;
+    s.max_iter = X.o.max_iter;
+    s.n_eval = X.o.n_eval;
+    s.kkt_prev = INFINITY;
+    s.status = NEEDS_INIT;
+    return s;
+}
+
+// start point, initial scalars and per-LP vectors of LP i into the staging image
+static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *wx, const double *wy) {
+    const PsData &p = *X.P[i];
+    const Layout &L = X.L;
+    put(st, L.c + X.coff[i] * 8, p.c.data(), p.n());
+    put(st, L.l + X.coff[i] * 8, p.l.data(), p.n());
+    put(st, L.u + X.coff[i] * 8, p.u.data(), p.n());
+    put(st, L.Dc + X.coff[i] * 8, p.Dc.data(), p.n());
+    put(st, L.q + X.roff[i] * 8, p.q.data(), p.m());
+    put(st, L.Dr + X.roff[i] * 8, p.Dr.data(), p.m());
+    double *x0 = (double *)(st.data() + L.x_init) + X.coff[i];
+    double *y0 = (double *)(st.data() + L.y_init) + X.roff[i];
+    for (int c = 0; c < p.n(); c++) x0[c] = std::min(std::max(wx ? wx[c] : 0.0, p.l[c]), p.u[c]);
+    for (int r = 0; r < p.m(); r++) {
+        const double v = wy ? wy[r] : 0.0;
+        y0[r] = r >= p.m_eq ? std::max(v, 0.0) : v;
+    }
+    X.S_init[i] = make_scalars(X, p);
+    put(st, L.S_init + sizeof(Scalars) * i, &X.S_init[i], 1);
+}
+
+static int capture(uc_session &X, int gi) {
+    cudaStream_t s = X.s;
+    const bool timing = X.o.kernel_timing != 0;
+    const Bufs &b = X.b;
+    UC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    auto rec = [&](int e) {
+        if (timing && err == cudaSuccess) err = cudaEventRecordWithFlags(X.tev[gi][e], s, cudaEventRecordExternal);
+    };
+    for (int it = 0; it < X.o.n_eval; it++) {
+        const int src = it & 1;
+        if (it == 0) rec(0);
+        if (X.n_sp) {
+            if (X.vb == 32) k_primal<float><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
+            else k_primal<double><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
+        }
+        if (it == 0) rec(1);
+        if (X.n_sd) {
+            if (X.vb == 32) k_dual<float><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
+            else k_dual<double><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
+        }
+        if (it == 0) rec(2);
+    }
+    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
+    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
+    k_control<<<X.k, kThreads, 0, s>>>(X.drg, b, 1);
+    if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error("recording the iteration graph failed: %s", cudaGetErrorString(err));
+        return UC_ECUDA;
+    }
+    if (ce != cudaSuccess) { set_error("graph capture failed: %s", cudaGetErrorString(ce)); return UC_ECUDA; }
+    X.graph[gi] = g;
+    UC_CUDA(cudaGraphInstantiate(&X.exec[gi], g, 0));
+    return UC_OK;
+}
+
+// launches of one replay without a graph (use_graph = 0)
+static int launch_direct(uc_session &X) {
+    cudaStream_t s = X.s;
+    const Bufs &b = X.b;
+    for (int it = 0; it < X.o.n_eval; it++) {
+        const int src = it & 1;
+        if (X.n_sp) {
+            if (X.vb == 32) k_primal<float><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
+            else k_primal<double><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
+        }
+        if (X.n_sd) {
+            if (X.vb == 32) k_dual<float><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
+            else k_dual<double><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
+        }
+    }
+    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
+    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
+    k_control<<<X.k, kThreads, 0, s>>>(X.drg, b, 1);
+    if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
+    UC_CUDA(cudaGetLastError());
+    UC_CUDA(cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s));
+    return UC_OK;
+}
+
+static int session_create(const PsData *const *Pp, const std::shared_ptr<const PsData> *owners, int k,
+                          const uc_solve_opts &o, cudaStream_t user_stream, uc_session **out) {
+    *out = nullptr;
+    if (k < 1) { set_error("need at least one LP"); return UC_EINVAL; }
+    if (o.n_eval < 2 || (o.n_eval & 1)) { set_error("n_eval must be even and >= 2"); return UC_EINVAL; }
+    if (o.max_iter < 0) { set_error("max_iter must be >= 0"); return UC_EINVAL; }
+    auto *X = new (std::nothrow) uc_session();
+    if (!X) { set_error("out of host memory"); return UC_ENOMEM; }
+    std::unique_ptr<uc_session> guard(X);
+    X->k = k;
+    X->o = o;
+    X->vb = Pp[0]->value_bits;
+    X->vs = X->vb == 32 ? 4 : 8;
+    X->P.assign(owners, owners + k);
+    for (int i = 1; i < k; i++)
+        if (Pp[i]->value_bits != X->vb) { set_error("batched LPs must share value_bits"); return UC_EINVAL; }
+    X->roff.assign(k + 1, 0); X->coff.assign(k + 1, 0); X->zoff.assign(k + 1, 0);
+    for (int i = 0; i < k; i++) {
+        X->roff[i + 1] = X->roff[i] + Pp[i]->m();
+        X->coff[i + 1] = X->coff[i] + Pp[i]->n();
+        X->zoff[i + 1] = X->zoff[i] + Pp[i]->A.nnz();
+    }
+    X->M = X->roff[k]; X->N = X->coff[k]; X->Z = X->zoff[k];
+    const int64_t M = X->M, N = X->N, Z = X->Z;
+    // row indices are also stored shifted left by one bit in the evaluation table
+    if (M >= (1LL << 30) || N >= INT32_MAX || Z >= INT32_MAX) { set_error("batch too large for int32 indices"); return UC_EINVAL; }
+
+    // CTA tables: every CTA works on a slice of one LP
+    std::vector<Seg> sp, sd, se, sa;
+    std::vector<InstRange> ranges(k);
+    for (int i = 0; i < k; i++) {
+        const int64_t c0 = X->coff[i], c1 = X->coff[i + 1], r0 = X->roff[i], r1 = X->roff[i + 1];
+        for (int64_t s = c0; s < c1; s += kThreads) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + kThreads, c1), 0});
+        const int eq_end = (int)(r0 + Pp[i]->m_eq);
+        for (int64_t s = r0; s < r1; s += kThreads) sd.push_back({i, (int)s, (int)std::min<int64_t>(s + kThreads, r1), eq_end});
+        ranges[i].eval_begin = (int)se.size();
+        for (int64_t s = r0; s < r1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, r1), eq_end << 1});
+        for (int64_t s = c0; s < c1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, c1), 1});
+        if (se.size() == (size_t)ranges[i].eval_begin) se.push_back({i, 0, 0, 0});
+        ranges[i].eval_end = (int)se.size();
+    }
+    sa = sp;
+    sa.insert(sa.end(), sd.begin(), sd.end());
+    X->n_sp = (int)sp.size(); X->n_sd = (int)sd.size(); X->n_se = (int)se.size(); X->n_sa = (int)sa.size();
+
+    Layout &L = X->L;
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t p = off; off += align_up(std::max<size_t>(n, 1), 256); return p; };
+    const size_t vs = X->vs;
+    L.A_rp = take((M + 1) * 4); L.A_ci = take(Z * 4); L.A_v = take(Z * vs);
+    L.AT_rp = take((N + 1) * 4); L.AT_ci = take(Z * 4); L.AT_v = take(Z * vs);
+    L.segs_p = take(sizeof(Seg) * X->n_sp); L.segs_d = take(sizeof(Seg) * X->n_sd);
+    L.segs_e = take(sizeof(Seg) * X->n_se); L.segs_a = take(sizeof(Seg) * X->n_sa);
+    L.ranges = take(sizeof(InstRange) * k);
+    L.c = take(N * 8); L.l = take(N * 8); L.u = take(N * 8); L.Dc = take(N * 8);
+    L.q = take(M * 8); L.Dr = take(M * 8);
+    L.x_init = take(N * 8); L.y_init = take(M * 8); L.S_init = take(sizeof(Scalars) * k);
+    L.upload_end = off;
+    L.x0 = take(N * 8); L.x1 = take(N * 8); L.y0 = take(M * 8); L.y1 = take(M * 8);
+    L.xsum = take(N * 8); L.ysum = take(M * 8); L.xa = take(N * 8); L.ya = take(M * 8);
+    L.xret = take(N * 8); L.yret = take(M * 8);
+    L.part = take(sizeof(double) * kPart * X->n_se);
+    L.S = take(sizeof(Scalars) * k);
+    L.status = take(sizeof(int) * k);
+    L.total = off;
+
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<char> st(L.upload_end);
+    X->S_init.resize(k);
+    {
+        int32_t *arp = (int32_t *)(st.data() + L.A_rp), *atrp = (int32_t *)(st.data() + L.AT_rp);
+        int32_t *aci = (int32_t *)(st.data() + L.A_ci), *atci = (int32_t *)(st.data() + L.AT_ci);
+        for (int i = 0; i < k; i++) {
+            const PsData &p = *Pp[i];
+            const int64_t ro = X->roff[i], co = X->coff[i], zo = X->zoff[i];
+            for (int r = 0; r < p.m(); r++) arp[ro + r] = (int32_t)(p.A.rowptr[r] + zo);
+            for (int c = 0; c < p.n(); c++) atrp[co + c] = (int32_t)(p.AT.rowptr[c] + zo);
+            for (int64_t z = 0; z < p.A.nnz(); z++) {
+                aci[zo + z] = (int32_t)(p.A.colidx[z] + co);
+                atci[zo + z] = (int32_t)(p.AT.colidx[z] + ro);
+            }
+            if (X->vb == 32) {
+                put(st, L.A_v + zo * 4, p.A_val32.data(), p.A.nnz());
+                put(st, L.AT_v + zo * 4, p.AT_val32.data(), p.A.nnz());
+            } else {
+                put(st, L.A_v + zo * 8, p.A.val.data(), p.A.nnz());
+                put(st, L.AT_v + zo * 8, p.AT.val.data(), p.A.nnz());
+            }
+            stage_lp(*X, st, i, (k == 1) ? o.warm_x : nullptr, (k == 1) ? o.warm_y : nullptr);
+        }
+        arp[M] = (int32_t)Z;
+        atrp[N] = (int32_t)Z;
+        put(st, L.segs_p, sp.data(), X->n_sp);
+        put(st, L.segs_d, sd.data(), X->n_sd);
+        put(st, L.segs_e, se.data(), X->n_se);
+        put(st, L.segs_a, sa.data(), X->n_sa);
+        put(st, L.ranges, ranges.data(), k);
+    }
+
+    if (user_stream) X->s = user_stream;
+    else {
+        UC_CUDA(cudaStreamCreateWithFlags(&X->s, cudaStreamNonBlocking));
+        X->own_stream = true;
+    }
+    cudaStream_t s = X->s;
+    X->bytes = L.total;
+    if (o.alloc) {
+        X->D = (char *)o.alloc(L.total, (void *)s, o.alloc_ctx);
+        if (!X->D) { set_error("device allocator returned NULL for %zu bytes", L.total); return UC_ENOMEM; }
+    } else {
+        cudaError_t e = cudaMallocAsync((void **)&X->D, L.total, s);
+        if (e != cudaSuccess) {
+            X->D = nullptr;
+            set_error("cudaMallocAsync(%zu) failed: %s", L.total, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? UC_ENOMEM : UC_ECUDA;
+        }
+    }
+    char *D = X->D;
+    UC_CUDA(cudaMemcpyAsync(D, st.data(), L.upload_end, cudaMemcpyHostToDevice, s));
+    X->h2d = (long long)L.upload_end;
+    Bufs &b = X->b;
+    b.A_rp = (const int *)(D + L.A_rp); b.A_ci = (const int *)(D + L.A_ci); b.A_v = D + L.A_v;
+    b.AT_rp = (const int *)(D + L.AT_rp); b.AT_ci = (const int *)(D + L.AT_ci); b.AT_v = D + L.AT_v;
+    b.c = (const double *)(D + L.c); b.l = (const double *)(D + L.l); b.u = (const double *)(D + L.u);
+    b.q = (const double *)(D + L.q); b.Dr = (const double *)(D + L.Dr); b.Dc = (const double *)(D + L.Dc);
+    b.x[0] = (double *)(D + L.x0); b.x[1] = (double *)(D + L.x1);
+    b.y[0] = (double *)(D + L.y0); b.y[1] = (double *)(D + L.y1);
+    b.xsum = (double *)(D + L.xsum); b.ysum = (double *)(D + L.ysum);
+    b.xa = (double *)(D + L.xa); b.ya = (double *)(D + L.ya);
+    b.xret = (double *)(D + L.xret); b.yret = (double *)(D + L.yret);
+    b.part = (double *)(D + L.part);
+    b.S = (Scalars *)(D + L.S);
+    b.status = (int *)(D + L.status);
+    X->dsp = (const Seg *)(D + L.segs_p); X->dsd = (const Seg *)(D + L.segs_d);
+    X->dse = (const Seg *)(D + L.segs_e); X->dsa = (const Seg *)(D + L.segs_a);
+    X->drg = (const InstRange *)(D + L.ranges);
+    // nothing runs until the first reset: mark every LP finished-as-idle
+    UC_CUDA(cudaMemsetAsync(D + L.S, 0xff, sizeof(Scalars) * k, s));   // status -1: idle
+    UC_CUDA(cudaMemsetAsync(D + L.status, 0xff, sizeof(int) * k, s));
+    UC_CUDA(cudaHostAlloc((void **)&X->h_status, sizeof(int) * k, cudaHostAllocDefault));
+    for (int i = 0; i < k; i++) X->h_status[i] = -1;
+    X->active.assign(k, 0);
+    const bool timing = o.kernel_timing != 0;
+    for (auto &e : X->ev) UC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (o.use_graph) {
+        for (int gi = 0; gi < 2; gi++) {
+            if (timing)
+                for (auto &e : X->tev[gi]) UC_CUDA(cudaEventCreate(&e));
+            int rc = capture(*X, gi);
+            if (rc) return rc;
+            if (!timing) break;   // one graph suffices without per-replay events
+        }
+    }
+    UC_CUDA(cudaStreamSynchronize(s));
+    X->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = guard.release();
+    return UC_OK;
+}
+
+// state of LP i (or all, i < 0) <- its start point; then the anchor KKT on the device
+static int session_reset(uc_session &X, int which) {
+    cudaStream_t s = X.s;
+    char *D = X.D;
+    const Layout &L = X.L;
+    const int i0 = which < 0 ? 0 : which, i1 = which < 0 ? X.k : which + 1;
+    if (which >= X.k) { set_error("LP index %d out of range", which); return UC_EINVAL; }
+    for (int i = i0; i < i1; i++) {
+        const size_t cx = X.coff[i] * 8, nx = (X.coff[i + 1] - X.coff[i]) * 8;
+        const size_t cy = X.roff[i] * 8, ny = (X.roff[i + 1] - X.roff[i]) * 8;
+        if (nx) {
+            for (size_t dst : {L.x0, L.x1, L.xa})
+                UC_CUDA(cudaMemcpyAsync(D + dst + cx, D + L.x_init + cx, nx, cudaMemcpyDeviceToDevice, s));
+            UC_CUDA(cudaMemsetAsync(D + L.xsum + cx, 0, nx, s));
+        }
+        if (ny) {
+            for (size_t dst : {L.y0, L.y1, L.ya})
+                UC_CUDA(cudaMemcpyAsync(D + dst + cy, D + L.y_init + cy, ny, cudaMemcpyDeviceToDevice, s));
+            UC_CUDA(cudaMemsetAsync(D + L.ysum + cy, 0, ny, s));
+        }
+        UC_CUDA(cudaMemcpyAsync(D + L.S + sizeof(Scalars) * i, D + L.S_init + sizeof(Scalars) * i,
+                                sizeof(Scalars), cudaMemcpyDeviceToDevice, s));
+        X.active[i] = 1;
+        X.h_status[i] = NEEDS_INIT;
+    }
+    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, 0);
+    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, 0);
+    k_control<<<X.k, kThreads, 0, s>>>(X.drg, X.b, 0);
+    X.launches += 2;
+    UC_CUDA(cudaGetLastError());
+    return UC_OK;
+}
+
+static bool all_done(const uc_session &X) {
+    for (int i = 0; i < X.k; i++) {
+        if (!X.active[i]) continue;
+        const int st = ((volatile int *)X.h_status)[i];
+        if (st == RUNNING || st == NEEDS_INIT) return false;
+    }
+    return true;
+}
+
+// replays until every active LP has stopped, or max_replays, cancel or timeout
+static int session_run(uc_session &X, int max_replays) {
+    cudaStream_t s = X.s;
+    const bool timing = X.o.kernel_timing != 0 && X.o.use_graph;
+    const int depth = 2;
+    int launched = 0, checked = 0;
+    X.host_status = UC_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        while (launched < max_replays && launched - checked < depth) {
+            if (X.o.use_graph) UC_CUDA(cudaGraphLaunch(X.exec[timing ? (launched & 1) : 0], s));
+            else { int rc = launch_direct(X); if (rc) return rc; }
+            UC_CUDA(cudaEventRecord(X.ev[launched & 3], s));
+            launched++;
+            X.polls++;
+            X.launches += 2LL * X.o.n_eval + 3;
+        }
+        if (checked >= launched) break;
+        UC_CUDA(cudaEventSynchronize(X.ev[checked & 3]));
+        const int gi = checked & 1;
+        checked++;
+        const bool done = all_done(X);
+        if (timing && !done) {
+            float a = 0.f, c = 0.f;
+            if (cudaEventElapsedTime(&a, X.tev[gi][0], X.tev[gi][1]) == cudaSuccess &&
+                cudaEventElapsedTime(&c, X.tev[gi][1], X.tev[gi][2]) == cudaSuccess) {
+                X.tp_sum += a; X.td_sum += c; X.timed++;
+            }
+        }
+        if (done) break;
+        if (X.o.cancel && *X.o.cancel) { X.host_status = UC_ECANCELLED; break; }
+        if (X.o.timeout_ms > 0) {
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (ms > X.o.timeout_ms) { X.host_status = UC_ETIMEOUT; break; }
+        }
+    }
+    UC_CUDA(cudaStreamSynchronize(s));
+    UC_CUDA(cudaGetLastError());
+    X.last_run_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return UC_OK;
+}
+
+static int session_result(uc_session &X, int i, uc_result **out) {
+    *out = nullptr;
+    if (i < 0 || i >= X.k) { set_error("LP index %d out of range", i); return UC_EINVAL; }
+    cudaStream_t s = X.s;
+    Scalars S;
+    UC_CUDA(cudaMemcpyAsync(&S, X.b.S + i, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    UC_CUDA(cudaStreamSynchronize(s));
+    const PsData &p = *X.P[i];
+    const int n = p.n(), m = p.m();
+    auto *res = new (std::nothrow) uc_result();
+    if (!res) { set_error("out of host memory"); return UC_ENOMEM; }
+    std::unique_ptr<uc_result> guard(res);
+    res->ps = X.P[i];
+    const int n_eval = X.o.n_eval;
+    const int part = X.o.max_iter % n_eval;
+    // current iterate: buffer 0 after a full block; after a limit reached
+    // inside a block, buffer (max_iter mod n_eval) & 1
+    const int cur = (S.status == ITER_LIMIT) ? (part & 1) : 0;
+    int j_now = S.j_base;
+    if (S.status == ITER_LIMIT && part) j_now = S.j_base + part;
+    res->x_cur.resize(n); res->y_cur.resize(m); res->x_avg.resize(n); res->y_avg.resize(m);
+    const size_t cx = X.coff[i], cy = X.roff[i];
+    UC_CUDA(cudaMemcpyAsync(res->x_cur.data(), X.b.x[cur] + cx, n * 8, cudaMemcpyDeviceToHost, s));
+    UC_CUDA(cudaMemcpyAsync(res->y_cur.data(), X.b.y[cur] + cy, m * 8, cudaMemcpyDeviceToHost, s));
+    UC_CUDA(cudaMemcpyAsync(res->x_avg.data(), X.b.xsum + cx, n * 8, cudaMemcpyDeviceToHost, s));
+    UC_CUDA(cudaMemcpyAsync(res->y_avg.data(), X.b.ysum + cy, m * 8, cudaMemcpyDeviceToHost, s));
+    if (S.status == OPTIMAL) {
+        res->x_ret.resize(n); res->y_ret.resize(m);
+        UC_CUDA(cudaMemcpyAsync(res->x_ret.data(), X.b.xret + cx, n * 8, cudaMemcpyDeviceToHost, s));
+        UC_CUDA(cudaMemcpyAsync(res->y_ret.data(), X.b.yret + cy, m * 8, cudaMemcpyDeviceToHost, s));
+    }
+    UC_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
+    for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
+    if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
+    uc_stats &o = res->stats;
+    int status;
+    if (S.status == OPTIMAL) status = UC_OK;
+    else if (S.status == ITER_LIMIT) status = UC_EITERLIMIT;
+    else if (S.status == NUMERIC) status = UC_ENUMERIC;
+    else status = X.host_status ? X.host_status : UC_EITERLIMIT;
+    o.status = status;
+    o.iters = (S.status == ITER_LIMIT) ? X.o.max_iter : S.k_base;
+    o.restarts = S.restarts;
+    o.evals = S.evals;
+    o.returned_average = (S.status == OPTIMAL && S.which == 1) ? 1 : 0;
+    o.rel_primal = S.rel_p; o.rel_dual = S.rel_d; o.rel_gap = S.rel_g;
+    o.abs_primal = S.abs_p;
+    o.dual_objective = S.dobj + p.obj_const;
+    o.omega = S.omega;
+    o.solve_ms = X.last_run_ms;
+    o.upload_ms = X.upload_ms;
+    o.primal_kernel_ms = X.timed ? X.tp_sum / X.timed : 0.0;
+    o.dual_kernel_ms = X.timed ? X.td_sum / X.timed : 0.0;
+    o.timed_launches = X.timed;
+    o.kernel_launches = (int)std::min<long long>(X.launches, INT32_MAX);
+    o.h2d_bytes = X.h2d;
+    o.d2h_bytes = (long long)(n + m) * 8 * (S.status == OPTIMAL ? 3 : 2) + (long long)sizeof(Scalars) +
+                  X.polls * 4LL * X.k;
+    X.active[i] = 0;
+    *out = guard.release();
+    return status;
+}
+
+static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const PsData> &np) {
+    if (i < 0 || i >= X.k) { set_error("LP index %d out of range", i); return UC_EINVAL; }
+    const PsData &a = *X.P[i], &c = *np;
+    if (a.n() != c.n() || a.m() != c.m() || a.m_eq != c.m_eq || a.A.rowptr != c.A.rowptr ||
+        a.A.colidx != c.A.colidx || a.A.val != c.A.val || a.value_bits != c.value_bits) {
+        set_error("update_lp: the new LP must have the same scaled matrix as slot %d", i);
+        return UC_EINVAL;
+    }
+    X.P[i] = np;
+    const Layout &L = X.L;
+    const size_t cx = X.coff[i] * 8, cy = X.roff[i] * 8;
+    std::vector<double> x0(c.n()), y0(c.m(), 0.0);
+    for (int j = 0; j < c.n(); j++) x0[j] = std::min(std::max(0.0, c.l[j]), c.u[j]);
+    auto h2d = [&](size_t base, size_t off, const std::vector<double> &v) -> int {
+        if (!v.empty()) UC_CUDA(cudaMemcpyAsync(X.D + base + off, v.data(), v.size() * 8, cudaMemcpyHostToDevice, X.s));
+        return UC_OK;
+    };
+    int rc = 0;
+    rc |= h2d(L.c, cx, c.c); rc |= h2d(L.l, cx, c.l); rc |= h2d(L.u, cx, c.u); rc |= h2d(L.Dc, cx, c.Dc);
+    rc |= h2d(L.x_init, cx, x0); rc |= h2d(L.q, cy, c.q); rc |= h2d(L.Dr, cy, c.Dr); rc |= h2d(L.y_init, cy, y0);
+    if (rc) return UC_ECUDA;
+    X.S_init[i] = make_scalars(X, c);
+    UC_CUDA(cudaMemcpyAsync(X.D + L.S_init + sizeof(Scalars) * i, &X.S_init[i], sizeof(Scalars),
+                            cudaMemcpyHostToDevice, X.s));
+    X.h2d += (long long)(5 * c.n() + 3 * c.m()) * 8 + (long long)sizeof(Scalars);
+    UC_CUDA(cudaStreamSynchronize(X.s));
+    return UC_OK;
+}
+
+static int session_set_start(uc_session &X, int i, const double *x, const double *y) {
+    if (i < 0 || i >= X.k) { set_error("LP index %d out of range", i); return UC_EINVAL; }
+    const PsData &p = *X.P[i];
+    std::vector<double> xs(p.n()), ys(p.m());
+    for (int c = 0; c < p.n(); c++) xs[c] = std::min(std::max(x ? x[c] : 0.0, p.l[c]), p.u[c]);
+    for (int r = 0; r < p.m(); r++) { const double v = y ? y[r] : 0.0; ys[r] = r >= p.m_eq ? std::max(v, 0.0) : v; }
+    if (p.n()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.x_init + X.coff[i] * 8, xs.data(), p.n() * 8, cudaMemcpyHostToDevice, X.s));
+    if (p.m()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.y_init + X.roff[i] * 8, ys.data(), p.m() * 8, cudaMemcpyHostToDevice, X.s));
+    X.h2d += (long long)(p.n() + p.m()) * 8;
+    UC_CUDA(cudaStreamSynchronize(X.s));
+    return UC_OK;
+}
+
+static int max_replays(const uc_session &X) { return X.o.max_iter / X.o.n_eval + 1; }
+
+}  // namespace dev
+}  // namespace uc
+
+using namespace uc;
+
+extern "C" {
+
+int uc_session_create(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
+                      uc_session **out) {
+    if (!ps || !out || k < 1) { set_error("uc_session_create: bad arguments"); return UC_EINVAL; }
+    uc_solve_opts o;
+    uc_default_solve_opts(&o);
+    if (opts) o = *opts;
+    std::vector<const PsData *> v(k);
+    std::vector<std::shared_ptr<const PsData>> own(k);
+    for (int i = 0; i < k; i++) {
+        if (!ps[i]) { set_error("uc_session_create: null LP %d", i); return UC_EINVAL; }
+        v[i] = ps[i]->d.get();
+        own[i] = ps[i]->d;
+    }
+    return dev::session_create(v.data(), own.data(), k, o, (cudaStream_t)stream, out);
+}
+
+int uc_session_reset(uc_session *s, int i) {
+    if (!s) { set_error("uc_session_reset: null session"); return UC_EINVAL; }
+    return dev::session_reset(*s, i);
+}
+
+int uc_session_run(uc_session *s, int max_replays, int *n_running) {
+    if (!s) { set_error("uc_session_run: null session"); return UC_EINVAL; }
+    int rc = dev::session_run(*s, max_replays > 0 ? max_replays : dev::max_replays(*s));
+    if (n_running) {
+        int r = 0;
+        for (int i = 0; i < s->k; i++)
+            if (s->active[i] && (s->h_status[i] == dev::RUNNING || s->h_status[i] == dev::NEEDS_INIT)) r++;
+        *n_running = r;
+    }
+    if (rc) return rc;
+    return s->host_status;
+}
+
+int uc_session_status(const uc_session *s, int i) {
+    if (!s || i < 0 || i >= s->k) { set_error("uc_session_status: bad arguments"); return UC_EINVAL; }
+    if (!s->active[i]) return 1;                           // idle
+    switch (s->h_status[i]) {
+        case dev::RUNNING: case dev::NEEDS_INIT: return 2;  // still iterating
+        case dev::OPTIMAL: return UC_OK;
+        case dev::ITER_LIMIT: return UC_EITERLIMIT;
+        case dev::NUMERIC: return UC_ENUMERIC;
+        default: return 1;
+    }
+}
+
+int uc_session_result(uc_session *s, int i, uc_result **out) {
+    if (!s || !out) { set_error("uc_session_result: null argument"); return UC_EINVAL; }
+    return dev::session_result(*s, i, out);
+}
+
+int uc_session_set_start(uc_session *s, int i, const double *x, const double *y) {
+    if (!s) { set_error("uc_session_set_start: null session"); return UC_EINVAL; }
+    return dev::session_set_start(*s, i, x, y);
+}
+
+int uc_session_update_lp(uc_session *s, int i, const uc_presolved *ps) {
+    if (!s || !ps) { set_error("uc_session_update_lp: null argument"); return UC_EINVAL; }
+    return dev::session_update_lp(*s, i, ps->d);
+}
+
+size_t uc_session_device_bytes(const uc_session *s) { return s ? s->bytes : 0; }
+
+void uc_session_free(uc_session *s) { delete s; }
+
+int uc_solve(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc_result **out) {
+    if (!ps || !out) { set_error("uc_solve: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    return uc_solve_batch(&ps, 1, opts, stream, out);
+}
+
+int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
+                   uc_result **outs) {
+    if (!ps || !outs || k < 1) { set_error("uc_solve_batch: bad arguments"); return UC_EINVAL; }
+    for (int i = 0; i < k; i++) outs[i] = nullptr;
+    uc_session *s = nullptr;
+    int rc = uc_session_create(ps, k, opts, stream, &s);
+    if (rc) return rc;
+    std::unique_ptr<uc_session> guard(s);
+    rc = uc_session_reset(s, -1);
+    if (rc) return rc;
+    rc = dev::session_run(*s, dev::max_replays(*s));
+    if (rc) return rc;
+    int overall = UC_OK;
+    for (int i = 0; i < k; i++) {
+        int st = dev::session_result(*s, i, &outs[i]);
+        if (!outs[i]) return st;
+        if (st != UC_OK && overall == UC_OK) overall = st;
+    }
+    return overall;
+}
+
+}  // extern "C"

@@ -1,0 +1,659 @@
+// Host side of the unit-commitment LP solver: LP construction, presolve,
+// diagonal scaling, the ||A||_2 estimate behind the PDHG step size, and
+// postsolve.  None of this runs on the device; it feeds the device solve.
+//
+// Model (DC relaxation of the UC problem of Sec. II-A, "same relaxed problem"
+// of Sec. II-C): per period t, columns [p (G), u (G), v (G), theta (B), f (L),
+// shed (B)], equality rows (bus balance, line-flow definition) of all periods
+// first, then ">=" rows (Pmax u - p, p - Pmin u, startup, ramp up, ramp down).
+// Presolve is the reduced form of Sec. II-D's presolve that the device path
+// needs; scaling is the PDLP preconditioner (Ruiz, then Pock-Chambolle).
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <thread>
+
+#include "uc_internal.h"
+
+namespace uc {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void clear_error() { g_err.clear(); }
+
+Csr transpose(const Csr &A) {
+    Csr T;
+    T.rows = A.cols;
+    T.cols = A.rows;
+    T.rowptr.assign((size_t)A.cols + 1, 0);
+    for (int32_t j : A.colidx) T.rowptr[(size_t)j + 1]++;
+    for (int j = 0; j < A.cols; j++) T.rowptr[j + 1] += T.rowptr[j];
+    T.colidx.resize(A.colidx.size());
+    T.val.resize(A.val.size());
+    std::vector<int32_t> next(T.rowptr.begin(), T.rowptr.end() - 1);
+    for (int i = 0; i < A.rows; i++) {
+        for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+            int32_t j = A.colidx[k];
+            int32_t dst = next[j]++;
+            T.colidx[dst] = i;   // rows visited in order -> ascending
+            T.val[dst] = A.val[k];
+        }
+    }
+    return T;
+}
+
+// Runs fn(begin, end) over [0, n) in fixed-size chunks on `threads` workers.
+template <class F>
+static void parallel_for(int64_t n, int threads, F fn) {
+    const int64_t chunk = 1 << 14;
+    int64_t nchunks = (n + chunk - 1) / chunk;
+    if (threads <= 1 || nchunks <= 1) {
+        fn((int64_t)0, n);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            int64_t c = next.fetch_add(1);
+            if (c >= nchunks) return;
+            fn(c * chunk, std::min(n, (c + 1) * chunk));
+        }
+    };
+    std::vector<std::thread> pool;
+    int nt = (int)std::min<int64_t>(threads, nchunks);
+    for (int t = 1; t < nt; t++) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+}
+
+// Deterministic sum of squares: fixed 16384-element chunks, partials added in order.
+static double sumsq(const std::vector<double> &v, int threads) {
+    const int64_t chunk = 1 << 14;
+    int64_t n = (int64_t)v.size();
+    int64_t nch = (n + chunk - 1) / chunk;
+    std::vector<double> part((size_t)std::max<int64_t>(nch, 1), 0.0);
+    parallel_for(nch, threads, [&](int64_t b, int64_t e) {
+        for (int64_t c = b; c < e; c++) {
+            double s = 0.0;
+            for (int64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); i++) s += v[i] * v[i];
+            part[c] = s;
+        }
+    });
+    double s = 0.0;
+    for (double p : part) s += p;
+    return s;
+}
+
+static void spmv(const Csr &A, const std::vector<double> &x, std::vector<double> &y, int threads) {
+    y.resize(A.rows);
+    parallel_for(A.rows, threads, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++) {
+            double s = 0.0;
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) s += A.val[k] * x[A.colidx[k]];
+            y[i] = s;
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
+// LP construction
+// ---------------------------------------------------------------------------
+static int validate(const uc_problem *P) {
+    if (!P) { set_error("uc_build_lp: null problem"); return UC_EINVAL; }
+    if (P->B < 1 || P->L < 0 || P->G < 0 || P->T < 1) {
+        set_error("uc_build_lp: need B >= 1, L >= 0, G >= 0, T >= 1 (got %d %d %d %d)", P->B, P->L, P->G, P->T);
+        return UC_EINVAL;
+    }
+    if (P->ref_bus < 0 || P->ref_bus >= P->B) { set_error("uc_build_lp: ref_bus out of range"); return UC_EINVAL; }
+    if ((P->L > 0 && (!P->line_from || !P->line_to || !P->x_pu || !P->fmax)) ||
+        (P->G > 0 && (!P->gen_bus || !P->pmax || !P->pmin || !P->ramp || !P->c_lin || !P->c_nl ||
+                      !P->c_su || !P->u0)) || !P->load) {
+        set_error("uc_build_lp: null data array");
+        return UC_EINVAL;
+    }
+    for (int l = 0; l < P->L; l++) {
+        int a = P->line_from[l], b = P->line_to[l];
+        if (a < 0 || a >= P->B || b < 0 || b >= P->B) { set_error("line %d: bus index out of range", l); return UC_EINVAL; }
+        if (a == b) { set_error("line %d: self loop at bus %d", l, a); return UC_EINVAL; }
+        if (!(P->x_pu[l] > 0.0) || !std::isfinite(P->x_pu[l])) { set_error("line %d: reactance must be > 0", l); return UC_EINVAL; }
+        if (!(P->fmax[l] >= 0.0) || !std::isfinite(P->fmax[l])) { set_error("line %d: flow limit must be finite and >= 0", l); return UC_EINVAL; }
+    }
+    for (int g = 0; g < P->G; g++) {
+        if (P->gen_bus[g] < 0 || P->gen_bus[g] >= P->B) { set_error("unit %d: bus index out of range", g); return UC_EINVAL; }
+        double a = P->pmin[g], b = P->pmax[g];
+        if (!(a >= 0.0) || !(b >= a) || !std::isfinite(b)) { set_error("unit %d: need 0 <= pmin <= pmax < inf", g); return UC_EINVAL; }
+        if (!(P->ramp[g] >= 0.0) || !std::isfinite(P->ramp[g])) { set_error("unit %d: ramp must be finite and >= 0", g); return UC_EINVAL; }
+        if (!std::isfinite(P->c_lin[g]) || !std::isfinite(P->c_nl[g]) || !std::isfinite(P->c_su[g]) ||
+            !std::isfinite(P->u0[g])) { set_error("unit %d: non-finite cost or u0", g); return UC_EINVAL; }
+    }
+    int64_t TB = (int64_t)P->T * P->B;
+    for (int64_t k = 0; k < TB; k++)
+        if (!(P->load[k] >= 0.0) || !std::isfinite(P->load[k])) { set_error("load[%lld] must be finite and >= 0", (long long)k); return UC_EINVAL; }
+    if (!std::isfinite(P->voll)) { set_error("voll must be finite"); return UC_EINVAL; }
+    int64_t nc = 3LL * P->G + P->B + P->L + (P->voll > 0 ? P->B : 0);
+    if (nc * P->T >= (1LL << 31) - 1) { set_error("problem too large for int32 indices"); return UC_EINVAL; }
+    return UC_OK;
+}
+
+static int build(const uc_problem *P, RawLp &lp) {
+    const int B = P->B, L = P->L, G = P->G, T = P->T;
+    const bool hs = P->voll > 0.0;
+    const int nc = 3 * G + B + L + (hs ? B : 0);
+    const int64_t n = (int64_t)T * nc;
+    lp.B = B; lp.L = L; lp.G = G; lp.T = T; lp.nc = nc; lp.has_shed = hs;
+    lp.c.assign(n, 0.0); lp.l.assign(n, 0.0); lp.u.assign(n, 0.0);
+    lp.col_kind.assign(n, 0); lp.col_t.assign(n, 0); lp.col_idx.assign(n, 0);
+    const double inf = std::numeric_limits<double>::infinity();
+    auto P_ = [&](int t, int g) { return t * nc + g; };
+    auto U_ = [&](int t, int g) { return t * nc + G + g; };
+    auto V_ = [&](int t, int g) { return t * nc + 2 * G + g; };
+    auto TH = [&](int t, int b) { return t * nc + 3 * G + b; };
+    auto F_ = [&](int t, int l) { return t * nc + 3 * G + B + l; };
+    auto S_ = [&](int t, int b) { return t * nc + 3 * G + B + L + b; };
+    for (int t = 0; t < T; t++) {
+        for (int g = 0; g < G; g++) {
+            int j = P_(t, g); lp.c[j] = P->c_lin[g]; lp.l[j] = 0; lp.u[j] = P->pmax[g];
+            lp.col_kind[j] = COL_P; lp.col_t[j] = t; lp.col_idx[j] = g;
+            j = U_(t, g); lp.c[j] = P->c_nl[g]; lp.l[j] = 0; lp.u[j] = 1;
+            lp.col_kind[j] = COL_U; lp.col_t[j] = t; lp.col_idx[j] = g;
+            j = V_(t, g); lp.c[j] = P->c_su[g]; lp.l[j] = 0; lp.u[j] = 1;
+            lp.col_kind[j] = COL_V; lp.col_t[j] = t; lp.col_idx[j] = g;
+        }
+        for (int b = 0; b < B; b++) {
+            int j = TH(t, b);
+            if (b == P->ref_bus) { lp.l[j] = 0; lp.u[j] = 0; }
+            else { lp.l[j] = -inf; lp.u[j] = inf; }
+            lp.col_kind[j] = COL_TH; lp.col_t[j] = t; lp.col_idx[j] = b;
+        }
+        for (int l = 0; l < L; l++) {
+            int j = F_(t, l); lp.l[j] = -P->fmax[l]; lp.u[j] = P->fmax[l];
+            lp.col_kind[j] = COL_F; lp.col_t[j] = t; lp.col_idx[j] = l;
+        }
+        if (hs) for (int b = 0; b < B; b++) {
+            int j = S_(t, b); lp.c[j] = P->voll; lp.l[j] = 0; lp.u[j] = P->load[(int64_t)t * B + b];
+            lp.col_kind[j] = COL_S; lp.col_t[j] = t; lp.col_idx[j] = b;
+        }
+    }
+    // adjacency: units and lines per bus, in index order
+    std::vector<std::vector<int>> gens(B);
+    std::vector<std::vector<std::pair<int, double>>> lines(B);
+    for (int g = 0; g < G; g++) gens[P->gen_bus[g]].push_back(g);
+    for (int l = 0; l < L; l++) {
+        lines[P->line_from[l]].push_back({l, -1.0});
+        lines[P->line_to[l]].push_back({l, 1.0});
+    }
+    for (auto &v : lines) std::sort(v.begin(), v.end());
+
+    Csr &A = lp.A;
+    A.cols = (int)n;
+    A.rowptr.push_back(0);
+    std::vector<std::pair<int32_t, double>> row;
+    auto emit = [&](double rhs, int8_t kind, int t, int idx) {
+        std::sort(row.begin(), row.end());
+        for (auto &e : row)
+            if (e.second != 0.0) { A.colidx.push_back(e.first); A.val.push_back(e.second); }
+        A.rowptr.push_back((int32_t)A.colidx.size());
+        lp.q.push_back(rhs); lp.row_kind.push_back(kind); lp.row_t.push_back(t); lp.row_idx.push_back(idx);
+        row.clear();
+    };
+    for (int t = 0; t < T; t++) {
+        for (int b = 0; b < B; b++) {
+            for (int g : gens[b]) row.push_back({P_(t, g), 1.0});
+            for (auto &e : lines[b]) row.push_back({F_(t, e.first), e.second});
+            if (hs) row.push_back({S_(t, b), 1.0});
+            emit(P->load[(int64_t)t * B + b], ROW_BAL, t, b);
+        }
+        for (int l = 0; l < L; l++) {
+            double ix = 1.0 / P->x_pu[l];
+            row.push_back({F_(t, l), 1.0});
+            row.push_back({TH(t, P->line_from[l]), -ix});
+            row.push_back({TH(t, P->line_to[l]), ix});
+            emit(0.0, ROW_FLOW, t, l);
+        }
+    }
+    lp.m_eq = (int)lp.q.size();
+    for (int t = 0; t < T; t++) {
+        for (int g = 0; g < G; g++) {
+            row.push_back({P_(t, g), -1.0}); row.push_back({U_(t, g), P->pmax[g]});
+            emit(0.0, ROW_GUP, t, g);
+        }
+        for (int g = 0; g < G; g++) {
+            row.push_back({P_(t, g), 1.0}); row.push_back({U_(t, g), -P->pmin[g]});
+            emit(0.0, ROW_GLO, t, g);
+        }
+        for (int g = 0; g < G; g++) {
+            row.push_back({U_(t, g), -1.0}); row.push_back({V_(t, g), 1.0});
+            if (t == 0) emit(-P->u0[g], ROW_SU, t, g);
+            else { row.push_back({U_(t - 1, g), 1.0}); emit(0.0, ROW_SU, t, g); }
+        }
+        if (t >= 1) {
+            for (int g = 0; g < G; g++) {
+                row.push_back({P_(t - 1, g), 1.0}); row.push_back({P_(t, g), -1.0});
+                emit(-P->ramp[g], ROW_RUP, t, g);
+            }
+            for (int g = 0; g < G; g++) {
+                row.push_back({P_(t - 1, g), -1.0}); row.push_back({P_(t, g), 1.0});
+                emit(-P->ramp[g], ROW_RDN, t, g);
+            }
+        }
+    }
+    A.rows = (int)lp.q.size();
+    return UC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Presolve
+// ---------------------------------------------------------------------------
+static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<double> &qr,
+                           std::vector<double> &cr, std::vector<double> &lr, std::vector<double> &ur) {
+    const Csr &A = raw.A;
+    const int n = A.cols, m = A.rows;
+    Csr AT = transpose(A);
+    std::vector<double> l = raw.l, u = raw.u, q = raw.q;
+    std::vector<char> col_on(n, 1), row_on(m, 1);
+    ps.xfix.assign(n, 0.0);
+    double obj_const = 0.0;
+    const double tol = 1e-9;
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int j = 0; j < n; j++) {                        // fixed columns
+            if (!col_on[j] || l[j] != u[j]) continue;
+            double v = l[j];
+            for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1]; k++)
+                if (row_on[AT.colidx[k]]) q[AT.colidx[k]] -= AT.val[k] * v;
+            obj_const += raw.c[j] * v;
+            ps.xfix[j] = v;
+            col_on[j] = 0;
+            changed = true;
+        }
+        for (int i = 0; i < m; i++) {                        // empty / singleton rows
+            if (!row_on[i]) continue;
+            int cnt = 0, jj = -1;
+            double aa = 0.0;
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
+                if (col_on[A.colidx[k]]) { cnt++; jj = A.colidx[k]; aa = A.val[k]; }
+            bool eq = i < raw.m_eq;
+            if (cnt == 0) {
+                if ((eq && std::fabs(q[i]) > tol) || (!eq && q[i] > tol)) {
+                    set_error("presolve: row %d has no columns but rhs %g", i, q[i]);
+                    return UC_EINFEASIBLE;
+                }
+                row_on[i] = 0;
+                ps.removed.push_back({i, -1, 0.0, eq, false});
+                changed = true;
+            } else if (cnt == 1) {
+                double bnd = q[i] / aa;
+                bool tight = false;
+                if (eq) {
+                    if (bnd < l[jj] - tol || bnd > u[jj] + tol) {
+                        set_error("presolve: singleton equality row %d outside the bounds of column %d", i, jj);
+                        return UC_EINFEASIBLE;
+                    }
+                    l[jj] = bnd; u[jj] = bnd; tight = true;
+                } else if (aa > 0) {
+                    if (bnd > l[jj]) { l[jj] = bnd; tight = true; }
+                } else {
+                    if (bnd < u[jj]) { u[jj] = bnd; tight = true; }
+                }
+                if (l[jj] > u[jj] + tol) { set_error("presolve: bounds of column %d cross", jj); return UC_EINFEASIBLE; }
+                if (l[jj] > u[jj]) u[jj] = l[jj];
+                row_on[i] = 0;
+                ps.removed.push_back({i, jj, aa, eq, tight});
+                changed = true;
+            }
+        }
+        for (int j = 0; j < n; j++) {                        // empty columns
+            if (!col_on[j]) continue;
+            bool used = false;
+            for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1] && !used; k++) used = row_on[AT.colidx[k]];
+            if (used) continue;
+            double cj = raw.c[j], v;
+            if (cj > 0) v = l[j];
+            else if (cj < 0) v = u[j];
+            else v = std::isfinite(l[j]) ? l[j] : (std::isfinite(u[j]) ? u[j] : 0.0);
+            if (!std::isfinite(v)) { set_error("presolve: column %d is unbounded", j); return UC_EUNBOUNDED; }
+            obj_const += cj * v;
+            ps.xfix[j] = v;
+            col_on[j] = 0;
+            changed = true;
+        }
+    }
+    std::vector<int32_t> newcol(n, -1);
+    for (int j = 0; j < n; j++)
+        if (col_on[j]) { newcol[j] = (int32_t)ps.col_map.size(); ps.col_map.push_back(j); }
+    for (int i = 0; i < m; i++)
+        if (row_on[i]) ps.row_map.push_back(i);
+    Ared.rows = (int)ps.row_map.size();
+    Ared.cols = (int)ps.col_map.size();
+    Ared.rowptr.assign(1, 0);
+    for (int32_t i : ps.row_map) {
+        for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
+            if (col_on[A.colidx[k]]) { Ared.colidx.push_back(newcol[A.colidx[k]]); Ared.val.push_back(A.val[k]); }
+        Ared.rowptr.push_back((int32_t)Ared.colidx.size());
+        qr.push_back(q[i]);
+    }
+    ps.m_eq = 0;
+    for (int32_t i : ps.row_map) ps.m_eq += (i < raw.m_eq);
+    for (int32_t j : ps.col_map) { cr.push_back(raw.c[j]); lr.push_back(l[j]); ur.push_back(u[j]); }
+    ps.l_tight = l;
+    ps.u_tight = u;
+    ps.obj_const = obj_const;
+    return UC_OK;
+}
+
+// one equilibration pass: divide rows by rf, columns by cf
+static void apply_scaling(Csr &A, const std::vector<double> &rf, const std::vector<double> &cf,
+                          std::vector<double> &Dr, std::vector<double> &Dc, int threads) {
+    parallel_for(A.rows, threads, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++)
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
+                A.val[k] = A.val[k] / rf[i] / cf[A.colidx[k]];
+    });
+    for (int i = 0; i < A.rows; i++) Dr[i] /= rf[i];
+    for (int j = 0; j < A.cols; j++) Dc[j] /= cf[j];
+}
+
+static void scale_lp(PsData &ps, const uc_presolve_opts &o, int threads) {
+    Csr &A = ps.A;
+    const int m = A.rows, n = A.cols;
+    ps.Dr.assign(m, 1.0);
+    ps.Dc.assign(n, 1.0);
+    std::vector<double> rf(m), cf(n);
+    for (int it = 0; it < o.ruiz_iters; it++) {           // Ruiz: sqrt of row / column max
+        std::fill(rf.begin(), rf.end(), 0.0);
+        std::fill(cf.begin(), cf.end(), 0.0);
+        for (int i = 0; i < m; i++)
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                double a = std::fabs(A.val[k]);
+                rf[i] = std::max(rf[i], a);
+                cf[A.colidx[k]] = std::max(cf[A.colidx[k]], a);
+            }
+        for (auto &v : rf) v = v > 0 ? std::sqrt(v) : 1.0;
+        for (auto &v : cf) v = v > 0 ? std::sqrt(v) : 1.0;
+        apply_scaling(A, rf, cf, ps.Dr, ps.Dc, threads);
+    }
+    if (o.pock_chambolle) {                                // Pock-Chambolle, alpha = 1
+        std::fill(rf.begin(), rf.end(), 0.0);
+        std::fill(cf.begin(), cf.end(), 0.0);
+        for (int i = 0; i < m; i++)
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                double a = std::fabs(A.val[k]);
+                rf[i] += a;
+                cf[A.colidx[k]] += a;
+            }
+        for (auto &v : rf) v = v > 0 ? std::sqrt(v) : 1.0;
+        for (auto &v : cf) v = v > 0 ? std::sqrt(v) : 1.0;
+        apply_scaling(A, rf, cf, ps.Dr, ps.Dc, threads);
+    }
+    for (int i = 0; i < m; i++) ps.q[i] *= ps.Dr[i];
+    for (int j = 0; j < n; j++) {
+        ps.c[j] *= ps.Dc[j];
+        ps.l[j] /= ps.Dc[j];
+        ps.u[j] /= ps.Dc[j];
+    }
+}
+
+// ||A||_2 by power iteration on A^T A from the unit vector 1/sqrt(n)
+static double power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, int threads) {
+    const int n = A.cols;
+    if (n == 0 || A.rows == 0) return 0.0;
+    std::vector<double> v(n, 1.0 / std::sqrt((double)n)), t, w;
+    double lam = 0.0, prev = 0.0;
+    for (int it = 0; it < max_iter; it++) {
+        spmv(A, v, t, threads);
+        spmv(AT, t, w, threads);
+        lam = std::sqrt(sumsq(w, threads));
+        if (lam == 0.0) return 0.0;
+        for (int j = 0; j < n; j++) v[j] = w[j] / lam;
+        if (std::fabs(lam - prev) <= tol * lam) break;
+        prev = lam;
+    }
+    return std::sqrt(lam);
+}
+
+void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
+               std::vector<double> &y) {
+    const RawLp &raw = *ps.raw;
+    x = ps.xfix;
+    for (size_t k = 0; k < ps.col_map.size(); k++) x[ps.col_map[k]] = ps.Dc[k] * xs[k];
+    y.assign(raw.A.rows, 0.0);
+    if (!ys) return;
+    for (size_t k = 0; k < ps.row_map.size(); k++) y[ps.row_map[k]] = ps.Dr[k] * ys[k];
+    bool any = false;
+    for (auto &r : ps.removed) any |= (r.col >= 0 && r.tightened);
+    if (!any) return;
+    Csr AT = transpose(raw.A);
+    auto redcost = [&](int j) {
+        double s = raw.c[j];
+        for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1]; k++) s -= AT.val[k] * y[AT.colidx[k]];
+        return s;
+    };
+    for (auto it = ps.removed.rbegin(); it != ps.removed.rend(); ++it) {
+        if (it->col < 0 || !it->tightened) continue;
+        int j = it->col;
+        double lam = redcost(j);
+        if (it->eq) {
+            y[it->row] = lam / it->a;
+        } else {
+            double bnd = it->a > 0 ? ps.l_tight[j] : ps.u_tight[j];
+            bool at = std::fabs(x[j] - bnd) <= 1e-9 * (1.0 + std::fabs(x[j]));
+            if (at && lam / it->a > 0) y[it->row] = lam / it->a;
+        }
+    }
+}
+
+}  // namespace uc
+
+using namespace uc;
+
+// ---------------------------------------------------------------------------
+// C ABI (host part)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *uc_last_error(void) { return g_err.c_str(); }
+
+void uc_default_presolve_opts(uc_presolve_opts *o) {
+    if (!o) return;
+    o->ruiz_iters = 10;
+    o->pock_chambolle = 1;
+    o->power_max_iter = 500;
+    o->power_tol = 1e-10;
+    o->value_bits = 64;
+    o->threads = 0;
+}
+
+void uc_default_solve_opts(uc_solve_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->tol_rel_kkt = 1e-4;
+    o->tol_abs_feas = 1e-5;
+    o->max_iter = 100000;
+    o->n_eval = 64;
+    o->use_graph = 1;
+}
+
+int uc_build_lp(const uc_problem *prob, uc_lp **out) {
+    if (!out) { set_error("uc_build_lp: null out"); return UC_EINVAL; }
+    *out = nullptr;
+    int rc = validate(prob);
+    if (rc) return rc;
+    try {
+        auto lp = std::make_shared<RawLp>();
+        rc = build(prob, *lp);
+        if (rc) return rc;
+        *out = new uc_lp{lp};
+    } catch (const std::bad_alloc &) {
+        set_error("uc_build_lp: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
+int uc_lp_dims(const uc_lp *lp, int *n, int *m, int *m_eq, int64_t *nnz) {
+    if (!lp) { set_error("uc_lp_dims: null lp"); return UC_EINVAL; }
+    if (n) *n = lp->d->A.cols;
+    if (m) *m = lp->d->A.rows;
+    if (m_eq) *m_eq = lp->d->m_eq;
+    if (nnz) *nnz = lp->d->A.nnz();
+    return UC_OK;
+}
+
+int uc_lp_export(const uc_lp *lp, int32_t *rowptr, int32_t *colidx, double *val, double *q,
+                 double *c, double *l, double *u) {
+    if (!lp) { set_error("uc_lp_export: null lp"); return UC_EINVAL; }
+    const RawLp &r = *lp->d;
+    if (rowptr) std::memcpy(rowptr, r.A.rowptr.data(), r.A.rowptr.size() * 4);
+    if (colidx) std::memcpy(colidx, r.A.colidx.data(), r.A.colidx.size() * 4);
+    if (val) std::memcpy(val, r.A.val.data(), r.A.val.size() * 8);
+    if (q) std::memcpy(q, r.q.data(), r.q.size() * 8);
+    if (c) std::memcpy(c, r.c.data(), r.c.size() * 8);
+    if (l) std::memcpy(l, r.l.data(), r.l.size() * 8);
+    if (u) std::memcpy(u, r.u.data(), r.u.size() * 8);
+    return UC_OK;
+}
+
+int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **out) {
+    if (!lp || !out) { set_error("uc_presolve: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    uc_presolve_opts o;
+    uc_default_presolve_opts(&o);
+    if (opts) o = *opts;
+    if (o.value_bits != 64 && o.value_bits != 32) { set_error("uc_presolve: value_bits must be 32 or 64"); return UC_EINVAL; }
+    if (o.ruiz_iters < 0 || o.power_max_iter < 1) { set_error("uc_presolve: bad iteration counts"); return UC_EINVAL; }
+    int threads = o.threads > 0 ? o.threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    try {
+        auto ps = std::make_shared<PsData>();
+        ps->raw = lp->d;
+        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u);
+        if (rc) return rc;
+        double qi = 0.0, ci = 0.0;
+        for (double v : ps->q) qi = std::max(qi, std::fabs(v));
+        for (double v : ps->c) ci = std::max(ci, std::fabs(v));
+        ps->q_inf = qi;
+        ps->c_inf = ci;
+        scale_lp(*ps, o, threads);
+        ps->AT = transpose(ps->A);
+        ps->norm_A = power_norm(ps->A, ps->AT, o.power_max_iter, o.power_tol, threads);
+        ps->eta = ps->norm_A > 0 ? 0.998 / ps->norm_A : 1.0;
+        double cn = std::sqrt(sumsq(ps->c, threads)), qn = std::sqrt(sumsq(ps->q, threads));
+        ps->omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
+        ps->value_bits = o.value_bits;
+        if (o.value_bits == 32) {
+            ps->A_val32.assign(ps->A.val.begin(), ps->A.val.end());
+            ps->AT_val32.assign(ps->AT.val.begin(), ps->AT.val.end());
+        }
+        *out = new uc_presolved{ps};
+    } catch (const std::bad_alloc &) {
+        set_error("uc_presolve: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
+int uc_presolved_dims(const uc_presolved *ps, int *n, int *m, int *m_eq, int64_t *nnz) {
+    if (!ps) { set_error("uc_presolved_dims: null handle"); return UC_EINVAL; }
+    if (n) *n = ps->d->n();
+    if (m) *m = ps->d->m();
+    if (m_eq) *m_eq = ps->d->m_eq;
+    if (nnz) *nnz = ps->d->A.nnz();
+    return UC_OK;
+}
+
+int uc_presolved_export(const uc_presolved *h, int32_t *rowptr, int32_t *colidx, double *val,
+                        double *q, double *c, double *l, double *u, double *Dr, double *Dc,
+                        int32_t *col_map, int32_t *row_map, double *scalars) {
+    if (!h) { set_error("uc_presolved_export: null handle"); return UC_EINVAL; }
+    const PsData &p = *h->d;
+    if (rowptr) std::memcpy(rowptr, p.A.rowptr.data(), p.A.rowptr.size() * 4);
+    if (colidx) std::memcpy(colidx, p.A.colidx.data(), p.A.colidx.size() * 4);
+    if (val) std::memcpy(val, p.A.val.data(), p.A.val.size() * 8);
+    if (q) std::memcpy(q, p.q.data(), p.q.size() * 8);
+    if (c) std::memcpy(c, p.c.data(), p.c.size() * 8);
+    if (l) std::memcpy(l, p.l.data(), p.l.size() * 8);
+    if (u) std::memcpy(u, p.u.data(), p.u.size() * 8);
+    if (Dr) std::memcpy(Dr, p.Dr.data(), p.Dr.size() * 8);
+    if (Dc) std::memcpy(Dc, p.Dc.data(), p.Dc.size() * 8);
+    if (col_map) std::memcpy(col_map, p.col_map.data(), p.col_map.size() * 4);
+    if (row_map) std::memcpy(row_map, p.row_map.data(), p.row_map.size() * 4);
+    if (scalars) {
+        scalars[0] = p.eta; scalars[1] = p.omega0; scalars[2] = p.norm_A;
+        scalars[3] = p.obj_const; scalars[4] = p.q_inf; scalars[5] = p.c_inf;
+    }
+    return UC_OK;
+}
+
+int uc_get_raw_solution(const uc_result *res, double *x, double *y) {
+    if (!res) { set_error("uc_get_raw_solution: null result"); return UC_EINVAL; }
+    std::vector<double> xr, yr;
+    postsolve(*res->ps, res->x_ret.data(), res->y_ret.data(), xr, yr);
+    if (x) std::memcpy(x, xr.data(), xr.size() * 8);
+    if (y) std::memcpy(y, yr.data(), yr.size() * 8);
+    return UC_OK;
+}
+
+int uc_get_solution(const uc_result *res, double *p, double *u, double *v, double *theta,
+                    double *f, double *shed, double *lmp, uc_stats *stats) {
+    if (!res) { set_error("uc_get_solution: null result"); return UC_EINVAL; }
+    const RawLp &raw = *res->ps->raw;
+    std::vector<double> xr, yr;
+    postsolve(*res->ps, res->x_ret.data(), res->y_ret.data(), xr, yr);
+    const int G = raw.G, B = raw.B, L = raw.L;
+    if (shed) std::memset(shed, 0, sizeof(double) * (size_t)raw.T * B);
+    for (size_t j = 0; j < xr.size(); j++) {
+        int64_t t = raw.col_t[j], k = raw.col_idx[j];
+        switch (raw.col_kind[j]) {
+            case COL_P: if (p) p[t * G + k] = xr[j]; break;
+            case COL_U: if (u) u[t * G + k] = xr[j]; break;
+            case COL_V: if (v) v[t * G + k] = xr[j]; break;
+            case COL_TH: if (theta) theta[t * B + k] = xr[j]; break;
+            case COL_F: if (f) f[t * L + k] = xr[j]; break;
+            case COL_S: if (shed) shed[t * B + k] = xr[j]; break;
+        }
+    }
+    if (lmp)
+        for (size_t i = 0; i < yr.size(); i++)
+            if (raw.row_kind[i] == ROW_BAL) lmp[(int64_t)raw.row_t[i] * B + raw.row_idx[i]] = yr[i];
+    if (stats) {
+        *stats = res->stats;
+        double obj = 0.0;
+        for (size_t j = 0; j < xr.size(); j++) obj += raw.c[j] * xr[j];
+        stats->objective = obj;
+    }
+    return UC_OK;
+}
+
+int uc_get_iterate(const uc_result *res, int which, double *x, double *y) {
+    if (!res) { set_error("uc_get_iterate: null result"); return UC_EINVAL; }
+    const std::vector<double> *xs, *ys;
+    switch (which) {
+        case 0: xs = &res->x_cur; ys = &res->y_cur; break;
+        case 1: xs = &res->x_avg; ys = &res->y_avg; break;
+        case 2: xs = &res->x_ret; ys = &res->y_ret; break;
+        default: set_error("uc_get_iterate: which must be 0, 1 or 2"); return UC_EINVAL;
+    }
+    if (x) std::memcpy(x, xs->data(), xs->size() * 8);
+    if (y) std::memcpy(y, ys->data(), ys->size() * 8);
+    return UC_OK;
+}
+
+void uc_free_lp(uc_lp *lp) { delete lp; }
+void uc_free_presolved(uc_presolved *ps) { delete ps; }
+void uc_free_result(uc_result *res) { delete res; }
+
+}  // extern "C"

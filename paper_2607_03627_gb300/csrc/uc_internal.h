@@ -1,0 +1,89 @@
+// Internal types shared by the host (presolve) and device (PDHG) translation units.
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "uc_pdhg.h"
+
+namespace uc {
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Compressed sparse rows, int32 indices (every matrix here has < 2^31 entries).
+struct Csr {
+    int rows = 0, cols = 0;
+    std::vector<int32_t> rowptr;   // rows + 1
+    std::vector<int32_t> colidx;   // nnz, ascending within a row
+    std::vector<double> val;       // nnz
+    int64_t nnz() const { return (int64_t)colidx.size(); }
+};
+
+Csr transpose(const Csr &A);
+
+enum ColKind : int8_t { COL_P = 0, COL_U, COL_V, COL_TH, COL_F, COL_S };
+enum RowKind : int8_t { ROW_BAL = 0, ROW_FLOW, ROW_GUP, ROW_GLO, ROW_SU, ROW_RUP, ROW_RDN };
+
+struct RawLp {
+    int B = 0, L = 0, G = 0, T = 0, nc = 0;
+    bool has_shed = false;
+    Csr A;
+    int m_eq = 0;
+    std::vector<double> q, c, l, u;
+    std::vector<int8_t> col_kind, row_kind;
+    std::vector<int32_t> col_t, col_idx, row_t, row_idx;
+};
+
+struct RemovedRow {
+    int row;          // raw row
+    int col;          // raw column of a singleton row, -1 for an empty row
+    double a;         // its coefficient
+    bool eq;
+    bool tightened;   // the row moved a bound
+};
+
+// Everything the device solve and the postsolve need.
+struct PsData {
+    std::shared_ptr<const RawLp> raw;
+    // reduced, scaled LP: A_s = diag(Dr) A diag(Dc)
+    Csr A;            // m x n, FP64 scaled values
+    Csr AT;           // n x m
+    std::vector<float> A_val32, AT_val32;  // FP32 copies when value_bits == 32
+    int m_eq = 0;
+    std::vector<double> q, c, l, u;        // scaled
+    std::vector<double> Dr, Dc;
+    std::vector<int32_t> col_map, row_map; // reduced -> raw
+    std::vector<double> xfix;              // raw n: value of fixed columns
+    std::vector<double> l_tight, u_tight;  // raw n: bounds after presolve
+    std::vector<RemovedRow> removed;
+    double eta = 1.0, omega0 = 1.0, norm_A = 0.0, obj_const = 0.0;
+    double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
+    int value_bits = 64;
+    int n() const { return A.cols; }
+    int m() const { return A.rows; }
+};
+
+// Host-side postsolve: scaled presolved (x_s, y_s) -> raw (x, y).
+void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
+               std::vector<double> &y);
+
+}  // namespace uc
+
+struct uc_lp {
+    std::shared_ptr<uc::RawLp> d;
+};
+
+struct uc_presolved {
+    std::shared_ptr<uc::PsData> d;
+};
+
+struct uc_result {
+    std::shared_ptr<const uc::PsData> ps;
+    std::vector<double> x_ret, y_ret;   // returned point (scaled presolved)
+    std::vector<double> x_cur, y_cur;   // current iterate
+    std::vector<double> x_avg, y_avg;   // average since the last restart
+    uc_stats stats{};
+};

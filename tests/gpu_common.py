@@ -1,0 +1,54 @@
+"""Shared helpers of the GPU parity tests (not collected by pytest)."""
+import json
+import os
+
+import numpy as np
+
+from oracle import kkt, lp as olp, pdhg, presolve as ops
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# Per-iterate agreement of the FP64 device path with the FP64 oracle PDHG:
+# both run the same arithmetic and differ only in summation order and FMA
+# contraction (about 1e-16 relative per step); PDHG steps are non-expansive,
+# so 1e-9 relative over the first few hundred iterations leaves a wide margin.
+ITERATE_RTOL = 1e-9
+KKT_TOL = 1e-4          # relative KKT (infinity norm), the paper's convergence tolerance
+OBJ_GAP_TOL = 1e-4      # |obj - obj_simplex| / max(1, |obj_simplex|)
+
+
+def golden_tiny():
+    with open(os.path.join(GOLDEN, "tiny_lp.json")) as f:
+        return json.load(f)
+
+
+def oracle_pipeline(P):
+    raw = olp.build_lp(P)
+    ps = ops.presolve(raw)
+    S = ops.scale(ps.lp)
+    return raw, ps, S
+
+
+def oracle_trace(S, ks, n_eval=pdhg.N_EVAL):
+    """Oracle current iterates after each step count in ks (tol 0: never stops)."""
+    out = {}
+    def rec(k, st):
+        out[k] = (st.x.copy(), st.y.copy(), st.restarts, st.omega)
+    pdhg.solve(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, trace=rec, trace_iters=ks)
+    return out
+
+
+def rel_inf(a, b):
+    d = np.max(np.abs(a - b), initial=0.0)
+    r = np.max(np.abs(b), initial=0.0)
+    return d / r if r > 0 else d
+
+
+def oracle_kkt_of_raw(ps, xr, yr):
+    """Relative KKT, as the oracle computes it, of a raw-LP point mapped to the
+    oracle's presolved LP."""
+    return kkt.relative_kkt(ps.lp, xr[ps.col_map], yr[ps.row_map])
+
+
+def raw_objective(raw, xr):
+    return float(raw.c @ xr)

@@ -1,0 +1,157 @@
+"""GPU parity of the device PDHG (through the C ABI) against the CPU oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import ucgen
+from gpu_common import (ITERATE_RTOL, KKT_TOL, OBJ_GAP_TOL, golden_tiny, oracle_kkt_of_raw,
+                        oracle_pipeline, oracle_trace, raw_objective, rel_inf)
+from oracle import lp as olp, pdhg, simplex
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding
+    return binding
+
+
+def _device_iterates(B, ps, n, m, K, **kw):
+    res, rc = B.uc_solve(ps, tol=0.0, max_iter=K, **kw)
+    assert rc == B.UC_EITERLIMIT
+    x, y = B.uc_get_iterate(res, 0, n, m)
+    st = B.uc_get_stats(res)
+    return x, y, st
+
+
+KS = [1, 2, 3, 17, 63, 64, 65, 127, 128, 129, 191, 192, 193, 200]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("which", ["tiny", "small_ragged"])
+def test_per_iterate_parity_first_200(B, which, use_graph):
+    if which == "tiny":
+        P = ucgen.tiny(0)
+    else:  # sizes far from the 256-row tiles, zero-Pmin units
+        P = ucgen.make_problem(7, B=37, L=53, G=11, T=5, lo=0.5, hi=0.9, noise=0.05, zero_pmin_frac=0.2)
+    raw, ps_o, S = oracle_pipeline(P)
+    ref = oracle_trace(S, KS)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    for K in KS:
+        x, y, st = _device_iterates(B, ps, n, m, K, use_graph=use_graph)
+        xo, yo, restarts, omega = ref[K]
+        assert st["iters"] == K
+        assert st["restarts"] == restarts, f"restart decision differs at K={K}"
+        assert rel_inf(x, xo) <= ITERATE_RTOL, (K, rel_inf(x, xo))
+        assert rel_inf(y, yo) <= ITERATE_RTOL, (K, rel_inf(y, yo))
+        assert st["omega"] == pytest.approx(omega, rel=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_solve_meets_gates(B, seed):
+    g = golden_tiny()
+    P = ucgen.tiny(seed)
+    raw, ps_o, S = oracle_pipeline(P)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    res, rc = B.uc_solve(ps, tol=KKT_TOL)
+    assert rc == B.UC_OK
+    st = B.uc_get_stats(res)
+    xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+    assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+    opt = g["objective_by_seed"][str(seed)]
+    assert abs(raw_objective(raw, xr) - opt) / max(1.0, abs(opt)) <= OBJ_GAP_TOL
+    assert st["objective"] == pytest.approx(raw_objective(raw, xr), rel=1e-12)
+    # the oracle PDHG takes the same path to the same stop
+    r = pdhg.solve(S, tol=KKT_TOL)
+    assert r.iters == st["iters"] and r.restarts == st["restarts"]
+    # power balance of the returned dispatch, per period (satisfied to the tolerance)
+    sol = B.uc_get_solution(res, P.T, P.B, P.L, P.G)
+    bal = sol["p"].sum(axis=1) + sol["shed"].sum(axis=1) - P.load.sum(axis=1)
+    assert np.max(np.abs(bal)) <= 1e-3 * P.load.sum(axis=1).max()
+
+
+def test_fp32_values_meet_gates_and_report_error(B):
+    g = golden_tiny()
+    P = ucgen.tiny(0)
+    raw, ps_o, S = oracle_pipeline(P)
+    lp = B.uc_build_lp(P)
+    r64, _ = B.uc_solve(B.uc_presolve(lp), tol=KKT_TOL)
+    r32, rc = B.uc_solve(B.uc_presolve(lp, value_bits=32), tol=KKT_TOL)
+    assert rc == B.UC_OK
+    xr, yr = B.uc_get_raw_solution(r32, raw.n, raw.m)
+    assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= 1.1 * KKT_TOL    # FP64 LP, FP32-stored matrix
+    assert abs(raw_objective(raw, xr) - g["objective"]) / g["objective"] <= OBJ_GAP_TOL
+    x64, _ = B.uc_get_raw_solution(r64, raw.n, raw.m)
+    # error of the FP32-value path against the FP64 path at the same tolerance
+    err = abs(raw_objective(raw, xr) - raw_objective(raw, x64)) / g["objective"]
+    assert err <= 2 * OBJ_GAP_TOL
+
+
+def test_batch_equals_single_solves(B):
+    Ps = [ucgen.tiny(s) for s in range(3)] + [ucgen.micro(5, B=9, L=12, G=3, T=4)]
+    pss = [B.uc_presolve(B.uc_build_lp(P)) for P in Ps]
+    singles = [B.uc_solve(p, tol=KKT_TOL)[0] for p in pss]
+    batch, rc = B.uc_solve_batch(pss, tol=KKT_TOL)
+    assert rc == B.UC_OK
+    for p, s, b in zip(pss, singles, batch):
+        n, m, _, _ = B.uc_presolved_dims(p)
+        xs, ys = B.uc_get_iterate(s, 2, n, m)
+        xb, yb = B.uc_get_iterate(b, 2, n, m)
+        np.testing.assert_array_equal(xb, xs)       # same arithmetic, same order
+        np.testing.assert_array_equal(yb, ys)
+        assert B.uc_get_stats(b)["iters"] == B.uc_get_stats(s)["iters"]
+
+
+def test_edge_cases(B):
+    P = ucgen.tiny(1)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    # max_iter 0: the starting point comes back unchanged
+    res, rc = B.uc_solve(ps, tol=KKT_TOL, max_iter=0)
+    assert rc == B.UC_EITERLIMIT
+    x, y = B.uc_get_iterate(res, 0, n, m)
+    d = B.uc_presolved_export(ps)
+    np.testing.assert_array_equal(x, np.clip(0.0, d["l"], d["u"]))
+    assert not y.any()
+    # warm start from a converged point stops at the first evaluation
+    res, rc = B.uc_solve(ps, tol=KKT_TOL)
+    x, y = B.uc_get_iterate(res, 2, n, m)
+    res2, rc2 = B.uc_solve(ps, tol=KKT_TOL * 1.5, warm_x=x, warm_y=y)
+    assert rc2 == B.UC_OK and B.uc_get_stats(res2)["iters"] == 64
+    # cancellation: a set flag stops the solve at the first replay boundary
+    flag = ctypes.c_int(1)
+    res3, rc3 = B.uc_solve(ps, tol=1e-12, cancel=flag)
+    assert rc3 == B.UC_ECANCELLED
+    assert B.uc_get_stats(res3)["iters"] <= 2 * 64
+    # no units: only shed, flows and angles
+    Q = ucgen.micro(3, B=4, L=5, G=1, T=2)
+    Q.G = 0
+    for f in ("gen_bus", "pmax", "pmin", "ramp", "c_lin", "c_nl", "c_su", "u0"):
+        setattr(Q, f, getattr(Q, f)[:0])
+    raw, ps_o, _ = oracle_pipeline(Q)
+    psq = B.uc_presolve(B.uc_build_lp(Q))
+    res, rc = B.uc_solve(psq, tol=KKT_TOL)
+    assert rc == B.UC_OK
+    xr, _ = B.uc_get_raw_solution(res, raw.n, raw.m)
+    ref = simplex.solve_lp(raw)
+    assert abs(raw_objective(raw, xr) - ref.obj) / ref.obj <= OBJ_GAP_TOL
+
+
+@pytest.mark.parametrize("n_eval", [2, 16, 128])
+def test_other_evaluation_periods(B, n_eval):
+    P = ucgen.micro(1, B=10, L=14, G=4, T=6)
+    raw, ps_o, S = oracle_pipeline(P)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    K = 3 * n_eval + 1
+    ref = oracle_trace(S, [K], n_eval=n_eval)
+    x, y, st = _device_iterates(B, ps, n, m, K, n_eval=n_eval)
+    assert rel_inf(x, ref[K][0]) <= ITERATE_RTOL and rel_inf(y, ref[K][1]) <= ITERATE_RTOL

@@ -1,0 +1,113 @@
+"""Host side of the C ABI on CPU: the library loads, exports every symbol the
+header declares, and its LP builder / presolve / scaling agree with the
+oracle's independently written ones."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import ucgen
+from oracle import lp as olp, presolve as ops
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding
+    return binding
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "uc_pdhg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(uc_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_library_exports_every_declared_symbol(B):
+    lib = ctypes.CDLL(B.LIB_PATH)
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _problems():
+    yield ucgen.tiny(0)
+    yield ucgen.make_problem(3, B=25, L=40, G=9, T=7, lo=0.4, hi=0.9, noise=0.05, zero_pmin_frac=0.3)
+    P = ucgen.micro(2, B=5, L=6, G=3, T=3)
+    P.voll = 0.0                                   # strict balance: no shed columns
+    yield P
+
+
+@pytest.mark.parametrize("P", list(_problems()), ids=lambda P: P.name or "strict")
+def test_builder_matches_oracle_exactly(B, P):
+    ref = olp.build_lp(P)
+    d = B.uc_lp_export(B.uc_build_lp(P))
+    assert (d["n"], d["m"], d["m_eq"]) == (ref.n, ref.m, ref.m_eq)
+    np.testing.assert_array_equal(d["rowptr"], ref.A.indptr)
+    np.testing.assert_array_equal(d["colidx"], ref.A.indices)
+    np.testing.assert_array_equal(d["val"], ref.A.data)
+    for k in ("q", "c", "l", "u"):
+        np.testing.assert_array_equal(d[k], getattr(ref, k))
+
+
+@pytest.mark.parametrize("P", list(_problems()), ids=lambda P: P.name or "strict")
+def test_presolve_and_scaling_match_oracle(B, P):
+    ps_o = ops.presolve(olp.build_lp(P))
+    S = ops.scale(ps_o.lp)
+    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P)))
+    assert (d["n"], d["m"], d["m_eq"]) == (ps_o.lp.n, ps_o.lp.m, ps_o.lp.m_eq)
+    np.testing.assert_array_equal(d["col_map"], ps_o.col_map)
+    np.testing.assert_array_equal(d["row_map"], ps_o.row_map)
+    np.testing.assert_array_equal(d["rowptr"], S.A.indptr)
+    np.testing.assert_array_equal(d["colidx"], S.A.indices)
+    np.testing.assert_allclose(d["val"], S.A.data, rtol=1e-13)
+    for k, ref in (("q", S.q), ("c", S.c), ("Dr", S.Dr), ("Dc", S.Dc)):
+        np.testing.assert_allclose(d[k], ref, rtol=1e-13, err_msg=k)
+    for k, ref in (("l", S.l), ("u", S.u)):
+        fin = np.isfinite(ref)
+        np.testing.assert_array_equal(np.isfinite(d[k]), fin)
+        np.testing.assert_allclose(d[k][fin], ref[fin], rtol=1e-13, err_msg=k)
+    assert d["eta"] == pytest.approx(S.eta, rel=1e-11)
+    assert d["omega0"] == pytest.approx(S.omega0, rel=1e-12)
+    assert d["obj_const"] == pytest.approx(ps_o.lp.obj_const, rel=1e-14, abs=1e-9)
+    assert d["q_inf"] == S.q_inf_unscaled and d["c_inf"] == S.c_inf_unscaled
+
+
+def test_builder_rejects_bad_data(B):
+    P = ucgen.micro(0, B=3, L=3, G=2, T=2)
+    bad = P.copy(); bad.line_to = bad.line_from.copy()
+    with pytest.raises(B.UCError, match="self loop"):
+        B.uc_build_lp(bad)
+    bad = P.copy(); bad.x_pu[0] = 0.0
+    with pytest.raises(B.UCError, match="reactance"):
+        B.uc_build_lp(bad)
+    bad = P.copy(); bad.pmin[0] = bad.pmax[0] + 1
+    with pytest.raises(B.UCError, match="pmin"):
+        B.uc_build_lp(bad)
+    bad = P.copy(); bad.load[0, 0] = -1.0
+    with pytest.raises(B.UCError, match="load"):
+        B.uc_build_lp(bad)
+    bad = P.copy(); bad.gen_bus[0] = 99
+    with pytest.raises(B.UCError, match="out of range"):
+        B.uc_build_lp(bad)
+
+
+def test_presolve_reports_infeasible(B):
+    # strict balance with more load than generation and line capacity can serve
+    P = ucgen.micro(0, B=2, L=1, G=1, T=1)
+    P.voll = 0.0
+    P.load[:] = 0.0
+    P.gen_bus[:] = 0
+    P.pmax[:] = 0.0
+    P.pmin[:] = 0.0
+    P.load[0, 0] = 5.0                          # bus 0: only p (fixed 0) and f
+    P.fmax[:] = 0.0                             # f fixed at 0 -> balance row empty with rhs 5
+    with pytest.raises(B.UCError, match="infeasible"):
+        B.uc_presolve(B.uc_build_lp(P))
