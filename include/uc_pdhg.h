@@ -220,6 +220,48 @@ int uc_get_raw_solution(const uc_result *res, double *x, double *y);
  * last restart, 2 returned point; x [n], y [m]. */
 int uc_get_iterate(const uc_result *res, int which, double *x, double *y);
 
+/* Device view of a presolved, scaled LP as uc_presolved_export returns it,
+ * copied by the caller into device memory (every pointer is device memory):
+ * A (m x n) and A^T (n x m) in CSR with FP64 values, the scaled c, l, u
+ * (+-inf allowed) and column scales D_c [n], the scaled q and row scales
+ * D_r [m]; rows [0, m_eq) are equalities, the rest ">="; q_inf and c_inf are
+ * the unscaled infinity norms (scalars[4], scalars[5] of the export). */
+typedef struct {
+    int n, m, m_eq;
+    const int32_t *A_rowptr, *A_colidx;
+    const double *A_val;
+    const int32_t *AT_rowptr, *AT_colidx;
+    const double *AT_val;
+    const double *c, *l, *u, *Dc;
+    const double *q, *Dr;
+    double q_inf, c_inf;
+} uc_device_lp;
+
+/* Relative KKT of a scaled presolved point (x [n], y [m], device memory) --
+ * the same quantities the solver's own evaluation reports -- computed
+ * WITHOUT ANY DEVICE ALLOCATION.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory, e.g. code being
+ * recorded into a CUDA graph under global stream capture, or a process whose
+ * device memory is all reserved ahead of time by its own pool allocator.
+ * Results go to `out`, 8 doubles of caller-owned device memory:
+ * {rel_primal, rel_dual, rel_gap, KKT_omega (with the given omega > 0),
+ *  primal objective, dual objective (both of the scaled presolved LP, no
+ *  presolve constant), max |unscaled primal residual|, 0}.
+ * Work is queued on `stream` (a cudaStream_t; NULL = legacy default) and the
+ * call returns without waiting for it.
+ * Scratch: a fixed array of 8192 x 8 doubles (512 KiB) in the library's
+ * device image, held by every GPU that loads the library until exit.  LPs
+ * with ceil(m/1024) + ceil(n/1024) > 8192 (about 8.4 million rows + columns)
+ * are rejected with UC_EINVAL.  All calls share that array, so calls whose
+ * device work overlaps (several streams or host threads at once) race and
+ * must be serialised by the caller; no part of it needs to start at zero.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before starting any stream capture.  No cudaMalloc, cudaFree or other
+ * allocating call is made. */
+int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, double omega, double *out,
+                   void *stream);
+
 void uc_free_lp(uc_lp *lp);
 void uc_free_presolved(uc_presolved *ps);
 void uc_free_result(uc_result *res);

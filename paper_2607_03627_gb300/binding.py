@@ -51,6 +51,14 @@ class uc_solve_opts(C.Structure):
                 ("spmv_rows_per_block", C.c_int), ("cancel", _P(C.c_int))]
 
 
+class uc_device_lp(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("m_eq", C.c_int),
+                ("A_rowptr", C.c_void_p), ("A_colidx", C.c_void_p), ("A_val", C.c_void_p),
+                ("AT_rowptr", C.c_void_p), ("AT_colidx", C.c_void_p), ("AT_val", C.c_void_p),
+                ("c", C.c_void_p), ("l", C.c_void_p), ("u", C.c_void_p), ("Dc", C.c_void_p),
+                ("q", C.c_void_p), ("Dr", C.c_void_p), ("q_inf", C.c_double), ("c_inf", C.c_double)]
+
+
 class uc_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("restarts", C.c_int), ("evals", C.c_int),
                 ("returned_average", C.c_int), ("rel_primal", C.c_double), ("rel_dual", C.c_double),
@@ -89,6 +97,8 @@ _SIGS = {
     "uc_session_update_lp": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "uc_session_device_bytes": (C.c_size_t, [C.c_void_p]),
     "uc_session_free": (None, [C.c_void_p]),
+    "uc_kkt_noalloc": (C.c_int, [_P(uc_device_lp), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                 C.c_void_p]),
     "uc_free_lp": (None, [C.c_void_p]),
     "uc_free_presolved": (None, [C.c_void_p]),
     "uc_free_result": (None, [C.c_void_p]),
@@ -414,3 +424,12 @@ class Session:
             self.close()
         except Exception:
             pass
+
+
+def uc_kkt_noalloc(dev_lp: uc_device_lp, x_ptr: int, y_ptr: int, omega: float, out_ptr: int,
+                   stream: int | None = None) -> int:
+    """Relative KKT of a device-resident point with no device allocation
+    (see include/uc_pdhg.h); all pointers are device addresses.  Returns the
+    status code; the 8 results land in `out_ptr` on `stream`."""
+    return lib.uc_kkt_noalloc(C.byref(dev_lp), C.c_void_p(x_ptr), C.c_void_p(y_ptr), float(omega),
+                              C.c_void_p(out_ptr), C.c_void_p(stream or 0))

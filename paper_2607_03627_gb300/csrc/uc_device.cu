@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <vector>
 
 #include "uc_internal.h"
@@ -916,6 +917,131 @@ static int session_set_start(uc_session &X, int i, const double *x, const double
 
 static int max_replays(const uc_session &X) { return X.o.max_iter / X.o.n_eval + 1; }
 
+// ---------------------------------------------------------------------------
+// KKT evaluation that allocates nothing (uc_kkt_noalloc)
+//
+// Some callers may not allocate device memory at all: code recorded into a
+// CUDA graph under global stream capture (where cudaMalloc is illegal), and
+// processes whose device memory is fully reserved up front by another pool
+// allocator, where a fresh driver allocation would fail or fragment the pool.
+// For them this variant of the evaluation keeps its per-CTA partial sums in
+// the file-scope array below instead of session memory.  Every GPU that loads
+// this library holds the array (kNoAllocMaxBlocks * kNoAllocSlots doubles,
+// 512 KiB) until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocSlots = 8;         // Slot entries RP2 .. BND (DY2 stays 0)
+constexpr int kNoAllocMaxBlocks = 8192;  // CTAs of 1024 rows or columns: n/1024 + m/1024 <= 8192
+
+static __device__ __align__(256) double g_kkt_scratch[kNoAllocMaxBlocks * kNoAllocSlots];
+
+// per-device address of g_kkt_scratch, looked up once per device
+static std::mutex g_kkt_scratch_mu;
+static void *g_kkt_scratch_ptr[128];
+
+static int kkt_scratch_address(double **out) {
+    int dev = 0;
+    UC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) { set_error("device ordinal %d unsupported", dev); return UC_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_kkt_scratch_mu);
+    if (!g_kkt_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(scratch) failed on device %d: %s", dev, cudaGetErrorString(e));
+            return UC_ECUDA;
+        }
+        g_kkt_scratch_ptr[dev] = p;
+    }
+    *out = (double *)g_kkt_scratch_ptr[dev];
+    return UC_OK;
+}
+
+// CTA b < nbr: rows [1024 b, ...); else columns.  Same per-thread order and
+// block reduction as k_eval, current point only.
+__global__ void __launch_bounds__(kThreads) k_kkt_partials_noalloc(uc_device_lp lp, int nbr, const double *__restrict__ x,
+                                                                   const double *__restrict__ y, double *__restrict__ scratch) {
+    double acc[kPart];
+#pragma unroll
+    for (int s = 0; s < kPart; s++) acc[s] = 0.0;
+    const bool rows = (int)blockIdx.x < nbr;
+    if (rows) {
+        const int b0 = blockIdx.x * kEvalRows, b1 = min(lp.m, b0 + kEvalRows);
+        for (int i = b0 + threadIdx.x; i < b1; i += kThreads) {
+            double ax = 0.0;
+            for (int k = lp.A_rowptr[i]; k < lp.A_rowptr[i + 1]; k++) ax += lp.A_val[k] * x[lp.A_colidx[k]];
+            const double qi = lp.q[i];
+            double r = ax - qi;
+            if (i >= lp.m_eq) r = fmin(r, 0.0);
+            acc[RP2] += r * r;
+            acc[RPU] = fmax(acc[RPU], fabs(r) / lp.Dr[i]);
+            acc[QY] += qi * y[i];
+        }
+    } else {
+        const int b0 = (blockIdx.x - nbr) * kEvalRows, b1 = min(lp.n, b0 + kEvalRows);
+        for (int j = b0 + threadIdx.x; j < b1; j += kThreads) {
+            double t = 0.0;
+            for (int k = lp.AT_rowptr[j]; k < lp.AT_rowptr[j + 1]; k++) t += lp.AT_val[k] * y[lp.AT_colidx[k]];
+            const double cj = lp.c[j], lj = lp.l[j], uj = lp.u[j];
+            const bool lf = isfinite(lj), uf = isfinite(uj);
+            const double lm = cj - t;
+            const double lpj = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
+            const double rd = lm - lpj;
+            double bnd = 0.0;
+            if (lf) bnd += lj * fmax(lpj, 0.0);
+            if (uf) bnd += uj * fmin(lpj, 0.0);
+            acc[RD2] += rd * rd;
+            acc[RDU] = fmax(acc[RDU], fabs(rd) / lp.Dc[j]);
+            acc[CX] += cj * x[j];
+            acc[BND] += bnd;
+        }
+    }
+    // every CTA overwrites its own record, so nothing in the scratch needs clearing
+    __shared__ double rec[kPart];
+    block_reduce_store(acc, rec);
+    __syncthreads();
+    if (threadIdx.x < kNoAllocSlots) scratch[(size_t)blockIdx.x * kNoAllocSlots + threadIdx.x] = rec[threadIdx.x];
+}
+
+// one CTA: fixed-order reduction of the partials (same order as k_control)
+__global__ void __launch_bounds__(kThreads) k_kkt_finish_noalloc(int nblocks, const double *__restrict__ scratch,
+                                                                 double q_inf, double c_inf, double omega,
+                                                                 double *__restrict__ out) {
+    __shared__ double red[kThreads][kNoAllocSlots];
+    double acc[kNoAllocSlots];
+#pragma unroll
+    for (int s = 0; s < kNoAllocSlots; s++) acc[s] = 0.0;
+    for (int blk = threadIdx.x; blk < nblocks; blk += kThreads) {
+#pragma unroll
+        for (int s = 0; s < kNoAllocSlots; s++) {
+            const double v = scratch[(size_t)blk * kNoAllocSlots + s];
+            acc[s] = (s == RPU || s == RDU) ? fmax(acc[s], v) : acc[s] + v;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kNoAllocSlots; s++) red[threadIdx.x][s] = acc[s];
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int s = 0; s < kNoAllocSlots; s++) {
+                const double a = red[threadIdx.x][s], c = red[threadIdx.x + h][s];
+                red[threadIdx.x][s] = (s == RPU || s == RDU) ? fmax(a, c) : a + c;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double *T = red[0];
+    const double pobj = T[CX], dobj = T[QY] + T[BND], gap = pobj - dobj;
+    out[0] = T[RPU] / (1.0 + q_inf);
+    out[1] = T[RDU] / (1.0 + c_inf);
+    out[2] = fabs(gap) / (1.0 + fabs(pobj) + fabs(dobj));
+    out[3] = kkt_w(T[RP2], T[RD2], gap, omega);
+    out[4] = pobj;
+    out[5] = dobj;
+    out[6] = T[RPU];
+    out[7] = 0.0;
+}
+
+
 }  // namespace dev
 }  // namespace uc
 
@@ -985,6 +1111,31 @@ int uc_session_update_lp(uc_session *s, int i, const uc_presolved *ps) {
 }
 
 size_t uc_session_device_bytes(const uc_session *s) { return s ? s->bytes : 0; }
+
+int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, double omega, double *out,
+                   void *stream) {
+    if (!lp || !x || !y || !out) { set_error("uc_kkt_noalloc: null argument"); return UC_EINVAL; }
+    if (lp->n < 0 || lp->m < 0 || lp->m_eq < 0 || lp->m_eq > lp->m || !(omega > 0.0)) {
+        set_error("uc_kkt_noalloc: need n, m >= 0, 0 <= m_eq <= m and omega > 0");
+        return UC_EINVAL;
+    }
+    const int nbr = (lp->m + dev::kEvalRows - 1) / dev::kEvalRows;
+    const int nbc = (lp->n + dev::kEvalRows - 1) / dev::kEvalRows;
+    const int nblocks = nbr + nbc;
+    if (nblocks > dev::kNoAllocMaxBlocks) {
+        set_error("uc_kkt_noalloc: LP too large for the fixed scratch: ceil(m/1024) + ceil(n/1024) = %d > %d "
+                  "(n + m up to about 8.4 million)", nblocks, dev::kNoAllocMaxBlocks);
+        return UC_EINVAL;
+    }
+    double *scratch = nullptr;
+    int rc = dev::kkt_scratch_address(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nblocks > 0) dev::k_kkt_partials_noalloc<<<nblocks, dev::kThreads, 0, s>>>(*lp, nbr, x, y, scratch);
+    dev::k_kkt_finish_noalloc<<<1, dev::kThreads, 0, s>>>(nblocks, scratch, lp->q_inf, lp->c_inf, omega, out);
+    UC_CUDA(cudaGetLastError());
+    return UC_OK;
+}
 
 void uc_session_free(uc_session *s) { delete s; }
 
