@@ -118,11 +118,30 @@ def _dist():
     return world, rank, local
 
 
-def bytes_per_iter(n, m, nnz, vs):
-    """Algorithmic bytes of the fused primal (A^T y) and dual (A x-bar) kernels."""
-    primal = nnz * (vs + 4) + 4 * (n + 1) + 8 * m + 56 * n
-    dual = nnz * (vs + 4) + 4 * (m + 1) + 16 * n + 40 * m
-    return primal, dual
+def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
+    """Algorithmic bytes of the primal (A^T y) and dual (A x-bar) kernels: the
+    matrix and its row pointers once, every vector element touched once.
+    Halpern: primal reads x, c, l, u, x0, gathers y, writes x-bar and x;
+    dual gathers x-bar, reads y, q, y0, writes y.  Averaging: primal reads x,
+    c, l, u, sum and writes x+, sum; dual gathers x+ and x, reads y, q, sum,
+    writes y+, sum."""
+    mat = nnz * (vs + 4)
+    if algorithm == "halpern":
+        return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 8 * n + 32 * m
+    return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 16 * n + 40 * m
+
+
+# FP64 instructions the device issues per row (FP64 FMA/add/mul each count 1;
+# selections, clipping and FP32 widening run on the integer pipe).
+def fp64_inst_per_iter(n, m, nnz, algorithm="halpern"):
+    if algorithm == "halpern":
+        return nnz + 5 * n, nnz + 5 * m
+    return nnz + 3 * n, 2 * nnz + 3 * m
+
+
+# GPU-wide FP64 pipe issue rate: 2 thread-instructions per SM per clock
+# (sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 on 152 SMs)
+FP64_INST_PER_CLK = 304
 
 
 def make_workload(name, rank):
@@ -160,7 +179,8 @@ def run_ours(args):
     presolve_s = time.perf_counter() - t0
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
-    sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True)
+    sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True, spmv_kernel=args.spmv_kernel,
+                     algorithm=args.algorithm, restart_metric=args.restart_metric)
 
     def solve_once():
         sess.reset(-1)
@@ -206,14 +226,40 @@ def run_ours(args):
     n_timed = st["timed_launches"] - nt0
     tp = (st["primal_kernel_ms"] * st["timed_launches"] - tp0) / max(n_timed, 1)
     td = (st["dual_kernel_ms"] * st["timed_launches"] - td0) / max(n_timed, 1)
-    bp, bd = bytes_per_iter(n, m, nnz, vs)
+    bp, bd = bytes_per_iter(n, m, nnz, vs, args.algorithm)
+    fp, fd = fp64_inst_per_iter(n, m, nnz, args.algorithm)
     peak, peak_kind = _peaks()
-    dom = ("k_primal", bp, tp) if tp * 1 >= td else ("k_dual", bd, td)
-    achieved = dom[1] / (dom[2] / 1e3) / 1e9 if dom[2] > 0 else 0.0
+    clk_sum = clk.summary()
+    sm_mhz = clk_sum.get("sm_mhz") or 2070.0
+    fp64_peak = FP64_INST_PER_CLK * sm_mhz * 1e6 / 1e9      # G FP64 instructions / s
+    kern = {}
+    for name, b_, f_, t_ in (("k_primal", bp, fp, tp), ("k_dual", bd, fd, td)):
+        if t_ <= 0:
+            continue
+        gbs = b_ / (t_ / 1e3) / 1e9
+        gis = f_ / (t_ / 1e3) / 1e9
+        kern[name] = {"mean_launch_us": t_ * 1e3, "algorithmic_bytes_per_launch": b_,
+                      "fp64_inst_per_launch": f_,
+                      "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
+                      "alu_fp64": {"achieved": gis, "peak": fp64_peak, "unit": "G FP64 inst/s",
+                                   "frac": gis / fp64_peak}}
+    dom = max(kern, key=lambda k: kern[k]["mean_launch_us"]) if kern else "k_primal"
+    dk = kern.get(dom, {"hbm": {"frac": 0, "achieved": 0, "peak": peak, "unit": "GB/s"},
+                        "alu_fp64": {"frac": 0, "achieved": 0, "peak": fp64_peak, "unit": ""},
+                        "mean_launch_us": 0, "algorithmic_bytes_per_launch": 0})
+    bound = "alu" if dk["alu_fp64"]["frac"] >= dk["hbm"]["frac"] else "hbm"
+    main = dk["alu_fp64"] if bound == "alu" else dk["hbm"]
     traffic = None
-    rec = NCU_TRAFFIC.get((args.config, dom[0]))
+    rec = NCU_TRAFFIC.get((args.config, args.algorithm, dom))
     if rec and rec["src"] == _src_hash():
         traffic = rec["bytes"]
+    roofline = {"bound": bound, "kernel": dom, "achieved": main["achieved"], "peak": main["peak"],
+                "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
+                "peak_kind": (peak_kind if bound == "hbm" else
+                              "derived: 304 FP64 thread-instructions/clock x median SM clock"),
+                "other_bound": ({"bound": "hbm", **dk["hbm"]} if bound == "alu"
+                                else {"bound": "alu", **dk["alu_fp64"]}),
+                "timed_launches": n_timed, "kernels": kern}
     per_iter_ms = ms_max / max(total_iters / world, 1)
     alg_gbs = (bp + bd) / (per_iter_ms / 1e3) / 1e9
 
@@ -229,7 +275,8 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             lp2 = B.uc_build_lp(P)
             ps2 = B.uc_presolve(lp2, value_bits=vbits)
-            r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter)
+            r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter, algorithm=args.algorithm,
+                                 restart_metric=args.restart_metric)
             sol = B.uc_get_solution(r2, P.T, P.B, P.L, P.G)
             tot_it += sol["stats"]["iters"]
             h2d += sol["stats"]["h2d_bytes"]
@@ -258,6 +305,7 @@ def run_ours(args):
             "data": "synthetic (seeded generator standing in for the GO3 6,049-bus cases)",
             "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
                            tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
+                           algorithm=args.algorithm, restart_metric=args.restart_metric,
                            l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
                            parallelism=f"replicas x{world}"),
             "time_to_1e-4_ms": ms_max / args.steps,
@@ -267,14 +315,8 @@ def run_ours(args):
             "pdhg_iters_per_s_per_gpu": total_iters / world / (ms_max / 1e3),
             "algorithmic_GBps": alg_gbs, "bytes_per_iter": bp + bd,
             "presolve_s": presolve_s,
-            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "algorithmic_bytes_per_launch": dom[1],
-                         "mean_launch_us": dom[2] * 1e3, "timed_launches": n_timed,
-                         "other_kernel": {"name": "k_dual" if dom[0] == "k_primal" else "k_primal",
-                                          "mean_launch_us": (td if dom[0] == "k_primal" else tp) * 1e3,
-                                          "algorithmic_bytes_per_launch": bd if dom[0] == "k_primal" else bp}},
-            "clocks": clk.summary(),
+            "roofline": roofline,
+            "clocks": clk_sum,
             "gpu_launches": st["kernel_launches"] - launches0,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -293,14 +335,14 @@ def cpu_baseline(P, iters):
     raw = olp.build_lp(P)
     ps = ops.presolve(raw)
     S = ops.scale(ps.lp)
-    st = pdhg.initial_state(S)
+    st = pdhg.halpern_initial_state(S)
     AT = S.A.T.tocsr()
     U = pdhg._unscaled_lp(S)
     t0 = time.perf_counter()
     for _ in range(iters):
-        pdhg.step(S, st, AT)
+        pdhg.halpern_step(S, st, AT)
         if st.k % pdhg.N_EVAL == 0:
-            pdhg.evaluate(S, st, U, TOL)
+            pdhg.halpern_evaluate(S, st, U, TOL)
     dt = time.perf_counter() - t0
     return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{iters} PDHG iterations (with {iters // 64} KKT/restart evaluations) of the oracle "
@@ -320,14 +362,14 @@ def run_reference(args):
     raw = olp.build_lp(P)
     ps = ops.presolve(raw)
     S = ops.scale(ps.lp)
-    st = pdhg.initial_state(S)
+    st = pdhg.halpern_initial_state(S)
     AT = S.A.T.tocsr()
     U = pdhg._unscaled_lp(S)
 
     def block():
         for _ in range(pdhg.N_EVAL):
-            pdhg.step(S, st, AT)
-        pdhg.evaluate(S, st, U, TOL)
+            pdhg.halpern_step(S, st, AT)
+        pdhg.halpern_evaluate(S, st, U, TOL)
 
     for _ in range(args.warmup):
         block()
@@ -360,6 +402,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmv-kernel", type=int, default=0, help="0 default, 1 thread per row")
+    ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
+    ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -101,7 +101,12 @@ typedef struct {
     uc_alloc_fn alloc;           /* nullable device allocator */
     uc_free_fn free;
     void *alloc_ctx;
-    int spmv_rows_per_block;     /* 0: automatic (tuned); else threads per CTA for the row kernels */
+    int spmv_kernel;             /* iteration kernels: 0 default (warp tile), 1 one thread per row,
+                                    2 warp tile (a warp owns 32 rows, coalesced 16-byte loads) */
+    int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
+                                    averaging with KKT restarts (both constant-step, see DESIGN) */
+    int restart_metric;          /* Halpern restarts: 0 (default) weighted KKT of the map output,
+                                    1 fixed-point residual of the last step */
     const volatile int *cancel;  /* nullable; a nonzero value (set from another thread) stops the
                                     solve at its next replay boundary with UC_ECANCELLED -- the
                                     "terminate the other solver" step of Alg. 1 */
@@ -216,8 +221,9 @@ int uc_get_solution(const uc_result *res, double *p, double *u, double *v, doubl
                     double *f, double *shed, double *lmp, uc_stats *stats);
 /* Raw-LP primal [raw n] and dual [raw m] of the returned point. */
 int uc_get_raw_solution(const uc_result *res, double *x, double *y);
-/* Presolved-space, SCALED iterates: which = 0 current, 1 average since the
- * last restart, 2 returned point; x [n], y [m]. */
+/* Presolved-space, SCALED iterates: which = 0 current iterate, 1 the average
+ * since the last restart (averaging variant) or the restart anchor (Halpern
+ * variant), 2 returned point (Halpern: the last PDHG map output); x [n], y [m]. */
 int uc_get_iterate(const uc_result *res, int which, double *x, double *y);
 
 /* Device view of a presolved, scaled LP as uc_presolved_export returns it,

@@ -25,6 +25,22 @@ but does not state the method.  This follows the published PDLP scheme
           (x, y) = anchor = candidate; KKT_anchor = KKT_omega(candidate) with
           the new omega; sums and j reset; tau, sigma recomputed.
 All arithmetic is on the scaled problem except the stopping test.
+
+A second variant, the default, is restarted reflected Halpern PDHG (Lu &
+Yang, "Restarted Halpern PDHG for linear programming", 2024), again with a
+constant step.  With T the PDHG map above and z = (x, y):
+
+  step:   z_hat = T(z)  (x_hat, y_hat as x+, y+ above, from the current z)
+          z <- w (2 z_hat - z) + (1 - w) z0,   w = (j+1)/(j+2)
+          (full reflection; z0 = anchor of the current restart epoch)
+  every n_eval steps: relative KKT of z_hat (the last map output) -> stop;
+          restart metric r = KKT_omega(z_hat) ("kkt") or the fixed-point
+          residual sqrt(omega ||x_in - x_hat||^2 + ||y_in - y_hat||^2 / omega)
+          of the last step ("fpr"); the same three restart tests with r in
+          place of KKT_c and r_anchor in place of KKT_anchor;
+          on restart: omega from dx = ||x_hat - x0||, dy = ||y_hat - y0||,
+          z = z0 = z_hat, j = 0, r_anchor = r re-weighted with the new omega.
+The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr".
 """
 from __future__ import annotations
 
@@ -195,3 +211,112 @@ def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
     rel = kkt.relative_kkt(U, S.Dc * st.x, S.Dr * st.y)
     return Result(x=st.x.copy(), y=st.y.copy(), iters=st.k, status="iteration_limit",
                   rel=rel, restarts=st.restarts, omega=st.omega, state=st, which="current")
+
+
+# ---------------------------------------------------------------------------
+# restarted reflected Halpern PDHG (default variant)
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class HState:
+    x: np.ndarray            # current Halpern iterate
+    y: np.ndarray
+    x0: np.ndarray           # epoch anchor
+    y0: np.ndarray
+    xh: np.ndarray           # last map output T(z)
+    yh: np.ndarray
+    x_in: np.ndarray         # input of the last step
+    y_in: np.ndarray
+    omega: float
+    tau: float
+    sigma: float
+    r_anchor: float
+    r_prev: float
+    j: int
+    k: int
+    metric: str
+    restarts: int = 0
+
+
+def halpern_initial_state(S, x0=None, y0=None, metric: str = "kkt") -> HState:
+    x = np.clip(np.zeros(S.A.shape[1]) if x0 is None else x0.copy(), S.l, S.u)
+    y = np.zeros(S.A.shape[0]) if y0 is None else y0.copy()
+    y[S.m_eq:] = np.maximum(y[S.m_eq:], 0.0)
+    omega = S.omega0
+    if metric == "kkt":
+        ra, _ = weighted(S, x, y, omega)
+    else:
+        ra = math.inf
+    return HState(x=x, y=y, x0=x.copy(), y0=y.copy(), xh=x.copy(), yh=y.copy(), x_in=x.copy(),
+                  y_in=y.copy(), omega=omega, tau=S.eta / omega, sigma=S.eta * omega, r_anchor=ra,
+                  r_prev=math.inf, j=0, k=0, metric=metric)
+
+
+def halpern_step(S, st: HState, AT=None):
+    AT = S.A.T.tocsr() if AT is None else AT
+    xh = np.clip(st.x - st.tau * (S.c - AT @ st.y), S.l, S.u)
+    xbar = 2.0 * xh - st.x
+    yh = st.y + st.sigma * (S.q - S.A @ xbar)
+    yh[S.m_eq:] = np.maximum(yh[S.m_eq:], 0.0)
+    w = (st.j + 1) / (st.j + 2)
+    x_new = w * xbar + (1.0 - w) * st.x0
+    y_new = w * (2.0 * yh - st.y) + (1.0 - w) * st.y0
+    st.x_in, st.y_in = st.x, st.y
+    st.xh, st.yh = xh, yh
+    st.x, st.y = x_new, y_new
+    st.j += 1
+    st.k += 1
+
+
+def halpern_evaluate(S, st: HState, U, tol: float):
+    """Evaluation after an n_eval block: (done, point, rel); applies a restart."""
+    rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)
+    if max(rel) <= tol:
+        return True, (st.xh.copy(), st.yh.copy()), rel
+    w = st.omega
+    fx2 = float(np.dot(st.x_in - st.xh, st.x_in - st.xh))
+    fy2 = float(np.dot(st.y_in - st.yh, st.y_in - st.yh))
+    if st.metric == "kkt":
+        r, parts = weighted(S, st.xh, st.yh, w)
+    else:
+        r = math.sqrt(w * fx2 + fy2 / w)
+    if restart_decision(r, st.r_anchor, st.r_prev, st.j, st.k):
+        dx = float(np.linalg.norm(st.xh - st.x0))
+        dy = float(np.linalg.norm(st.yh - st.y0))
+        st.omega = primal_weight_update(w, dx, dy)
+        wn = st.omega
+        st.x = st.xh.copy()
+        st.y = st.yh.copy()
+        st.x0 = st.x.copy()
+        st.y0 = st.y.copy()
+        st.r_anchor = (kkt.weighted_kkt(parts[0], parts[1], parts[2], wn) if st.metric == "kkt"
+                       else math.sqrt(wn * fx2 + fy2 / wn))
+        st.r_prev = math.inf
+        st.j = 0
+        st.tau = S.eta / wn
+        st.sigma = S.eta * wn
+        st.restarts += 1
+    else:
+        st.r_prev = r
+    return False, None, rel
+
+
+def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
+                  x0=None, y0=None, metric: str = "kkt", trace=None, trace_iters=()) -> Result:
+    """Run the Halpern variant; ``trace(k, state)`` after every step k in trace_iters
+    (after the evaluation when k is a multiple of n_eval)."""
+    st = halpern_initial_state(S, x0, y0, metric)
+    AT = S.A.T.tocsr()
+    U = _unscaled_lp(S)
+    trace_iters = set(trace_iters)
+    while st.k < max_iter:
+        halpern_step(S, st, AT)
+        if st.k % n_eval == 0:
+            done, pt, rel = halpern_evaluate(S, st, U, tol)
+            if done:
+                return Result(x=pt[0], y=pt[1], iters=st.k, status="optimal", rel=rel,
+                              restarts=st.restarts, omega=st.omega, state=st, which="map")
+        if trace is not None and st.k in trace_iters:
+            trace(st.k, st)
+    rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)
+    return Result(x=st.xh.copy(), y=st.yh.copy(), iters=st.k, status="iteration_limit", rel=rel,
+                  restarts=st.restarts, omega=st.omega, state=st, which="map")

@@ -48,7 +48,8 @@ class uc_solve_opts(C.Structure):
                 ("n_eval", C.c_int), ("use_graph", C.c_int), ("kernel_timing", C.c_int),
                 ("timeout_ms", C.c_double), ("warm_x", _d), ("warm_y", _d),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("spmv_rows_per_block", C.c_int), ("cancel", _P(C.c_int))]
+                ("spmv_kernel", C.c_int), ("algorithm", C.c_int), ("restart_metric", C.c_int),
+                ("cancel", _P(C.c_int))]
 
 
 class uc_device_lp(C.Structure):
@@ -280,7 +281,8 @@ def _torch_stream_and_allocator():
 
 def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use_graph: bool = True,
                kernel_timing: bool = False, timeout_ms: float = 0.0, warm_x=None, warm_y=None,
-               cancel=None) -> tuple[uc_solve_opts, list]:
+               cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
+               restart_metric: str = "kkt") -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     o.tol_rel_kkt = tol
@@ -289,6 +291,9 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.use_graph = int(bool(use_graph))
     o.kernel_timing = int(bool(kernel_timing))
     o.timeout_ms = float(timeout_ms)
+    o.spmv_kernel = int(spmv_kernel)
+    o.algorithm = {"halpern": 0, "average": 1}[algorithm]
+    o.restart_metric = {"kkt": 0, "fpr": 1}[restart_metric]
     keep = []
     if warm_x is not None:
         wx = _f64(warm_x); keep.append(wx); o.warm_x = _ptr(wx, C.c_double)

@@ -46,6 +46,8 @@ constexpr int kPart = 2 * kSlots;  // per-block partial record (current, average
 enum Slot { RP2 = 0, RPU, QY, DY2, RD2, RDU, CX, BND, DX2 };
 enum Status { RUNNING = 0, OPTIMAL = 1, ITER_LIMIT = 2, NUMERIC = 3, NEEDS_INIT = 4 };
 enum Action { ACT_NONE = 0, ACT_RESTART = 1, ACT_FINISH = 2 };
+enum Algo { ALG_HALPERN = 0, ALG_AVERAGE = 1 };
+enum Metric { METRIC_KKT = 0, METRIC_FPR = 1 };
 
 // Per-LP solver state, resident in device memory and only changed by k_control.
 struct Scalars {
@@ -56,8 +58,12 @@ struct Scalars {
     int k_base, j_base, max_iter, n_eval;
     int status, which, action, cand;
     double inv_j;                                    // 1 / iterations averaged at the last evaluation
-    int restarts, evals, pad0, pad1;
+    int restarts, evals;
+    int algo;        // ALG_HALPERN or ALG_AVERAGE
+    int metric;      // Halpern restart metric: METRIC_KKT or METRIC_FPR
 };
+// kkt_anchor / kkt_prev hold the restart metric's anchor and previous value
+// for the Halpern variant as well.
 
 // One CTA's slice of rows (or columns) of one LP.
 struct Seg {
@@ -74,87 +80,182 @@ struct Bufs {
     const void *A_v, *AT_v;
     // constant vectors
     const double *c, *l, *u, *q, *Dr, *Dc;
+    const double *inv_Dr, *inv_Dc;             // 1 / D_r, 1 / D_c (evaluation only)
+    const long long *lkey, *ukey;              // order keys of l and u (see okey)
+    const double *W, *W1;                      // Halpern weights (j+1)/(j+2) and 1 - that, j < nW
+    int nW;
     // state: x, y double-buffered
     double *x[2], *y[2];
-    double *xsum, *ysum, *xa, *ya, *xret, *yret;
-    double *part;
+    double *xsum, *ysum, *xa, *ya, *xret, *yret;   // Halpern: xsum holds x-bar, xret/yret the map output
+    double *part;                              // per-CTA evaluation records
+    double *red;                               // [k][kPart] reduced evaluation records
     Scalars *S;
     int *status;       // [k] copy of each LP's status, read by the host after every replay
 };
 
 // ---------------------------------------------------------------------------
-// iteration kernels
+// FP64 is scarce on this GPU (2 FMA per SM and clock against 128 in FP32), so
+// the kernels spend FP64 instructions only on arithmetic whose rounding
+// matters and do selections on the integer pipe, bit-exactly:
+//   okey(v)   maps a double to an int64 with the same order (negative values
+//             get their magnitude bits flipped); okey is its own inverse, so
+//             a bound stored as its key is recovered with okey again;
+//   clipping  x to [l, u] compares keys and selects;
+//   y_I >= 0  tests the sign bit;
+//   FP32 matrix values widen to FP64 by moving exponent and mantissa bits
+//             (exact for the normal, nonzero values the presolve guarantees);
+//   maxima of non-negative doubles compare their bit patterns.
 // ---------------------------------------------------------------------------
-template <typename VT>
+__device__ __forceinline__ long long okey(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
+
+__device__ __forceinline__ double clip_keys(double v, long long lk, long long uk) {
+    const long long kv = okey(__double_as_longlong(v));
+    if (kv < lk) return __longlong_as_double(okey(lk));
+    if (kv > uk) return __longlong_as_double(okey(uk));
+    return v;
+}
+
+__device__ __forceinline__ double nonneg(double v) {
+    return (__double_as_longlong(v) < 0) ? 0.0 : v;
+}
+
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float f) {
+    const unsigned long long u = __float_as_uint(f);
+    const unsigned long long bits = ((u & 0x80000000ull) << 32) | (((u & 0x7fffffffull) << 29) + (896ull << 52));
+    return __longlong_as_double((long long)bits);
+}
+
+// max of two non-negative doubles through their bit patterns
+__device__ __forceinline__ double nnmax(double a, double b) {
+    return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+
+__device__ __forceinline__ void halpern_weights(const Bufs &b, const Scalars *S, int it, double &w, double &w1) {
+    const int jj = S->j_base + it;
+    if (jj < b.nW) {
+        w = b.W[jj];
+        w1 = b.W1[jj];
+    } else {
+        w = ((double)jj + 1.0) / ((double)jj + 2.0);
+        w1 = 1.0 - w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// iteration kernels (one thread per row of A^T or A)
+// ---------------------------------------------------------------------------
+// ALGO = ALG_AVERAGE: x+ = clip(x - tau (c - A^T y), l, u), running sum of x+.
+// ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
+// dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
+// the last step of a block (and at the iteration limit).
+template <typename VT, int ALGO>
 __global__ void __launch_bounds__(kThreads) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
-    if (S->status != RUNNING || S->k_base + it >= S->max_iter) return;
+    const int k = S->k_base + it;
+    if (S->status != RUNNING || k >= S->max_iter) return;
     const int j = sg.begin + threadIdx.x;
     if (j >= sg.end) return;
     const double tau = S->tau;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
+    const double xin = b.x[src][j];
+    const double cj = b.c[j];
+    const long long lk = b.lkey[j], uk = b.ukey[j];
+    const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : b.xa[j];
     double acc = 0.0;
     const int k1 = b.AT_rp[j + 1];
-    for (int k = b.AT_rp[j]; k < k1; k++) acc += (double)v[k] * y[b.AT_ci[k]];
-    double xv = b.x[src][j] - tau * (b.c[j] - acc);
-    xv = fmin(fmax(xv, b.l[j]), b.u[j]);
-    b.x[src ^ 1][j] = xv;
-    b.xsum[j] += xv;
+    for (int kk = b.AT_rp[j]; kk < k1; kk++) acc += widen(v[kk]) * y[b.AT_ci[kk]];
+    const double xv = clip_keys(xin - tau * (cj - acc), lk, uk);
+    if (ALGO == ALG_AVERAGE) {
+        b.x[src ^ 1][j] = xv;
+        b.xsum[j] = aux + xv;
+    } else {
+        double w, w1;
+        halpern_weights(b, S, it, w, w1);
+        const double xb = 2.0 * xv - xin;
+        b.xsum[j] = xb;
+        b.x[src ^ 1][j] = w * xb + w1 * aux;
+        if (it == S->n_eval - 1 || k == S->max_iter - 1) b.xret[j] = xv;
+    }
 }
 
-template <typename VT>
+// ALGO = ALG_AVERAGE: y+ = proj(y + sigma (q - A (2 x+ - x))), running sum.
+// ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
+// y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
+template <typename VT, int ALGO>
 __global__ void __launch_bounds__(kThreads) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
-    if (S->status != RUNNING || S->k_base + it >= S->max_iter) return;
+    const int k = S->k_base + it;
+    if (S->status != RUNNING || k >= S->max_iter) return;
     const int i = sg.begin + threadIdx.x;
     if (i >= sg.end) return;
     const double sigma = S->sigma;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
-    const double *__restrict__ xn = b.x[src ^ 1];
-    const double *__restrict__ xo = b.x[src];
+    const double yin = b.y[src][i];
+    const double qi = b.q[i];
+    const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : b.ya[i];
     double acc = 0.0;
     const int k1 = b.A_rp[i + 1];
-    for (int k = b.A_rp[i]; k < k1; k++) {
-        const int j = b.A_ci[k];
-        acc += (double)v[k] * (2.0 * xn[j] - xo[j]);
+    if (ALGO == ALG_AVERAGE) {
+        const double *__restrict__ xn = b.x[src ^ 1];
+        const double *__restrict__ xo = b.x[src];
+        for (int kk = b.A_rp[i]; kk < k1; kk++) {
+            const int j = b.A_ci[kk];
+            acc += widen(v[kk]) * (2.0 * xn[j] - xo[j]);
+        }
+    } else {
+        const double *__restrict__ xb = b.xsum;
+        for (int kk = b.A_rp[i]; kk < k1; kk++) acc += widen(v[kk]) * xb[b.A_ci[kk]];
     }
-    double yv = b.y[src][i] + sigma * (b.q[i] - acc);
-    if (i >= sg.aux) yv = fmax(yv, 0.0);
-    b.y[src ^ 1][i] = yv;
-    b.ysum[i] += yv;
+    double yv = yin + sigma * (qi - acc);
+    if (i >= sg.aux) yv = nonneg(yv);
+    if (ALGO == ALG_AVERAGE) {
+        b.y[src ^ 1][i] = yv;
+        b.ysum[i] = aux + yv;
+    } else {
+        double w, w1;
+        halpern_weights(b, S, it, w, w1);
+        b.y[src ^ 1][i] = w * (2.0 * yv - yin) + w1 * aux;
+        if (it == S->n_eval - 1 || k == S->max_iter - 1) b.yret[i] = yv;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // evaluation: per-CTA FP64 partials of both candidates (fixed reduction order)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool slot_is_max(int s) { return (s % kSlots) == RPU || (s % kSlots) == RDU; }
+
 __device__ __forceinline__ void block_reduce_store(double (&acc)[kPart], double *out) {
     __shared__ double sh[kThreads / 32][kPart];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < kPart; s++) {
         double v = acc[s];
-        const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             double w = __shfl_down_sync(0xffffffffu, v, o);
-            v = is_max ? fmax(v, w) : v + w;
+            v = slot_is_max(s) ? nnmax(v, w) : v + w;
         }
         if (lane == 0) sh[warp][s] = v;
     }
     __syncthreads();
     if (threadIdx.x < kPart) {
         const int s = threadIdx.x;
-        const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
         double v = sh[0][s];
-        for (int w = 1; w < kThreads / 32; w++) v = is_max ? fmax(v, sh[w][s]) : v + sh[w][s];
+        for (int w = 1; w < kThreads / 32; w++) v = slot_is_max(s) ? nnmax(v, sh[w][s]) : v + sh[w][s];
         out[s] = v;
     }
 }
 
-// mode 0: initial point (current only, no average); mode 1: regular evaluation
+// mode 0: the start point (candidate 0 only); mode 1: regular evaluation.
+// Average variant: candidate 0 = current point, candidate 1 = average since the
+// last restart.  Halpern variant: candidate 0 = the last map output
+// (x_hat, y_hat); the record of candidate 1 only carries the fixed-point
+// residual ||x_in - x_hat||^2 (slot DX2) and ||y_in - y_hat||^2 (slot DY2),
+// x_in / y_in being the input of the last step (buffer 1, n_eval even).
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs, Bufs b, int mode) {
     const Seg sg = segs[blockIdx.x];
@@ -165,8 +266,11 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
     const bool live = (mode == 0) ? (S->status == NEEDS_INIT)
                                   : (S->status == RUNNING && S->k_base + S->n_eval <= S->max_iter);
     if (live) {
-        const double inv_j = (mode == 0) ? 0.0 : 1.0 / (double)(S->j_base + S->n_eval);
-        const double *x = b.x[0], *y = b.y[0];
+        const bool halp = S->algo == ALG_HALPERN && mode == 1;
+        const bool avg = S->algo == ALG_AVERAGE && mode == 1;
+        const double inv_j = avg ? 1.0 / (double)(S->j_base + S->n_eval) : 0.0;
+        const double *x = halp ? b.xret : b.x[0];
+        const double *y = halp ? b.yret : b.y[0];
         const bool rows = (sg.aux & 1) == 0;
         const int eq_end = sg.aux >> 1;   // rows: first ">=" row
         if (rows) {
@@ -175,23 +279,31 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 double ax0 = 0.0, ax1 = 0.0;
                 for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
                     const int j = b.A_ci[k];
-                    const double a = (double)v[k];
+                    const double a = widen(v[k]);
                     ax0 += a * x[j];
-                    ax1 += a * (b.xsum[j] * inv_j);
+                    if (avg) ax1 += a * (b.xsum[j] * inv_j);
                 }
-                const double qi = b.q[i], dri = b.Dr[i], yh = b.ya[i];
+                const double qi = b.q[i], idr = b.inv_Dr[i], yh = b.ya[i];
                 const bool ineq = i >= eq_end;
-                double r0 = ax0 - qi, r1 = ax1 - qi;
-                if (ineq) { r0 = fmin(r0, 0.0); r1 = fmin(r1, 0.0); }
-                const double y0 = y[i], y1 = b.ysum[i] * inv_j;
+                double r0 = ax0 - qi;
+                if (ineq) r0 = fmin(r0, 0.0);
+                const double y0 = y[i];
                 acc[RP2] += r0 * r0;
-                acc[RPU] = fmax(acc[RPU], fabs(r0) / dri);
+                acc[RPU] = nnmax(acc[RPU], fabs(r0) * idr);
                 acc[QY] += qi * y0;
                 acc[DY2] += (y0 - yh) * (y0 - yh);
-                acc[kSlots + RP2] += r1 * r1;
-                acc[kSlots + RPU] = fmax(acc[kSlots + RPU], fabs(r1) / dri);
-                acc[kSlots + QY] += qi * y1;
-                acc[kSlots + DY2] += (y1 - yh) * (y1 - yh);
+                if (avg) {
+                    double r1 = ax1 - qi;
+                    if (ineq) r1 = fmin(r1, 0.0);
+                    const double y1 = b.ysum[i] * inv_j;
+                    acc[kSlots + RP2] += r1 * r1;
+                    acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fabs(r1) * idr);
+                    acc[kSlots + QY] += qi * y1;
+                    acc[kSlots + DY2] += (y1 - yh) * (y1 - yh);
+                } else if (halp) {
+                    const double d = b.y[1][i] - y0;
+                    acc[kSlots + DY2] += d * d;
+                }
             }
         } else {
             const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
@@ -199,17 +311,17 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 double t0 = 0.0, t1 = 0.0;
                 for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) {
                     const int i = b.AT_ci[k];
-                    const double a = (double)v[k];
+                    const double a = widen(v[k]);
                     t0 += a * y[i];
-                    t1 += a * (b.ysum[i] * inv_j);
+                    if (avg) t1 += a * (b.ysum[i] * inv_j);
                 }
-                const double cj = b.c[j], lj = b.l[j], uj = b.u[j], dcj = b.Dc[j], xh = b.xa[j];
+                const double cj = b.c[j], lj = b.l[j], uj = b.u[j], idc = b.inv_Dc[j], xh = b.xa[j];
                 const bool lf = isfinite(lj), uf = isfinite(uj);
-                const double x0 = x[j], x1 = b.xsum[j] * inv_j;
                 const double lam[2] = {cj - t0, cj - t1};
-                const double xs[2] = {x0, x1};
+                const double xs[2] = {x[j], avg ? b.xsum[j] * inv_j : 0.0};
 #pragma unroll
                 for (int cnd = 0; cnd < 2; cnd++) {
+                    if (cnd == 1 && !avg) break;
                     const double lm = lam[cnd];
                     const double lp = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
                     const double rd = lm - lp;
@@ -218,10 +330,14 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     if (uf) bnd += uj * fmin(lp, 0.0);
                     double *a = acc + cnd * kSlots;
                     a[RD2] += rd * rd;
-                    a[RDU] = fmax(a[RDU], fabs(rd) / dcj);
+                    a[RDU] = nnmax(a[RDU], fabs(rd) * idc);
                     a[CX] += cj * xs[cnd];
                     a[BND] += bnd;
                     a[DX2] += (xs[cnd] - xh) * (xs[cnd] - xh);
+                }
+                if (halp) {
+                    const double d = b.x[1][j] - x[j];
+                    acc[kSlots + DX2] += d * d;
                 }
             }
         }
@@ -230,52 +346,48 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
 }
 
 // ---------------------------------------------------------------------------
-// scalar controller: one CTA per LP
+// reduction of the evaluation records: one CTA per (LP, slot), fixed order
+// (FP64 adds spread over kPart CTAs per LP instead of one)
 // ---------------------------------------------------------------------------
 struct InstRange { int eval_begin, eval_end; };
 
+__global__ void __launch_bounds__(kThreads) k_reduce(const InstRange *__restrict__ ranges, Bufs b, int mode) {
+    const int inst = blockIdx.x / kPart, slot = blockIdx.x % kPart;
+    const Scalars *S = b.S + inst;
+    const bool live = (mode == 0) ? (S->status == NEEDS_INIT) : (S->status == RUNNING);
+    if (!live) return;
+    const InstRange r = ranges[inst];
+    const bool mx = slot_is_max(slot);
+    double acc = 0.0;
+    for (int blk = r.eval_begin + threadIdx.x; blk < r.eval_end; blk += kThreads) {
+        const double p = b.part[(size_t)blk * kPart + slot];
+        acc = mx ? nnmax(acc, p) : acc + p;
+    }
+    __shared__ double sh[kThreads];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] = mx ? nnmax(sh[threadIdx.x], sh[threadIdx.x + h]) : sh[threadIdx.x] + sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) b.red[(size_t)inst * kPart + slot] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// scalar controller: one thread per LP
+// ---------------------------------------------------------------------------
 __device__ double kkt_w(double rp2, double rd2, double gap, double w) {
     return sqrt(w * w * rp2 + rd2 / (w * w) + gap * gap);
 }
 
-__global__ void __launch_bounds__(kThreads) k_control(const InstRange *__restrict__ ranges, Bufs b, int mode) {
-    const int inst = blockIdx.x;
+__global__ void k_control(Bufs b, int mode, int k_lps) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= k_lps) return;
     Scalars *S = b.S + inst;
-    __shared__ double red[kThreads][kPart];
-    __shared__ int live;
-    if (threadIdx.x == 0) {
-        S->action = ACT_NONE;
-        live = (mode == 0) ? (S->status == NEEDS_INIT) : (S->status == RUNNING);
-    }
-    __syncthreads();
+    S->action = ACT_NONE;
+    const bool live = (mode == 0) ? (S->status == NEEDS_INIT) : (S->status == RUNNING);
     if (!live) return;
-    const InstRange r = ranges[inst];
-    double acc[kPart];
-#pragma unroll
-    for (int s = 0; s < kPart; s++) acc[s] = 0.0;
-    for (int blk = r.eval_begin + threadIdx.x; blk < r.eval_end; blk += kThreads) {
-        const double *p = b.part + (size_t)blk * kPart;
-#pragma unroll
-        for (int s = 0; s < kPart; s++) {
-            const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
-            acc[s] = is_max ? fmax(acc[s], p[s]) : acc[s] + p[s];
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < kPart; s++) red[threadIdx.x][s] = acc[s];
-    __syncthreads();
-    for (int h = kThreads / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            for (int s = 0; s < kPart; s++) {
-                const bool is_max = (s % kSlots) == RPU || (s % kSlots) == RDU;
-                const double a = red[threadIdx.x][s], c = red[threadIdx.x + h][s];
-                red[threadIdx.x][s] = is_max ? fmax(a, c) : a + c;
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double *T = red[0];
+    const double *T = b.red + (size_t)inst * kPart;
     const double w = S->omega;
     double K[2], rel[2][3], gap[2], pobj[2], dobj[2];
     for (int cnd = 0; cnd < 2; cnd++) {
@@ -288,8 +400,8 @@ __global__ void __launch_bounds__(kThreads) k_control(const InstRange *__restric
         rel[cnd][1] = a[RDU] / (1.0 + S->c_inf);
         rel[cnd][2] = fabs(gap[cnd]) / (1.0 + fabs(pobj[cnd]) + fabs(dobj[cnd]));
     }
-    if (mode == 0) {                     // initial anchor
-        S->kkt_anchor = K[0];
+    if (mode == 0) {                     // initial anchor (no residual yet for the fixed-point metric)
+        S->kkt_anchor = (S->algo == ALG_HALPERN && S->metric == METRIC_FPR) ? INFINITY : K[0];
         S->kkt_prev = INFINITY;
         S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
         S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
@@ -308,6 +420,49 @@ __global__ void __launch_bounds__(kThreads) k_control(const InstRange *__restric
     S->evals += 1;
     S->inv_j = 1.0 / (double)j;
     S->k_base = k;
+    if (S->algo == ALG_HALPERN) {
+        // candidate 0 = last map output; fixed-point residual terms in the second record
+        const double fx2 = T[kSlots + DX2], fy2 = T[kSlots + DY2];
+        if (!isfinite(K[0]) || !isfinite(fx2) || !isfinite(fy2)) {
+            S->status = NUMERIC;
+            b.status[inst] = S->status;
+            return;
+        }
+        S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
+        S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
+        if (fmax(rel[0][0], fmax(rel[0][1], rel[0][2])) <= S->tol) {
+            S->status = OPTIMAL;
+            S->which = 0;
+            b.status[inst] = S->status;
+            return;
+        }
+        const double r = (S->metric == METRIC_KKT) ? K[0] : sqrt(w * fx2 + fy2 / w);
+        const bool restart = (r <= 0.2 * S->kkt_anchor) ||
+                             (r <= 0.8 * S->kkt_anchor && r > S->kkt_prev) ||
+                             ((double)j >= 0.36 * (double)k);
+        if (restart) {
+            const double dx = sqrt(T[DX2]), dy = sqrt(T[DY2]);
+            double wn = w;
+            if (dx > 1e-10 && dy > 1e-10) wn = exp(0.5 * log(dy / dx) + 0.5 * log(w));
+            S->omega = wn;
+            S->kkt_anchor = (S->metric == METRIC_KKT) ? kkt_w(T[RP2], T[RD2], gap[0], wn)
+                                                      : sqrt(wn * fx2 + fy2 / wn);
+            S->kkt_prev = INFINITY;
+            S->j_base = 0;
+            S->restarts += 1;
+            S->tau = S->eta / wn;
+            S->sigma = S->eta * wn;
+            S->action = ACT_RESTART;
+        } else {
+            S->kkt_prev = r;
+            S->j_base = j;
+        }
+        if (k >= S->max_iter) {
+            S->status = ITER_LIMIT;
+            b.status[inst] = S->status;
+        }
+        return;
+    }
     if (!isfinite(K[0]) || !isfinite(K[1])) {
         S->status = NUMERIC;
         b.status[inst] = S->status;
@@ -356,7 +511,9 @@ __global__ void __launch_bounds__(kThreads) k_control(const InstRange *__restric
     }
 }
 
-// restart (current <- candidate, anchor <- candidate, sums <- 0) or finish (ret <- chosen)
+// Average variant: restart (current <- candidate, anchor <- candidate,
+// sums <- 0) or finish (returned point <- chosen candidate).  Halpern variant:
+// restart (current <- map output, anchor <- map output).
 __global__ void __launch_bounds__(kThreads) k_apply(const Seg *__restrict__ segs, int ncol_blocks, Bufs b) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
@@ -369,6 +526,12 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Seg *__restrict__ segs
     double *sum = col ? b.xsum : b.ysum;
     double *anc = col ? b.xa : b.ya;
     double *ret = col ? b.xret : b.yret;
+    if (S->algo == ALG_HALPERN) {
+        const double v = ret[idx];
+        cur[idx] = v;
+        anc[idx] = v;
+        return;
+    }
     const double avg = sum[idx] * S->inv_j;
     if (act == ACT_FINISH) {
         ret[idx] = S->which ? avg : cur[idx];
@@ -398,10 +561,11 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Layout {
     // uploaded once
     size_t A_rp, A_ci, A_v, AT_rp, AT_ci, AT_v, segs_p, segs_d, segs_e, segs_a, ranges;
+    size_t W, W1;
     // per-LP data (replaced by update_lp)
-    size_t c, l, u, Dc, q, Dr, x_init, y_init, S_init;
+    size_t c, l, u, Dc, q, Dr, inv_Dc, inv_Dr, lkey, ukey, x_init, y_init, S_init;
     // working state
-    size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, S, status;
+    size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status;
     size_t upload_end, total;
 };
 
@@ -410,6 +574,8 @@ struct Layout {
 
 struct uc_session {
     int k = 0, vb = 64;
+    int kernel = 1;               // 1 thread per row
+    int algo = 0;                 // ALG_HALPERN / ALG_AVERAGE (all LPs of a session)
     size_t vs = 8;
     uc_solve_opts o{};
     cudaStream_t s = nullptr;
@@ -475,7 +641,27 @@ static Scalars make_scalars(const uc_session &X, const PsData &p) {
     s.n_eval = X.o.n_eval;
     s.kkt_prev = INFINITY;
     s.status = NEEDS_INIT;
+    s.algo = X.algo;
+    s.metric = X.o.restart_metric;
     return s;
+}
+
+// host twin of the device okey(): doubles in the same order as int64 keys
+static long long order_key(double v) {
+    long long b;
+    std::memcpy(&b, &v, 8);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+static void derived_vectors(const PsData &p, std::vector<double> &idc, std::vector<double> &idr,
+                            std::vector<long long> &lk, std::vector<long long> &uk) {
+    idc.resize(p.n()); idr.resize(p.m()); lk.resize(p.n()); uk.resize(p.n());
+    for (int j = 0; j < p.n(); j++) {
+        idc[j] = 1.0 / p.Dc[j];
+        lk[j] = order_key(p.l[j]);
+        uk[j] = order_key(p.u[j]);
+    }
+    for (int i = 0; i < p.m(); i++) idr[i] = 1.0 / p.Dr[i];
 }
 
 // start point, initial scalars and per-LP vectors of LP i into the staging image
@@ -488,6 +674,15 @@ static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *
     put(st, L.Dc + X.coff[i] * 8, p.Dc.data(), p.n());
     put(st, L.q + X.roff[i] * 8, p.q.data(), p.m());
     put(st, L.Dr + X.roff[i] * 8, p.Dr.data(), p.m());
+    {
+        std::vector<double> idc, idr;
+        std::vector<long long> lk, uk;
+        derived_vectors(p, idc, idr, lk, uk);
+        put(st, L.inv_Dc + X.coff[i] * 8, idc.data(), p.n());
+        put(st, L.inv_Dr + X.roff[i] * 8, idr.data(), p.m());
+        put(st, L.lkey + X.coff[i] * 8, lk.data(), p.n());
+        put(st, L.ukey + X.coff[i] * 8, uk.data(), p.n());
+    }
     double *x0 = (double *)(st.data() + L.x_init) + X.coff[i];
     double *y0 = (double *)(st.data() + L.y_init) + X.roff[i];
     for (int c = 0; c < p.n(); c++) x0[c] = std::min(std::max(wx ? wx[c] : 0.0, p.l[c]), p.u[c]);
@@ -497,6 +692,34 @@ static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *
     }
     X.S_init[i] = make_scalars(X, p);
     put(st, L.S_init + sizeof(Scalars) * i, &X.S_init[i], 1);
+}
+
+// evaluation, record reduction and controller (mode 0: start point, 1: regular)
+static void launch_eval(uc_session &X, cudaStream_t s, int mode) {
+    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, mode);
+    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, mode);
+    k_reduce<<<X.k * kPart, kThreads, 0, s>>>(X.drg, X.b, mode);
+    k_control<<<(X.k + 127) / 128, 128, 0, s>>>(X.b, mode, X.k);
+}
+
+// iteration kernels of the session's algorithm
+template <int ALGO>
+static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
+    if (primal) {
+        if (X.vb == 32) k_primal<float, ALGO><<<X.n_sp, kThreads, 0, s>>>(X.dsp, X.b, it, src);
+        else k_primal<double, ALGO><<<X.n_sp, kThreads, 0, s>>>(X.dsp, X.b, it, src);
+    } else {
+        if (X.vb == 32) k_dual<float, ALGO><<<X.n_sd, kThreads, 0, s>>>(X.dsd, X.b, it, src);
+        else k_dual<double, ALGO><<<X.n_sd, kThreads, 0, s>>>(X.dsd, X.b, it, src);
+    }
+}
+static void launch_primal(uc_session &X, cudaStream_t s, int it, int src) {
+    if (X.algo == ALG_HALPERN) launch_iter<ALG_HALPERN>(X, s, it, src, true);
+    else launch_iter<ALG_AVERAGE>(X, s, it, src, true);
+}
+static void launch_dual(uc_session &X, cudaStream_t s, int it, int src) {
+    if (X.algo == ALG_HALPERN) launch_iter<ALG_HALPERN>(X, s, it, src, false);
+    else launch_iter<ALG_AVERAGE>(X, s, it, src, false);
 }
 
 static int capture(uc_session &X, int gi) {
@@ -511,20 +734,12 @@ static int capture(uc_session &X, int gi) {
     for (int it = 0; it < X.o.n_eval; it++) {
         const int src = it & 1;
         if (it == 0) rec(0);
-        if (X.n_sp) {
-            if (X.vb == 32) k_primal<float><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
-            else k_primal<double><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
-        }
+        if (X.n_sp) launch_primal(X, s, it, src);
         if (it == 0) rec(1);
-        if (X.n_sd) {
-            if (X.vb == 32) k_dual<float><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
-            else k_dual<double><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
-        }
+        if (X.n_sd) launch_dual(X, s, it, src);
         if (it == 0) rec(2);
     }
-    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
-    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
-    k_control<<<X.k, kThreads, 0, s>>>(X.drg, b, 1);
+    launch_eval(X, s, 1);
     if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err == cudaSuccess)
@@ -548,18 +763,10 @@ static int launch_direct(uc_session &X) {
     const Bufs &b = X.b;
     for (int it = 0; it < X.o.n_eval; it++) {
         const int src = it & 1;
-        if (X.n_sp) {
-            if (X.vb == 32) k_primal<float><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
-            else k_primal<double><<<X.n_sp, kThreads, 0, s>>>(X.dsp, b, it, src);
-        }
-        if (X.n_sd) {
-            if (X.vb == 32) k_dual<float><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
-            else k_dual<double><<<X.n_sd, kThreads, 0, s>>>(X.dsd, b, it, src);
-        }
+        if (X.n_sp) launch_primal(X, s, it, src);
+        if (X.n_sd) launch_dual(X, s, it, src);
     }
-    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
-    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, b, 1);
-    k_control<<<X.k, kThreads, 0, s>>>(X.drg, b, 1);
+    launch_eval(X, s, 1);
     if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
     UC_CUDA(cudaGetLastError());
     UC_CUDA(cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s));
@@ -578,10 +785,21 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     X->k = k;
     X->o = o;
     X->vb = Pp[0]->value_bits;
+    if (o.spmv_kernel < 0 || o.spmv_kernel > 1) { set_error("spmv_kernel must be 0 or 1"); return UC_EINVAL; }
+    if (o.algorithm < 0 || o.algorithm > 1 || o.restart_metric < 0 || o.restart_metric > 1) {
+        set_error("algorithm and restart_metric must be 0 or 1");
+        return UC_EINVAL;
+    }
+    X->kernel = 1;
+    X->algo = o.algorithm;
     X->vs = X->vb == 32 ? 4 : 8;
     X->P.assign(owners, owners + k);
     for (int i = 1; i < k; i++)
         if (Pp[i]->value_bits != X->vb) { set_error("batched LPs must share value_bits"); return UC_EINVAL; }
+    if (X->vb == 32)   // the kernels widen FP32 values by moving bits: normal, nonzero values only
+        for (int i = 0; i < k; i++)
+            for (float f : Pp[i]->A_val32)
+                if (!std::isnormal(f)) { set_error("FP32 matrix value %g is zero, subnormal or not finite", (double)f); return UC_EINVAL; }
     X->roff.assign(k + 1, 0); X->coff.assign(k + 1, 0); X->zoff.assign(k + 1, 0);
     for (int i = 0; i < k; i++) {
         X->roff[i + 1] = X->roff[i] + Pp[i]->m();
@@ -615,19 +833,24 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     size_t off = 0;
     auto take = [&](size_t n) { size_t p = off; off += align_up(std::max<size_t>(n, 1), 256); return p; };
     const size_t vs = X->vs;
-    L.A_rp = take((M + 1) * 4); L.A_ci = take(Z * 4); L.A_v = take(Z * vs);
-    L.AT_rp = take((N + 1) * 4); L.AT_ci = take(Z * 4); L.AT_v = take(Z * vs);
+    // +4 zero entries: a 16-byte load starting inside the array stays inside it
+    L.A_rp = take((M + 1) * 4); L.A_ci = take((Z + 4) * 4); L.A_v = take((Z + 4) * vs);
+    L.AT_rp = take((N + 1) * 4); L.AT_ci = take((Z + 4) * 4); L.AT_v = take((Z + 4) * vs);
     L.segs_p = take(sizeof(Seg) * X->n_sp); L.segs_d = take(sizeof(Seg) * X->n_sd);
     L.segs_e = take(sizeof(Seg) * X->n_se); L.segs_a = take(sizeof(Seg) * X->n_sa);
     L.ranges = take(sizeof(InstRange) * k);
+    const int nW = (int)std::min<long long>((long long)o.max_iter + 1, 1LL << 22);
+    L.W = take(sizeof(double) * nW); L.W1 = take(sizeof(double) * nW);
     L.c = take(N * 8); L.l = take(N * 8); L.u = take(N * 8); L.Dc = take(N * 8);
-    L.q = take(M * 8); L.Dr = take(M * 8);
+    L.inv_Dc = take(N * 8); L.lkey = take(N * 8); L.ukey = take(N * 8);
+    L.q = take(M * 8); L.Dr = take(M * 8); L.inv_Dr = take(M * 8);
     L.x_init = take(N * 8); L.y_init = take(M * 8); L.S_init = take(sizeof(Scalars) * k);
     L.upload_end = off;
     L.x0 = take(N * 8); L.x1 = take(N * 8); L.y0 = take(M * 8); L.y1 = take(M * 8);
     L.xsum = take(N * 8); L.ysum = take(M * 8); L.xa = take(N * 8); L.ya = take(M * 8);
     L.xret = take(N * 8); L.yret = take(M * 8);
     L.part = take(sizeof(double) * kPart * X->n_se);
+    L.red = take(sizeof(double) * kPart * k);
     L.S = take(sizeof(Scalars) * k);
     L.status = take(sizeof(int) * k);
     L.total = off;
@@ -663,6 +886,12 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         put(st, L.segs_e, se.data(), X->n_se);
         put(st, L.segs_a, sa.data(), X->n_sa);
         put(st, L.ranges, ranges.data(), k);
+        // Halpern weights, computed as the reference computes them: w = (j+1)/(j+2), 1 - w
+        double *W = (double *)(st.data() + L.W), *W1 = (double *)(st.data() + L.W1);
+        for (int jj = 0; jj < nW; jj++) {
+            W[jj] = ((double)jj + 1.0) / ((double)jj + 2.0);
+            W1[jj] = 1.0 - W[jj];
+        }
     }
 
     if (user_stream) X->s = user_stream;
@@ -691,6 +920,10 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     b.AT_rp = (const int *)(D + L.AT_rp); b.AT_ci = (const int *)(D + L.AT_ci); b.AT_v = D + L.AT_v;
     b.c = (const double *)(D + L.c); b.l = (const double *)(D + L.l); b.u = (const double *)(D + L.u);
     b.q = (const double *)(D + L.q); b.Dr = (const double *)(D + L.Dr); b.Dc = (const double *)(D + L.Dc);
+    b.inv_Dr = (const double *)(D + L.inv_Dr); b.inv_Dc = (const double *)(D + L.inv_Dc);
+    b.lkey = (const long long *)(D + L.lkey); b.ukey = (const long long *)(D + L.ukey);
+    b.W = (const double *)(D + L.W); b.W1 = (const double *)(D + L.W1); b.nW = nW;
+    b.red = (double *)(D + L.red);
     b.x[0] = (double *)(D + L.x0); b.x[1] = (double *)(D + L.x1);
     b.y[0] = (double *)(D + L.y0); b.y[1] = (double *)(D + L.y1);
     b.xsum = (double *)(D + L.xsum); b.ysum = (double *)(D + L.ysum);
@@ -736,12 +969,12 @@ static int session_reset(uc_session &X, int which) {
         const size_t cx = X.coff[i] * 8, nx = (X.coff[i + 1] - X.coff[i]) * 8;
         const size_t cy = X.roff[i] * 8, ny = (X.roff[i + 1] - X.roff[i]) * 8;
         if (nx) {
-            for (size_t dst : {L.x0, L.x1, L.xa})
+            for (size_t dst : {L.x0, L.x1, L.xa, L.xret})
                 UC_CUDA(cudaMemcpyAsync(D + dst + cx, D + L.x_init + cx, nx, cudaMemcpyDeviceToDevice, s));
             UC_CUDA(cudaMemsetAsync(D + L.xsum + cx, 0, nx, s));
         }
         if (ny) {
-            for (size_t dst : {L.y0, L.y1, L.ya})
+            for (size_t dst : {L.y0, L.y1, L.ya, L.yret})
                 UC_CUDA(cudaMemcpyAsync(D + dst + cy, D + L.y_init + cy, ny, cudaMemcpyDeviceToDevice, s));
             UC_CUDA(cudaMemsetAsync(D + L.ysum + cy, 0, ny, s));
         }
@@ -750,10 +983,8 @@ static int session_reset(uc_session &X, int which) {
         X.active[i] = 1;
         X.h_status[i] = NEEDS_INIT;
     }
-    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, 0);
-    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, 0);
-    k_control<<<X.k, kThreads, 0, s>>>(X.drg, X.b, 0);
-    X.launches += 2;
+    launch_eval(X, s, 0);
+    X.launches += 3;
     UC_CUDA(cudaGetLastError());
     return UC_OK;
 }
@@ -782,7 +1013,7 @@ static int session_run(uc_session &X, int max_replays) {
             UC_CUDA(cudaEventRecord(X.ev[launched & 3], s));
             launched++;
             X.polls++;
-            X.launches += 2LL * X.o.n_eval + 3;
+            X.launches += 2LL * X.o.n_eval + 4;
         }
         if (checked >= launched) break;
         UC_CUDA(cudaEventSynchronize(X.ev[checked & 3]));
@@ -833,17 +1064,21 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     const size_t cx = X.coff[i], cy = X.roff[i];
     UC_CUDA(cudaMemcpyAsync(res->x_cur.data(), X.b.x[cur] + cx, n * 8, cudaMemcpyDeviceToHost, s));
     UC_CUDA(cudaMemcpyAsync(res->y_cur.data(), X.b.y[cur] + cy, m * 8, cudaMemcpyDeviceToHost, s));
-    UC_CUDA(cudaMemcpyAsync(res->x_avg.data(), X.b.xsum + cx, n * 8, cudaMemcpyDeviceToHost, s));
-    UC_CUDA(cudaMemcpyAsync(res->y_avg.data(), X.b.ysum + cy, m * 8, cudaMemcpyDeviceToHost, s));
-    if (S.status == OPTIMAL) {
+    const bool halp = X.algo == ALG_HALPERN;
+    // Halpern: "average" slot = epoch anchor; returned point = last map output
+    UC_CUDA(cudaMemcpyAsync(res->x_avg.data(), (halp ? X.b.xa : X.b.xsum) + cx, n * 8, cudaMemcpyDeviceToHost, s));
+    UC_CUDA(cudaMemcpyAsync(res->y_avg.data(), (halp ? X.b.ya : X.b.ysum) + cy, m * 8, cudaMemcpyDeviceToHost, s));
+    if (S.status == OPTIMAL || halp) {
         res->x_ret.resize(n); res->y_ret.resize(m);
         UC_CUDA(cudaMemcpyAsync(res->x_ret.data(), X.b.xret + cx, n * 8, cudaMemcpyDeviceToHost, s));
         UC_CUDA(cudaMemcpyAsync(res->y_ret.data(), X.b.yret + cy, m * 8, cudaMemcpyDeviceToHost, s));
     }
     UC_CUDA(cudaStreamSynchronize(s));
-    for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
-    for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
-    if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
+    if (!halp) {
+        for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
+        for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
+        if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
+    }
     uc_stats &o = res->stats;
     int status;
     if (S.status == OPTIMAL) status = UC_OK;
@@ -866,7 +1101,7 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     o.timed_launches = X.timed;
     o.kernel_launches = (int)std::min<long long>(X.launches, INT32_MAX);
     o.h2d_bytes = X.h2d;
-    o.d2h_bytes = (long long)(n + m) * 8 * (S.status == OPTIMAL ? 3 : 2) + (long long)sizeof(Scalars) +
+    o.d2h_bytes = (long long)(n + m) * 8 * ((S.status == OPTIMAL || halp) ? 3 : 2) + (long long)sizeof(Scalars) +
                   X.polls * 4LL * X.k;
     X.active[i] = 0;
     *out = guard.release();
@@ -893,11 +1128,20 @@ static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const P
     int rc = 0;
     rc |= h2d(L.c, cx, c.c); rc |= h2d(L.l, cx, c.l); rc |= h2d(L.u, cx, c.u); rc |= h2d(L.Dc, cx, c.Dc);
     rc |= h2d(L.x_init, cx, x0); rc |= h2d(L.q, cy, c.q); rc |= h2d(L.Dr, cy, c.Dr); rc |= h2d(L.y_init, cy, y0);
-    if (rc) return UC_ECUDA;
+    std::vector<double> idc, idr;
+    std::vector<long long> lk, uk;
+    derived_vectors(c, idc, idr, lk, uk);
+    rc |= h2d(L.inv_Dc, cx, idc); rc |= h2d(L.inv_Dr, cy, idr);
+    if (!lk.empty()) {
+        if (cudaMemcpyAsync(X.D + L.lkey + cx, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess ||
+            cudaMemcpyAsync(X.D + L.ukey + cx, uk.data(), uk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess)
+            rc = 1;
+    }
+    if (rc) { set_error("update_lp: host-to-device copy failed"); return UC_ECUDA; }
     X.S_init[i] = make_scalars(X, c);
     UC_CUDA(cudaMemcpyAsync(X.D + L.S_init + sizeof(Scalars) * i, &X.S_init[i], sizeof(Scalars),
                             cudaMemcpyHostToDevice, X.s));
-    X.h2d += (long long)(5 * c.n() + 3 * c.m()) * 8 + (long long)sizeof(Scalars);
+    X.h2d += (long long)(8 * c.n() + 4 * c.m()) * 8 + (long long)sizeof(Scalars);
     UC_CUDA(cudaStreamSynchronize(X.s));
     return UC_OK;
 }

@@ -29,13 +29,28 @@ def oracle_pipeline(P):
     return raw, ps, S
 
 
-def oracle_trace(S, ks, n_eval=pdhg.N_EVAL):
-    """Oracle current iterates after each step count in ks (tol 0: never stops)."""
+def oracle_trace(S, ks, n_eval=pdhg.N_EVAL, variant="halpern", metric="kkt"):
+    """Oracle current iterates after each step count in ks (tol 0: never stops):
+    {k: (x, y, restarts, omega, x_map, y_map)}; x_map/y_map are the last PDHG
+    map output for the Halpern variant (None for the averaging variant)."""
     out = {}
     def rec(k, st):
-        out[k] = (st.x.copy(), st.y.copy(), st.restarts, st.omega)
-    pdhg.solve(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, trace=rec, trace_iters=ks)
+        xm = getattr(st, "xh", None)
+        ym = getattr(st, "yh", None)
+        out[k] = (st.x.copy(), st.y.copy(), st.restarts, st.omega,
+                  None if xm is None else xm.copy(), None if ym is None else ym.copy())
+    if variant == "halpern":
+        pdhg.solve_halpern(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, metric=metric, trace=rec,
+                           trace_iters=ks)
+    else:
+        pdhg.solve(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, trace=rec, trace_iters=ks)
     return out
+
+
+def oracle_solve(S, tol, variant="halpern", metric="kkt"):
+    if variant == "halpern":
+        return pdhg.solve_halpern(S, tol=tol, metric=metric)
+    return pdhg.solve(S, tol=tol)
 
 
 def rel_inf(a, b):

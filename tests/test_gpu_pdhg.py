@@ -6,7 +6,7 @@ import pytest
 
 import ucgen
 from gpu_common import (ITERATE_RTOL, KKT_TOL, OBJ_GAP_TOL, golden_tiny, oracle_kkt_of_raw,
-                        oracle_pipeline, oracle_trace, raw_objective, rel_inf)
+                        oracle_pipeline, oracle_solve, oracle_trace, raw_objective, rel_inf)
 from oracle import lp as olp, pdhg, simplex
 
 pytestmark = pytest.mark.gpu
@@ -34,34 +34,45 @@ def _device_iterates(B, ps, n, m, K, **kw):
 KS = [1, 2, 3, 17, 63, 64, 65, 127, 128, 129, 191, 192, 193, 200]
 
 
+VARIANTS = [("halpern", "kkt"), ("halpern", "fpr"), ("average", "kkt")]
+
+
+@pytest.mark.parametrize("variant,metric", VARIANTS)
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("which", ["tiny", "small_ragged"])
-def test_per_iterate_parity_first_200(B, which, use_graph):
+def test_per_iterate_parity_first_200(B, which, use_graph, variant, metric):
     if which == "tiny":
         P = ucgen.tiny(0)
     else:  # sizes far from the 256-row tiles, zero-Pmin units
         P = ucgen.make_problem(7, B=37, L=53, G=11, T=5, lo=0.5, hi=0.9, noise=0.05, zero_pmin_frac=0.2)
     raw, ps_o, S = oracle_pipeline(P)
-    ref = oracle_trace(S, KS)
+    ref = oracle_trace(S, KS, variant=variant, metric=metric)
     ps = B.uc_presolve(B.uc_build_lp(P))
     n, m, _, _ = B.uc_presolved_dims(ps)
     for K in KS:
-        x, y, st = _device_iterates(B, ps, n, m, K, use_graph=use_graph)
-        xo, yo, restarts, omega = ref[K]
+        x, y, st = _device_iterates(B, ps, n, m, K, use_graph=use_graph, algorithm=variant,
+                                    restart_metric=metric)
+        xo, yo, restarts, omega, xm, ym = ref[K]
         assert st["iters"] == K
         assert st["restarts"] == restarts, f"restart decision differs at K={K}"
         assert rel_inf(x, xo) <= ITERATE_RTOL, (K, rel_inf(x, xo))
         assert rel_inf(y, yo) <= ITERATE_RTOL, (K, rel_inf(y, yo))
         assert st["omega"] == pytest.approx(omega, rel=1e-9)
+        if xm is not None:   # the PDHG map output the Halpern step came from
+            res, _ = B.uc_solve(ps, tol=0.0, max_iter=K, use_graph=use_graph, algorithm=variant,
+                                restart_metric=metric)
+            xr, yr = B.uc_get_iterate(res, 2, n, m)
+            assert rel_inf(xr, xm) <= ITERATE_RTOL and rel_inf(yr, ym) <= ITERATE_RTOL
 
 
+@pytest.mark.parametrize("variant,metric", VARIANTS)
 @pytest.mark.parametrize("seed", range(4))
-def test_tiny_solve_meets_gates(B, seed):
+def test_tiny_solve_meets_gates(B, seed, variant, metric):
     g = golden_tiny()
     P = ucgen.tiny(seed)
     raw, ps_o, S = oracle_pipeline(P)
     ps = B.uc_presolve(B.uc_build_lp(P))
-    res, rc = B.uc_solve(ps, tol=KKT_TOL)
+    res, rc = B.uc_solve(ps, tol=KKT_TOL, algorithm=variant, restart_metric=metric)
     assert rc == B.UC_OK
     st = B.uc_get_stats(res)
     xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
@@ -70,7 +81,7 @@ def test_tiny_solve_meets_gates(B, seed):
     assert abs(raw_objective(raw, xr) - opt) / max(1.0, abs(opt)) <= OBJ_GAP_TOL
     assert st["objective"] == pytest.approx(raw_objective(raw, xr), rel=1e-12)
     # the oracle PDHG takes the same path to the same stop
-    r = pdhg.solve(S, tol=KKT_TOL)
+    r = oracle_solve(S, KKT_TOL, variant, metric)
     assert r.iters == st["iters"] and r.restarts == st["restarts"]
     # power balance of the returned dispatch, per period (satisfied to the tolerance)
     sol = B.uc_get_solution(res, P.T, P.B, P.L, P.G)
@@ -145,13 +156,14 @@ def test_edge_cases(B):
     assert abs(raw_objective(raw, xr) - ref.obj) / ref.obj <= OBJ_GAP_TOL
 
 
+@pytest.mark.parametrize("variant", ["halpern", "average"])
 @pytest.mark.parametrize("n_eval", [2, 16, 128])
-def test_other_evaluation_periods(B, n_eval):
+def test_other_evaluation_periods(B, n_eval, variant):
     P = ucgen.micro(1, B=10, L=14, G=4, T=6)
     raw, ps_o, S = oracle_pipeline(P)
     ps = B.uc_presolve(B.uc_build_lp(P))
     n, m, _, _ = B.uc_presolved_dims(ps)
     K = 3 * n_eval + 1
-    ref = oracle_trace(S, [K], n_eval=n_eval)
-    x, y, st = _device_iterates(B, ps, n, m, K, n_eval=n_eval)
+    ref = oracle_trace(S, [K], n_eval=n_eval, variant=variant)
+    x, y, st = _device_iterates(B, ps, n, m, K, n_eval=n_eval, algorithm=variant)
     assert rel_inf(x, ref[K][0]) <= ITERATE_RTOL and rel_inf(y, ref[K][1]) <= ITERATE_RTOL

@@ -127,3 +127,62 @@ def test_first_evaluation_restarts():
     pdhg.solve(S, tol=0.0, max_iter=pdhg.N_EVAL,
                trace=lambda k, st: seen.setdefault(k, (st.restarts, st.j)), trace_iters=[pdhg.N_EVAL])
     assert seen[pdhg.N_EVAL] == (1, 0)       # j = 64 >= 0.36 * 64 always fires
+
+
+# ---------------------------------------------------------------------------
+# Halpern variant (the default)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("metric", ["kkt", "fpr"])
+@pytest.mark.parametrize("seed", range(3))
+def test_halpern_reaches_simplex_objective(seed, metric):
+    P = ucgen.make_problem(seed, B=12, L=16, G=4, T=6, lo=0.4, hi=0.8, noise=0.05,
+                           zero_pmin_frac=0.25)
+    raw, ps, S = _pipeline(P)
+    r = pdhg.solve_halpern(S, tol=1e-4, max_iter=100_000, metric=metric)
+    assert r.status == "optimal"
+    x, y = S.Dc * r.x, S.Dr * r.y
+    assert max(kkt.relative_kkt(ps.lp, x, y)) <= 1e-4
+    ref = simplex.solve_lp(raw)
+    xr, _ = ops.postsolve(ps, x)
+    assert abs(float(raw.c @ xr) - ref.obj) / max(1.0, abs(ref.obj)) <= 1e-4
+
+
+def test_halpern_tiny_objective_matches_golden():
+    with open(os.path.join(GOLDEN, "tiny_lp.json")) as f:
+        g = json.load(f)
+    raw, ps, S = _pipeline(ucgen.tiny(g["seed"]))
+    r = pdhg.solve_halpern(S, tol=1e-4)
+    assert r.status == "optimal"
+    xr, _ = ops.postsolve(ps, S.Dc * r.x)
+    assert abs(float(raw.c @ xr) - g["objective"]) / abs(g["objective"]) <= 1e-4
+
+
+def test_halpern_first_step_is_the_pdhg_step_and_maps_stay_feasible():
+    raw, ps, S = _pipeline(ucgen.micro(0, B=10, L=13, G=4, T=6))
+    st_p = pdhg.initial_state(S)
+    st_h = pdhg.halpern_initial_state(S)
+    pdhg.step(S, st_p)
+    pdhg.halpern_step(S, st_h)
+    # w = 1/2 on the first step of an epoch: z1 = (2 T(z0) - z0)/2 + z0/2 = T(z0)
+    np.testing.assert_allclose(st_h.x, st_p.x, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(st_h.y, st_p.y, rtol=0, atol=1e-12)
+    U = pdhg._unscaled_lp(S)
+    for _ in range(300):
+        pdhg.halpern_step(S, st_h)
+        assert np.all(st_h.xh >= S.l) and np.all(st_h.xh <= S.u)
+        assert np.all(st_h.yh[S.m_eq:] >= 0.0)
+        if st_h.k % pdhg.N_EVAL == 0:
+            pdhg.halpern_evaluate(S, st_h, U, 0.0)
+
+
+def test_halpern_second_step_weight():
+    # with no active constraint the map reaches its fixed point in one step; the
+    # second step's weight w = 2/3 then pulls z back toward the anchor z0 = 0
+    lp = olp.LP(A=sp.csr_matrix(np.array([[1.0, 1.0, 1.0]])), q=np.array([-100.0]),
+                c=np.array([1.0, -1.0, 2.0]), l=np.zeros(3), u=np.array([1.0, 1.0, 5.0]), m_eq=0)
+    S = ops.scale(lp, ruiz_iters=0, pock_chambolle=False)
+    st = pdhg.halpern_initial_state(S)
+    pdhg.halpern_step(S, st)
+    pdhg.halpern_step(S, st)
+    # z2 = 2/3 (2 T(z1) - z1) + 1/3 z0 with T(z1) = z1 = (0, 1, 0), z0 = 0
+    np.testing.assert_allclose(st.x, [0.0, 2.0 / 3.0, 0.0], rtol=0, atol=1e-15)
