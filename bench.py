@@ -391,13 +391,109 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """64 uneven UC LPs (buses log-uniform in [300, 6049], T in {24, 48}, seeds
+    1-64) in one block-diagonal session with FP32 matrix values and autotuned
+    row splits, against one-at-a-time FP64 solves of the same LPs."""
+    import numpy as np
+    import torch
+    import ucgen
+    torch.cuda.set_device(0)
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding as B
+    from paper_2607_03627_gb300.batch import presolve_all, solve_batch
+    from paper_2607_03627_gb300.tune import Tuner
+    probs = [ucgen.batch_member(s) for s in range(1, args.batch + 1)]
+    t0 = time.perf_counter()
+    ps32 = presolve_all(probs, value_bits=32)
+    presolve_s = time.perf_counter() - t0
+    tuner = Tuner()
+    solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32)      # warm-up + tuning
+    with ClockSampler(0) as clk:
+        res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32)
+    st32 = [B.uc_get_stats(r) for r, _ in res32]
+    line = {"metric": METRIC, "value": args.batch / (info["solve_ms"] / 1e3), "unit": "UC LP/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": info["solve_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-values/f64", "data": "synthetic",
+            "config": {"workload": f"{args.batch} UC LPs, buses log-uniform in [300, 6049], T 24/48, seeds 1-{args.batch}",
+                       "total_nnz": int(sum(B.uc_presolved_dims(p)[3] for p in ps32)),
+                       "matrix_values": "fp32", "vectors": "fp64", "tol_rel_kkt": TOL},
+            "rows_per_thread": info["rows_per_thread"], "all_optimal": all(s["status"] == 0 for s in st32),
+            "per_lp": [{"buses": P.B, "T": P.T, "iters": s["iters"], "status": s["status_name"],
+                        "rel_kkt": max(s["rel_primal"], s["rel_dual"], s["rel_gap"])} for P, s in zip(probs, st32)],
+            "max_iters": max(s["iters"] for s in st32), "presolve_s": presolve_s,
+            "device_bytes": info["device_bytes"], "clocks": clk.summary(), "impl": "ours"}
+    if not args.no_sequential:
+        ps64 = presolve_all(probs, value_bits=64)
+        tot_ms = 0.0
+        errs = []
+        seq_iters = []
+        for p, (r32, _), s32 in zip(ps64, res32, st32):
+            sess = B.Session([p], tol=TOL, max_iter=args.max_iter)
+            sess.reset(-1); sess.run()                      # warm-up
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); sess.reset(-1); sess.run(); e1.record(); torch.cuda.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            r64, _ = sess.result(0)
+            s64 = B.uc_get_stats(r64)
+            o64 = s64["objective"]
+            seq_iters.append((s64["iters"], s64["status_name"]))
+            errs.append(abs(s32["objective"] - o64) / max(1.0, abs(o64)))
+            sess.close()
+        line["sequential_fp64"] = {"ms": tot_ms, "lp_per_s": args.batch / (tot_ms / 1e3), "per_lp": seq_iters,
+                                   "note": "one-at-a-time FP64 sessions, device-resident, summed device time"}
+        line["speedup_vs_sequential_fp64"] = tot_ms / info["solve_ms"]
+        line["objective_gap_vs_fp64"] = {"max": max(errs), "mean": float(np.mean(errs))}
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Served stream: requests on the 6,049-bus grid with loads scaled by
+    {0.80..1.20} and AR(1) noise, Poisson arrivals at 2 req/s, continuous
+    batching with warm starts, against one-at-a-time cold FP64 solves."""
+    import torch
+    import ucgen
+    torch.cuda.set_device(0)
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300.serve import Request, Server, sequential_baseline
+    base = ucgen.paper_scale(0)
+    reqs = []
+    t = 0.0
+    for w in range((args.requests + 44) // 45):
+        n = min(45, args.requests - 45 * w)
+        arr = ucgen.poisson_arrivals(100 + w, n, 2.0) + t
+        for r in range(n):
+            reqs.append(Request(rid=45 * w + r, problem=ucgen.served_request(base, w, r), arrival=float(arr[r])))
+        t = float(arr[-1])
+    srv = Server(base, slots=args.slots, hbm_budget_gb=150.0, tol=TOL, max_iter=args.max_iter)
+    with ClockSampler(0) as clk:
+        m = srv.serve(reqs, realtime=True)
+    srv.close()
+    line = {"metric": METRIC, "value": m["p50_latency_s"], "unit": "s (p50 served latency)",
+            "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": m["makespan_s"] / len(reqs) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{len(reqs)} requests on the 6049-bus / 700-unit / 48-period grid, "
+                                            "load x{0.80..1.20} + AR(1) 5%, Poisson 2 req/s",
+                                            "slots": m["slots"], "hbm_budget_gb": 150.0, "tol_rel_kkt": TOL},
+            "served": m, "clocks": clk.summary(), "impl": "ours"}
+    if not args.no_sequential:
+        line["sequential_fp64_cold"] = sequential_baseline(reqs, base, tol=TOL, max_iter=args.max_iter)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="paper", choices=["paper", "paper-fp32", "tiny"])
+    ap.add_argument("--config", default="paper", choices=["paper", "paper-fp32", "tiny", "batch64", "served"])
+    ap.add_argument("--batch", type=int, default=64, help="batch64: number of LPs")
+    ap.add_argument("--requests", type=int, default=45, help="served: requests (45 per wave)")
+    ap.add_argument("--slots", type=int, default=4, help="served: session slots")
+    ap.add_argument("--no-sequential", action="store_true", help="batch64/served: skip the one-at-a-time baseline")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=256)
@@ -410,6 +506,10 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch64":
+        run_batch(args)
+    elif args.config == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -101,8 +101,12 @@ typedef struct {
     uc_alloc_fn alloc;           /* nullable device allocator */
     uc_free_fn free;
     void *alloc_ctx;
-    int spmv_kernel;             /* iteration kernels: 0 default (warp tile), 1 one thread per row,
-                                    2 warp tile (a warp owns 32 rows, coalesced 16-byte loads) */
+    int spmv_kernel;             /* iteration kernels: 0 or 1, one thread per row (the only variant) */
+    int cta_rows;                /* threads per CTA of the iteration kernels: 0 (default 256), 128,
+                                    256 or 512; results do not depend on it (tuning knob) */
+    const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or
+                                    4 (default 1); results do not depend on it (autotuned per size
+                                    bucket, so LPs of one launch may differ) */
     int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
                                     averaging with KKT restarts (both constant-step, see DESIGN) */
     int restart_metric;          /* Halpern restarts: 0 (default) weighted KKT of the map output,
@@ -153,6 +157,14 @@ int uc_lp_export(const uc_lp *lp, int32_t *rowptr, int32_t *colidx, double *val,
  * scaling and the step size.  Host only.  UC_EINFEASIBLE / UC_EUNBOUNDED
  * when presolve proves it. */
 int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **out);
+/* Presolve `lp` reusing the scaling, scaled matrices and step size of `base`:
+ * for an LP with the same grid and units as `base` (only loads differ), whose
+ * raw matrix and presolve reductions are therefore identical.  The result is
+ * what uc_presolve would give except that omega0 is recomputed from the new
+ * q and c, while D_r, D_c, A_s and eta are the base's.  UC_EINVAL if the raw
+ * matrix or the removed rows/columns differ.  Sessions accept it in
+ * uc_session_update_lp for a slot that holds `base`. */
+int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **out);
 int uc_presolved_dims(const uc_presolved *ps, int *n, int *m, int *m_eq, int64_t *nnz);
 /* Copy out the scaled reduced LP and its scaling: rowptr [m+1], colidx [nnz],
  * val [nnz] (FP64 scaled values), q, Dr [m], c, l, u, Dc [n], col_map [n] and

@@ -48,7 +48,9 @@ class uc_solve_opts(C.Structure):
                 ("n_eval", C.c_int), ("use_graph", C.c_int), ("kernel_timing", C.c_int),
                 ("timeout_ms", C.c_double), ("warm_x", _d), ("warm_y", _d),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("spmv_kernel", C.c_int), ("algorithm", C.c_int), ("restart_metric", C.c_int),
+                ("spmv_kernel", C.c_int), ("cta_rows", C.c_int), ("rows_per_thread", _P(C.c_int)),
+                ("algorithm", C.c_int),
+                ("restart_metric", C.c_int),
                 ("cancel", _P(C.c_int))]
 
 
@@ -82,6 +84,7 @@ _SIGS = {
     "uc_lp_dims": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int64)]),
     "uc_lp_export": (C.c_int, [C.c_void_p, _i, _i, _d, _d, _d, _d, _d]),
     "uc_presolve": (C.c_int, [C.c_void_p, _P(uc_presolve_opts), _P(C.c_void_p)]),
+    "uc_presolve_reuse": (C.c_int, [C.c_void_p, C.c_void_p, _P(C.c_void_p)]),
     "uc_presolved_dims": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int64)]),
     "uc_presolved_export": (C.c_int, [C.c_void_p, _i, _i, _d, _d, _d, _d, _d, _d, _d, _i, _i, _d]),
     "uc_solve": (C.c_int, [C.c_void_p, _P(uc_solve_opts), C.c_void_p, _P(C.c_void_p)]),
@@ -217,6 +220,12 @@ def uc_presolve(lp, value_bits: int = 64, **kw) -> PresolvedHandle:
     return PresolvedHandle(out.value, keep=lp)
 
 
+def uc_presolve_reuse(base, lp) -> PresolvedHandle:
+    out = C.c_void_p()
+    _check(lib.uc_presolve_reuse(base.ptr, lp.ptr, C.byref(out)), "uc_presolve_reuse")
+    return PresolvedHandle(out.value, keep=lp)
+
+
 def uc_presolved_dims(ps):
     n, m, me, z = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
     _check(lib.uc_presolved_dims(ps.ptr, C.byref(n), C.byref(m), C.byref(me), C.byref(z)),
@@ -282,9 +291,11 @@ def _torch_stream_and_allocator():
 def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use_graph: bool = True,
                kernel_timing: bool = False, timeout_ms: float = 0.0, warm_x=None, warm_y=None,
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
-               restart_metric: str = "kkt") -> tuple[uc_solve_opts, list]:
+               restart_metric: str = "kkt", cta_rows: int = 0,
+               rows_per_thread=None) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
+    keep = []
     o.tol_rel_kkt = tol
     o.max_iter = int(max_iter)
     o.n_eval = int(n_eval)
@@ -292,9 +303,13 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.kernel_timing = int(bool(kernel_timing))
     o.timeout_ms = float(timeout_ms)
     o.spmv_kernel = int(spmv_kernel)
+    o.cta_rows = int(cta_rows)
+    if rows_per_thread is not None:
+        rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
+        keep.append(rp)
+        o.rows_per_thread = _ptr(rp, C.c_int32)
     o.algorithm = {"halpern": 0, "average": 1}[algorithm]
     o.restart_metric = {"kkt": 0, "fpr": 1}[restart_metric]
-    keep = []
     if warm_x is not None:
         wx = _f64(warm_x); keep.append(wx); o.warm_x = _ptr(wx, C.c_double)
     if warm_y is not None:

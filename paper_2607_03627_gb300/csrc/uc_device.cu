@@ -72,6 +72,7 @@ struct Seg {
     int end;     // one past the last
     int aux;     // dual kernel: first ">=" row of this LP; evaluation kernel: 1 for a
                  // column slice, (first ">=" row) << 1 for a row slice
+    int rpt;     // iteration kernels: rows per thread (the slice has rpt * blockDim rows)
 };
 
 struct Bufs {
@@ -149,17 +150,18 @@ __device__ __forceinline__ void halpern_weights(const Bufs &b, const Scalars *S,
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
 // the last step of a block (and at the iteration limit).
-template <typename VT, int ALGO>
-__global__ void __launch_bounds__(kThreads) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+template <typename VT, int ALGO, int BS>
+__global__ void __launch_bounds__(BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
     if (S->status != RUNNING || k >= S->max_iter) return;
-    const int j = sg.begin + threadIdx.x;
-    if (j >= sg.end) return;
     const double tau = S->tau;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
+    for (int t = 0; t < sg.rpt; t++) {
+    const int j = sg.begin + t * BS + threadIdx.x;
+    if (j >= sg.end) return;
     const double xin = b.x[src][j];
     const double cj = b.c[j];
     const long long lk = b.lkey[j], uk = b.ukey[j];
@@ -179,21 +181,23 @@ __global__ void __launch_bounds__(kThreads) k_primal(const Seg *__restrict__ seg
         b.x[src ^ 1][j] = w * xb + w1 * aux;
         if (it == S->n_eval - 1 || k == S->max_iter - 1) b.xret[j] = xv;
     }
+    }
 }
 
 // ALGO = ALG_AVERAGE: y+ = proj(y + sigma (q - A (2 x+ - x))), running sum.
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
-template <typename VT, int ALGO>
-__global__ void __launch_bounds__(kThreads) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+template <typename VT, int ALGO, int BS>
+__global__ void __launch_bounds__(BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
     if (S->status != RUNNING || k >= S->max_iter) return;
-    const int i = sg.begin + threadIdx.x;
-    if (i >= sg.end) return;
     const double sigma = S->sigma;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    for (int t = 0; t < sg.rpt; t++) {
+    const int i = sg.begin + t * BS + threadIdx.x;
+    if (i >= sg.end) return;
     const double yin = b.y[src][i];
     const double qi = b.q[i];
     const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : b.ya[i];
@@ -220,6 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(const Seg *__restrict__ segs,
         halpern_weights(b, S, it, w, w1);
         b.y[src ^ 1][i] = w * (2.0 * yv - yin) + w1 * aux;
         if (it == S->n_eval - 1 || k == S->max_iter - 1) b.yret[i] = yv;
+    }
     }
 }
 
@@ -514,12 +519,14 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
 // Average variant: restart (current <- candidate, anchor <- candidate,
 // sums <- 0) or finish (returned point <- chosen candidate).  Halpern variant:
 // restart (current <- map output, anchor <- map output).
-__global__ void __launch_bounds__(kThreads) k_apply(const Seg *__restrict__ segs, int ncol_blocks, Bufs b) {
+template <int BS>
+__global__ void __launch_bounds__(BS) k_apply(const Seg *__restrict__ segs, int ncol_blocks, Bufs b) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int act = S->action;
     if (act == ACT_NONE) return;
-    const int idx = sg.begin + threadIdx.x;
+    for (int t = 0; t < sg.rpt; t++) {
+    const int idx = sg.begin + t * BS + threadIdx.x;
     if (idx >= sg.end) return;
     const bool col = blockIdx.x < (unsigned)ncol_blocks;
     double *cur = col ? b.x[0] : b.y[0];
@@ -530,17 +537,18 @@ __global__ void __launch_bounds__(kThreads) k_apply(const Seg *__restrict__ segs
         const double v = ret[idx];
         cur[idx] = v;
         anc[idx] = v;
-        return;
+        continue;
     }
     const double avg = sum[idx] * S->inv_j;
     if (act == ACT_FINISH) {
         ret[idx] = S->which ? avg : cur[idx];
-        return;
+        continue;
     }
     const double v = S->cand ? avg : cur[idx];
     cur[idx] = v;
     anc[idx] = v;
     sum[idx] = 0.0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -575,6 +583,7 @@ struct Layout {
 struct uc_session {
     int k = 0, vb = 64;
     int kernel = 1;               // 1 thread per row
+    int cta = 256;                // rows (= threads) per CTA of the row kernels
     int algo = 0;                 // ALG_HALPERN / ALG_AVERAGE (all LPs of a session)
     size_t vs = 8;
     uc_solve_opts o{};
@@ -597,6 +606,11 @@ struct uc_session {
     cudaEvent_t tev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int *h_status = nullptr;      // pinned [k]
     std::vector<char> active;     // LPs reset since their last result
+    std::vector<int> rpt;         // rows per thread of each LP's iteration CTAs
+    std::vector<int> m_eq;        // equality rows of each LP
+    std::vector<char> tabled;     // LPs whose CTAs are in the current tables and graph
+    int cap_sp = 0, cap_sd = 0, cap_se = 0, cap_sa = 0;
+    int retables = 0;
     double tp_sum = 0.0, td_sum = 0.0;
     int timed = 0;
     long long launches = 0;
@@ -703,23 +717,39 @@ static void launch_eval(uc_session &X, cudaStream_t s, int mode) {
 }
 
 // iteration kernels of the session's algorithm
-template <int ALGO>
+template <int ALGO, int BS>
 static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
     if (primal) {
-        if (X.vb == 32) k_primal<float, ALGO><<<X.n_sp, kThreads, 0, s>>>(X.dsp, X.b, it, src);
-        else k_primal<double, ALGO><<<X.n_sp, kThreads, 0, s>>>(X.dsp, X.b, it, src);
+        if (X.vb == 32) k_primal<float, ALGO, BS><<<X.n_sp, BS, 0, s>>>(X.dsp, X.b, it, src);
+        else k_primal<double, ALGO, BS><<<X.n_sp, BS, 0, s>>>(X.dsp, X.b, it, src);
     } else {
-        if (X.vb == 32) k_dual<float, ALGO><<<X.n_sd, kThreads, 0, s>>>(X.dsd, X.b, it, src);
-        else k_dual<double, ALGO><<<X.n_sd, kThreads, 0, s>>>(X.dsd, X.b, it, src);
+        if (X.vb == 32) k_dual<float, ALGO, BS><<<X.n_sd, BS, 0, s>>>(X.dsd, X.b, it, src);
+        else k_dual<double, ALGO, BS><<<X.n_sd, BS, 0, s>>>(X.dsd, X.b, it, src);
+    }
+}
+template <int ALGO>
+static void launch_iter_bs(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
+    switch (X.cta) {
+        case 128: launch_iter<ALGO, 128>(X, s, it, src, primal); break;
+        case 512: launch_iter<ALGO, 512>(X, s, it, src, primal); break;
+        default: launch_iter<ALGO, 256>(X, s, it, src, primal); break;
     }
 }
 static void launch_primal(uc_session &X, cudaStream_t s, int it, int src) {
-    if (X.algo == ALG_HALPERN) launch_iter<ALG_HALPERN>(X, s, it, src, true);
-    else launch_iter<ALG_AVERAGE>(X, s, it, src, true);
+    if (X.algo == ALG_HALPERN) launch_iter_bs<ALG_HALPERN>(X, s, it, src, true);
+    else launch_iter_bs<ALG_AVERAGE>(X, s, it, src, true);
 }
 static void launch_dual(uc_session &X, cudaStream_t s, int it, int src) {
-    if (X.algo == ALG_HALPERN) launch_iter<ALG_HALPERN>(X, s, it, src, false);
-    else launch_iter<ALG_AVERAGE>(X, s, it, src, false);
+    if (X.algo == ALG_HALPERN) launch_iter_bs<ALG_HALPERN>(X, s, it, src, false);
+    else launch_iter_bs<ALG_AVERAGE>(X, s, it, src, false);
+}
+static void launch_apply(uc_session &X, cudaStream_t s) {
+    if (!X.n_sa) return;
+    switch (X.cta) {
+        case 128: k_apply<128><<<X.n_sa, 128, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        case 512: k_apply<512><<<X.n_sa, 512, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        default: k_apply<256><<<X.n_sa, 256, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+    }
 }
 
 static int capture(uc_session &X, int gi) {
@@ -740,7 +770,7 @@ static int capture(uc_session &X, int gi) {
         if (it == 0) rec(2);
     }
     launch_eval(X, s, 1);
-    if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
+    launch_apply(X, s);
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s);
@@ -767,11 +797,74 @@ static int launch_direct(uc_session &X) {
         if (X.n_sd) launch_dual(X, s, it, src);
     }
     launch_eval(X, s, 1);
-    if (X.n_sa) k_apply<<<X.n_sa, kThreads, 0, s>>>(X.dsa, X.n_sp, b);
+    launch_apply(X, s);
     UC_CUDA(cudaGetLastError());
     UC_CUDA(cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s));
     return UC_OK;
 }
+
+// CTA tables of the LPs with mask[i]: every CTA works on a slice of one LP.
+// LPs outside the mask get no CTAs (and an empty evaluation range).
+static void build_tables(const uc_session &X, const std::vector<char> &mask, std::vector<Seg> &sp,
+                         std::vector<Seg> &sd, std::vector<Seg> &se, std::vector<Seg> &sa,
+                         std::vector<InstRange> &ranges) {
+    sp.clear(); sd.clear(); se.clear(); sa.clear();
+    ranges.assign(X.k, InstRange{0, 0});
+    for (int i = 0; i < X.k; i++) {
+        if (!mask[i]) continue;
+        const int64_t c0 = X.coff[i], c1 = X.coff[i + 1], r0 = X.roff[i], r1 = X.roff[i + 1];
+        const int rpt = X.rpt[i];
+        const int cta = X.cta * rpt;
+        for (int64_t s = c0; s < c1; s += cta) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, c1), 0, rpt});
+        const int eq_end = (int)(r0 + X.m_eq[i]);
+        for (int64_t s = r0; s < r1; s += cta) sd.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, r1), eq_end, rpt});
+        ranges[i].eval_begin = (int)se.size();
+        for (int64_t s = r0; s < r1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, r1), eq_end << 1, 1});
+        for (int64_t s = c0; s < c1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, c1), 1, 1});
+        if (se.size() == (size_t)ranges[i].eval_begin) se.push_back({i, 0, 0, 0, 1});
+        ranges[i].eval_end = (int)se.size();
+    }
+    sa = sp;
+    sa.insert(sa.end(), sd.begin(), sd.end());
+}
+
+static int capture(uc_session &X, int gi);
+
+// Rebuild the tables for the LPs in `mask` and re-capture the graphs; the
+// stream must be idle.  Used when LPs finish (compaction) or are reset.
+static int retable(uc_session &X, const std::vector<char> &mask) {
+    std::vector<Seg> sp, sd, se, sa;
+    std::vector<InstRange> ranges;
+    build_tables(X, mask, sp, sd, se, sa, ranges);
+    const Layout &L = X.L;
+    auto up = [&](size_t off, const void *src, size_t bytes) -> int {
+        if (bytes) UC_CUDA(cudaMemcpyAsync(X.D + off, src, bytes, cudaMemcpyHostToDevice, X.s));
+        return UC_OK;
+    };
+    int rc = up(L.segs_p, sp.data(), sizeof(Seg) * sp.size());
+    if (!rc) rc = up(L.segs_d, sd.data(), sizeof(Seg) * sd.size());
+    if (!rc) rc = up(L.segs_e, se.data(), sizeof(Seg) * se.size());
+    if (!rc) rc = up(L.segs_a, sa.data(), sizeof(Seg) * sa.size());
+    if (!rc) rc = up(L.ranges, ranges.data(), sizeof(InstRange) * ranges.size());
+    if (rc) return rc;
+    X.n_sp = (int)sp.size(); X.n_sd = (int)sd.size(); X.n_se = (int)se.size(); X.n_sa = (int)sa.size();
+    X.tabled = mask;
+    X.retables++;
+    UC_CUDA(cudaStreamSynchronize(X.s));
+    if (X.o.use_graph) {
+        for (int gi = 0; gi < 2; gi++) {
+            if (X.exec[gi]) { cudaGraphExecDestroy(X.exec[gi]); X.exec[gi] = nullptr; }
+            if (X.graph[gi]) { cudaGraphDestroy(X.graph[gi]); X.graph[gi] = nullptr; }
+        }
+        for (int gi = 0; gi < (X.o.kernel_timing ? 2 : 1); gi++) {
+            int r2 = capture(X, gi);
+            if (r2) return r2;
+        }
+    }
+    return UC_OK;
+}
+
+static bool live_status(int st) { return st == RUNNING || st == NEEDS_INIT; }
 
 static int session_create(const PsData *const *Pp, const std::shared_ptr<const PsData> *owners, int k,
                           const uc_solve_opts &o, cudaStream_t user_stream, uc_session **out) {
@@ -792,6 +885,11 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     }
     X->kernel = 1;
     X->algo = o.algorithm;
+    if (o.cta_rows != 0 && o.cta_rows != 128 && o.cta_rows != 256 && o.cta_rows != 512) {
+        set_error("cta_rows must be 0, 128, 256 or 512");
+        return UC_EINVAL;
+    }
+    X->cta = o.cta_rows ? o.cta_rows : 256;
     X->vs = X->vb == 32 ? 4 : 8;
     X->P.assign(owners, owners + k);
     for (int i = 1; i < k; i++)
@@ -811,23 +909,22 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     // row indices are also stored shifted left by one bit in the evaluation table
     if (M >= (1LL << 30) || N >= INT32_MAX || Z >= INT32_MAX) { set_error("batch too large for int32 indices"); return UC_EINVAL; }
 
-    // CTA tables: every CTA works on a slice of one LP
-    std::vector<Seg> sp, sd, se, sa;
-    std::vector<InstRange> ranges(k);
+    X->rpt.assign(k, 1);
+    X->m_eq.assign(k, 0);
     for (int i = 0; i < k; i++) {
-        const int64_t c0 = X->coff[i], c1 = X->coff[i + 1], r0 = X->roff[i], r1 = X->roff[i + 1];
-        for (int64_t s = c0; s < c1; s += kThreads) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + kThreads, c1), 0});
-        const int eq_end = (int)(r0 + Pp[i]->m_eq);
-        for (int64_t s = r0; s < r1; s += kThreads) sd.push_back({i, (int)s, (int)std::min<int64_t>(s + kThreads, r1), eq_end});
-        ranges[i].eval_begin = (int)se.size();
-        for (int64_t s = r0; s < r1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, r1), eq_end << 1});
-        for (int64_t s = c0; s < c1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, c1), 1});
-        if (se.size() == (size_t)ranges[i].eval_begin) se.push_back({i, 0, 0, 0});
-        ranges[i].eval_end = (int)se.size();
+        const int r = (o.rows_per_thread && o.rows_per_thread[i]) ? o.rows_per_thread[i] : 1;
+        if (r != 1 && r != 2 && r != 4) { set_error("rows_per_thread must be 1, 2 or 4"); return UC_EINVAL; }
+        X->rpt[i] = r;
+        X->m_eq[i] = Pp[i]->m_eq;
     }
-    sa = sp;
-    sa.insert(sa.end(), sd.begin(), sd.end());
-    X->n_sp = (int)sp.size(); X->n_sd = (int)sd.size(); X->n_se = (int)se.size(); X->n_sa = (int)sa.size();
+    // CTA tables for every LP (their sizes are the capacities of the device tables)
+    std::vector<Seg> sp, sd, se, sa;
+    std::vector<InstRange> ranges;
+    std::vector<char> all(k, 1);
+    build_tables(*X, all, sp, sd, se, sa, ranges);
+    X->tabled = all;
+    X->n_sp = X->cap_sp = (int)sp.size(); X->n_sd = X->cap_sd = (int)sd.size();
+    X->n_se = X->cap_se = (int)se.size(); X->n_sa = X->cap_sa = (int)sa.size();
 
     Layout &L = X->L;
     size_t off = 0;
@@ -983,6 +1080,17 @@ static int session_reset(uc_session &X, int which) {
         X.active[i] = 1;
         X.h_status[i] = NEEDS_INIT;
     }
+    // the tables must hold every LP that is still iterating or about to start
+    std::vector<char> want(X.k, 0);
+    bool differ = false;
+    for (int i = 0; i < X.k; i++) {
+        want[i] = X.active[i] && live_status(X.h_status[i]);
+        differ |= want[i] && !X.tabled[i];
+    }
+    if (differ) {
+        int rc = retable(X, want);
+        if (rc) return rc;
+    }
     launch_eval(X, s, 0);
     X.launches += 3;
     UC_CUDA(cudaGetLastError());
@@ -1020,6 +1128,25 @@ static int session_run(uc_session &X, int max_replays) {
         const int gi = checked & 1;
         checked++;
         const bool done = all_done(X);
+        if (!done && X.o.use_graph) {
+            int live = 0, tab = 0;
+            std::vector<char> want(X.k, 0);
+            for (int i = 0; i < X.k; i++) {
+                want[i] = X.active[i] && live_status(((volatile int *)X.h_status)[i]);
+                live += want[i];
+                tab += X.tabled[i];
+            }
+            if (live > 0 && 4 * live <= 3 * tab) {
+                // drain the replay still in flight, then rebuild for the live LPs only
+                UC_CUDA(cudaStreamSynchronize(s));
+                checked = launched;
+                for (int i = 0; i < X.k; i++) want[i] = X.active[i] && live_status(((volatile int *)X.h_status)[i]);
+                if (!all_done(X)) {
+                    int rc = retable(X, want);
+                    if (rc) return rc;
+                }
+            }
+        }
         if (timing && !done) {
             float a = 0.f, c = 0.f;
             if (cudaEventElapsedTime(&a, X.tev[gi][0], X.tev[gi][1]) == cudaSuccess &&

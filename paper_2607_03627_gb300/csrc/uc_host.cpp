@@ -542,6 +542,7 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
         ps->raw = lp->d;
         int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u);
         if (rc) return rc;
+        ps->raw_reduced_val = ps->A.val;
         double qi = 0.0, ci = 0.0;
         for (double v : ps->q) qi = std::max(qi, std::fabs(v));
         for (double v : ps->c) ci = std::max(ci, std::fabs(v));
@@ -561,6 +562,58 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
         *out = new uc_presolved{ps};
     } catch (const std::bad_alloc &) {
         set_error("uc_presolve: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
+int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **out) {
+    if (!base || !lp || !out) { set_error("uc_presolve_reuse: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    const PsData &b = *base->d;
+    const RawLp &r0 = *b.raw, &r1 = *lp->d;
+    if (r0.A.rows != r1.A.rows || r0.A.cols != r1.A.cols || r0.m_eq != r1.m_eq ||
+        r0.A.rowptr != r1.A.rowptr || r0.A.colidx != r1.A.colidx || r0.A.val != r1.A.val) {
+        set_error("uc_presolve_reuse: the LP's matrix differs from the base LP's");
+        return UC_EINVAL;
+    }
+    try {
+        auto ps = std::make_shared<PsData>();
+        ps->raw = lp->d;
+        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u);
+        if (rc) return rc;
+        if (ps->col_map != b.col_map || ps->row_map != b.row_map || ps->A.val != b.raw_reduced_val) {
+            set_error("uc_presolve_reuse: presolve removed different rows or columns than for the base LP");
+            return UC_EINVAL;
+        }
+        double qi = 0.0, ci = 0.0;
+        for (double v : ps->q) qi = std::max(qi, std::fabs(v));
+        for (double v : ps->c) ci = std::max(ci, std::fabs(v));
+        ps->q_inf = qi;
+        ps->c_inf = ci;
+        // same reduced matrix: take the base's scaling, scaled matrices and step size
+        ps->A = b.A;
+        ps->AT = b.AT;
+        ps->A_val32 = b.A_val32;
+        ps->AT_val32 = b.AT_val32;
+        ps->raw_reduced_val = b.raw_reduced_val;
+        ps->Dr = b.Dr;
+        ps->Dc = b.Dc;
+        for (size_t i = 0; i < ps->q.size(); i++) ps->q[i] *= ps->Dr[i];
+        for (size_t j = 0; j < ps->c.size(); j++) {
+            ps->c[j] *= ps->Dc[j];
+            ps->l[j] /= ps->Dc[j];
+            ps->u[j] /= ps->Dc[j];
+        }
+        ps->norm_A = b.norm_A;
+        ps->eta = b.eta;
+        // same fixed-chunk sums as uc_presolve, so omega0 is bit-identical to a full presolve
+        const double cn = std::sqrt(sumsq(ps->c, 1)), qn = std::sqrt(sumsq(ps->q, 1));
+        ps->omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
+        ps->value_bits = b.value_bits;
+        *out = new uc_presolved{ps};
+    } catch (const std::bad_alloc &) {
+        set_error("uc_presolve_reuse: out of host memory");
         return UC_ENOMEM;
     }
     return UC_OK;

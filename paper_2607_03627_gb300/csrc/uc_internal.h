@@ -59,6 +59,7 @@ struct PsData {
     std::vector<double> xfix;              // raw n: value of fixed columns
     std::vector<double> l_tight, u_tight;  // raw n: bounds after presolve
     std::vector<RemovedRow> removed;
+    std::vector<double> raw_reduced_val;   // reduced matrix values before scaling
     double eta = 1.0, omega0 = 1.0, norm_A = 0.0, obj_const = 0.0;
     double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
     int value_bits = 64;

@@ -1,0 +1,201 @@
+"""Continuous-batching server for unit-commitment LP requests on one GPU.
+
+Requests share a grid and unit fleet and differ in load (day-ahead re-solves),
+so every request's scaled matrix is the base LP's.  The server keeps one
+device-resident session whose slots hold the base matrix; admitting a
+request replaces a free slot's right-hand side and bounds (uc_session_update_lp,
+no matrix upload), warm-starts it from the solved request with the nearest
+net-load vector, and resets just that slot while the other slots keep
+iterating.  Finished slots are harvested between short runs of CUDA-graph
+replays and refilled from the queue (continuous batching).  The number of
+slots is capped by an HBM budget.  Host presolve (uc_presolve_reuse: the
+base LP's scaling is reused) runs on a thread pool as requests arrive.
+
+Because every slot's arithmetic is independent and deterministic, a request
+returns the same iterates and solution alone or in the mix (tested).
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import binding as B
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    problem: object          # ucgen.UCProblem-like
+    arrival: float           # seconds after the stream starts
+    admitted: float = math.nan
+    finished: float = math.nan
+    status: int = 1
+    iters: int = 0
+    objective: float = math.nan
+    rel_kkt: float = math.nan
+    warm_from: int = -1
+    slot: int = -1
+    start_x: np.ndarray | None = None    # warm start actually used (scaled presolved)
+    start_y: np.ndarray | None = None
+    x: np.ndarray | None = None          # returned point (scaled presolved)
+    y: np.ndarray | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, base_problem, slots: int = 8, hbm_budget_gb: float = 150.0, tol: float = 1e-4,
+                 max_iter: int = 100_000, value_bits: int = 64, warm_start: bool = True,
+                 replays_per_step: int = 4, presolve_workers: int = 8, keep_solutions: bool = False):
+        self.tol = tol
+        self.warm_start = warm_start
+        self.replays = replays_per_step
+        self.keep = keep_solutions
+        self.base_lp = B.uc_build_lp(base_problem)
+        self.base_ps = B.uc_presolve(self.base_lp, value_bits=value_bits)
+        self.n, self.m, _, _ = B.uc_presolved_dims(self.base_ps)
+        # slots the HBM budget allows (bytes of a one-slot session, scaled)
+        probe = B.Session([self.base_ps], tol=tol, max_iter=max_iter)
+        per_slot = probe.device_bytes()
+        probe.close()
+        fit = max(1, int(hbm_budget_gb * 1e9 // per_slot))
+        self.slots = max(1, min(slots, fit))
+        self.bytes_per_slot = per_slot
+        self.sess = B.Session([self.base_ps] * self.slots, tol=tol, max_iter=max_iter)
+        self.pool = cf.ThreadPoolExecutor(max_workers=presolve_workers)
+        self.library: list[tuple[np.ndarray, np.ndarray, np.ndarray, int]] = []   # load, x, y, rid
+
+    def close(self):
+        self.sess.close()
+        self.pool.shutdown(wait=False)
+
+    def _presolve(self, req: Request):
+        lp = B.uc_build_lp(req.problem)
+        return B.uc_presolve_reuse(self.base_ps, lp)
+
+    def _nearest(self, load: np.ndarray):
+        if not self.library:
+            return None
+        d = [float(np.linalg.norm(load - L)) for L, _, _, _ in self.library]
+        j = int(np.argmin(d))
+        return self.library[j]
+
+    def serve(self, requests: list[Request], realtime: bool = True) -> dict:
+        """Serve the requests (arrival times relative to now); returns metrics."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        futures: dict[int, cf.Future] = {}
+        queue: list[Request] = []            # arrived, waiting for presolve / a slot
+        running: dict[int, Request] = {}     # slot -> request
+        free = list(range(self.slots))
+        done = 0
+        nxt = 0
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0) if realtime else None
+        sim_t = 0.0
+        gpu_busy = 0.0
+        while done < len(reqs):
+            now = clock() if realtime else sim_t
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                r = reqs[nxt]
+                futures[r.rid] = self.pool.submit(self._presolve, r)
+                queue.append(r)
+                nxt += 1
+            # admit in arrival order while slots are free and presolve is ready
+            while free and queue and futures[queue[0].rid].done():
+                r = queue.pop(0)
+                ps = futures.pop(r.rid).result()
+                slot = free.pop(0)
+                self.sess.update_lp(slot, ps)
+                load = np.ascontiguousarray(r.problem.load, dtype=np.float64).ravel()
+                near = self._nearest(load) if self.warm_start else None
+                if near is not None:
+                    self.sess.set_start(slot, near[1], near[2])
+                    r.warm_from = near[3]
+                    if self.keep:
+                        r.start_x, r.start_y = near[1].copy(), near[2].copy()
+                self.sess.reset(slot)
+                r.slot = slot
+                r.admitted = clock() if realtime else sim_t
+                r._ps = ps
+                r._load = load
+                running[slot] = r
+            if running:
+                g0 = time.perf_counter()
+                self.sess.run(self.replays)
+                g = time.perf_counter() - g0
+                gpu_busy += g
+                if not realtime:
+                    sim_t += g
+                for slot in list(running):
+                    st = self.sess.status(slot)
+                    if st == 2:
+                        continue
+                    r = running.pop(slot)
+                    res, rc = self.sess.result(slot)
+                    stats = B.uc_get_stats(res)
+                    r.finished = clock() if realtime else sim_t
+                    r.status = rc
+                    r.iters = stats["iters"]
+                    r.objective = stats["objective"]
+                    r.rel_kkt = max(stats["rel_primal"], stats["rel_dual"], stats["rel_gap"])
+                    x, y = B.uc_get_iterate(res, 2, self.n, self.m)
+                    if self.keep:
+                        r.x, r.y = x, y
+                    if rc == B.UC_OK:
+                        self.library.append((r._load, x, y, r.rid))
+                    del r._ps, r._load
+                    free.append(slot)
+                    done += 1
+            else:
+                # idle: wait for the next arrival or a presolve to finish
+                if realtime:
+                    waits = [reqs[nxt].arrival - now] if nxt < len(reqs) else []
+                    time.sleep(min([0.002] + [w for w in waits if w > 0]))
+                else:
+                    if queue:
+                        futures[queue[0].rid].result()
+                    elif nxt < len(reqs):
+                        sim_t = max(sim_t, reqs[nxt].arrival)
+        lat = np.array([r.latency for r in reqs])
+        span = max(r.finished for r in reqs) - min(r.arrival for r in reqs)
+        return {"requests": len(reqs), "slots": self.slots, "bytes_per_slot": self.bytes_per_slot,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "mean_latency_s": float(lat.mean()), "throughput_req_per_s": len(reqs) / span,
+                "makespan_s": span, "gpu_busy_s": gpu_busy,
+                "mean_iters": float(np.mean([r.iters for r in reqs])),
+                "warm_started": int(sum(r.warm_from >= 0 for r in reqs)),
+                "all_optimal": bool(all(r.status == B.UC_OK for r in reqs))}
+
+
+def sequential_baseline(requests: list[Request], base_problem, tol: float = 1e-4, max_iter: int = 100_000,
+                        value_bits: int = 64) -> dict:
+    """Plain one-at-a-time cold FP64 solves of the same requests in arrival
+    order (each starts when it has arrived and the previous one finished)."""
+    base_ps = B.uc_presolve(B.uc_build_lp(base_problem), value_bits=value_bits)
+    sess = B.Session([base_ps], tol=tol, max_iter=max_iter)
+    t = 0.0
+    lat = []
+    iters = []
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    for r in reqs:
+        ps = B.uc_presolve_reuse(base_ps, B.uc_build_lp(r.problem))
+        g0 = time.perf_counter()
+        sess.update_lp(0, ps)
+        sess.reset(0)
+        sess.run()
+        res, rc = sess.result(0)
+        g = time.perf_counter() - g0
+        iters.append(B.uc_get_stats(res)["iters"])
+        t = max(t, r.arrival) + g
+        lat.append(t - r.arrival)
+    sess.close()
+    lat = np.array(lat)
+    return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "throughput_req_per_s": len(reqs) / (t - reqs[0].arrival), "mean_iters": float(np.mean(iters)),
+            "note": "device time of cold solves replayed on a simulated clock; presolve not counted"}

@@ -1,0 +1,85 @@
+"""Autotuner for the row split of the iteration kernels.
+
+The iteration kernels give each thread `rows_per_thread` rows (1, 2 or 4) of
+one LP; the results do not depend on the choice, the speed does (more rows
+per thread means more independent loads in flight per thread but fewer
+CTAs).  The tuner times a few CUDA-graph replays of one representative LP of
+each size bucket (by nonzeros) for every choice and keeps the fastest, cached
+in a JSON file keyed by GPU name, bucket and value precision.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import binding as B
+
+CHOICES = (1, 2, 4)
+# nonzero-count buckets: [lo, hi)
+BUCKETS = ((0, 1 << 17), (1 << 17, 1 << 19), (1 << 19, 1 << 21), (1 << 21, 1 << 62))
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+
+
+def bucket_of(nnz: int) -> int:
+    for i, (lo, hi) in enumerate(BUCKETS):
+        if lo <= nnz < hi:
+            return i
+    return len(BUCKETS) - 1
+
+
+class Tuner:
+    def __init__(self, cache_path: str | None = DEFAULT_CACHE, trial_replays: int = 3):
+        self.cache_path = cache_path
+        self.trial_replays = trial_replays
+        self._lock = threading.Lock()
+        self.cache = {}
+        if cache_path and os.path.exists(cache_path):
+            try:
+                with open(cache_path) as f:
+                    self.cache = json.load(f)
+            except (OSError, ValueError):
+                self.cache = {}
+
+    @staticmethod
+    def _gpu_name() -> str:
+        import torch
+        return torch.cuda.get_device_name()
+
+    def key(self, nnz: int, value_bits: int) -> str:
+        return f"{self._gpu_name()}|bucket{bucket_of(nnz)}|fp{value_bits}"
+
+    def time_choice(self, ps, rpt: int) -> float:
+        """Milliseconds per PDHG iteration of `ps` with `rpt` rows per thread."""
+        import torch
+        n_eval = 64
+        sess = B.Session([ps], tol=0.0, max_iter=n_eval * self.trial_replays, rows_per_thread=[rpt])
+        sess.reset(-1)
+        sess.run()                       # warm-up (graph already captured)
+        s = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sess.reset(-1)
+        e0.record(s)
+        sess.run()
+        e1.record(s)
+        torch.cuda.synchronize()
+        sess.close()
+        return e0.elapsed_time(e1) / (n_eval * self.trial_replays)
+
+    def choose(self, ps, value_bits: int) -> int:
+        nnz = B.uc_presolved_dims(ps)[3]
+        k = self.key(nnz, value_bits)
+        with self._lock:
+            if k in self.cache:
+                return int(self.cache[k]["rows_per_thread"])
+        times = {r: self.time_choice(ps, r) for r in CHOICES}
+        best = min(times, key=times.get)
+        with self._lock:
+            self.cache[k] = {"rows_per_thread": best, "ms_per_iter": times, "nnz_sample": nnz}
+            if self.cache_path:
+                tmp = self.cache_path + f".tmp{os.getpid()}"
+                with open(tmp, "w") as f:
+                    json.dump(self.cache, f, indent=1)
+                os.replace(tmp, self.cache_path)
+        return best
