@@ -37,7 +37,11 @@ MAX_ITER = 100_000
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only for the device source it was taken on (sha256 of uc_device.cu).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, 6,049-bus LP, FP64 values, Halpern (profiles/pdhg_kernels_grid6049.md)
+    ("paper", "halpern", "k_primal"): {"src": "366872adccc224af", "bytes": (84.921600 + 5.372928) * 1e6},
+    ("paper", "halpern", "k_dual"): {"src": "366872adccc224af", "bytes": (63.294720 + 1.053184) * 1e6},
+}
 
 
 def _peaks():
@@ -180,7 +184,8 @@ def run_ours(args):
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
     sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True, spmv_kernel=args.spmv_kernel,
-                     algorithm=args.algorithm, restart_metric=args.restart_metric)
+                     algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
+                     reorder=not args.no_reorder)
 
     def solve_once():
         sess.reset(-1)
@@ -500,6 +505,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-kernel", type=int, default=0, help="0 default, 1 thread per row")
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
+    ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
+    ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

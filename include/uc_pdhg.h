@@ -98,6 +98,8 @@ typedef struct {
     double timeout_ms;           /* 0: none */
     const double *warm_x;        /* nullable [n] presolved-space primal start (scaled) */
     const double *warm_y;        /* nullable [m] presolved-space dual start (scaled) */
+    double warm_omega;           /* > 0: initial primal weight (e.g. the final omega of the solve the
+                                    warm start comes from); <= 0: omega0 of the presolve */
     uc_alloc_fn alloc;           /* nullable device allocator */
     uc_free_fn free;
     void *alloc_ctx;
@@ -107,6 +109,11 @@ typedef struct {
     const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or
                                     4 (default 1); results do not depend on it (autotuned per size
                                     bucket, so LPs of one launch may differ) */
+    int no_reorder;              /* 1: keep the LP's row/column order on the device (default: rows
+                                    and columns sorted by length within 1024-row windows so warps
+                                    see similar lengths; results come back in the LP's order) */
+    int no_pdl;                  /* 1: launch iteration kernels without programmatic dependent
+                                    launch (no overlap of consecutive kernels); default 0 */
     int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
                                     averaging with KKT restarts (both constant-step, see DESIGN) */
     int restart_metric;          /* Halpern restarts: 0 (default) weighted KKT of the map output,
@@ -209,7 +216,8 @@ int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *op
  *   uc_session_status     1 idle, 2 iterating, else the LP's final status
  *   uc_session_result     copy LP i's state out as a uc_result (LP becomes idle)
  *   uc_session_set_start  warm start of LP i (scaled presolved space, [n], [m];
- *                         NULL = zeros), used by the next reset
+ *                         NULL = zeros) and its initial primal weight (omega > 0;
+ *                         <= 0 keeps the presolve's omega0), used by the next reset
  *   uc_session_update_lp  replace slot i by an LP with the same scaled matrix
  *                         (e.g. the same grid and units with another load):
  *                         new q, c, l, u and scalars; the start point becomes
@@ -221,7 +229,7 @@ int uc_session_reset(uc_session *s, int i);
 int uc_session_run(uc_session *s, int max_replays, int *n_running);
 int uc_session_status(const uc_session *s, int i);
 int uc_session_result(uc_session *s, int i, uc_result **out);
-int uc_session_set_start(uc_session *s, int i, const double *x, const double *y);
+int uc_session_set_start(uc_session *s, int i, const double *x, const double *y, double omega);
 int uc_session_update_lp(uc_session *s, int i, const uc_presolved *ps);
 size_t uc_session_device_bytes(const uc_session *s);
 void uc_session_free(uc_session *s);

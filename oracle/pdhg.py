@@ -237,11 +237,14 @@ class HState:
     restarts: int = 0
 
 
-def halpern_initial_state(S, x0=None, y0=None, metric: str = "kkt") -> HState:
+def halpern_initial_state(S, x0=None, y0=None, metric: str = "kkt", omega0=None) -> HState:
+    """Start point clip(x0, l, u), y0 with y_I >= 0 (zeros by default); the
+    primal weight starts at omega0 when given (a warm start's weight), else
+    at S.omega0."""
     x = np.clip(np.zeros(S.A.shape[1]) if x0 is None else x0.copy(), S.l, S.u)
     y = np.zeros(S.A.shape[0]) if y0 is None else y0.copy()
     y[S.m_eq:] = np.maximum(y[S.m_eq:], 0.0)
-    omega = S.omega0
+    omega = S.omega0 if omega0 is None else float(omega0)
     if metric == "kkt":
         ra, _ = weighted(S, x, y, omega)
     else:
@@ -301,10 +304,11 @@ def halpern_evaluate(S, st: HState, U, tol: float):
 
 
 def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
-                  x0=None, y0=None, metric: str = "kkt", trace=None, trace_iters=()) -> Result:
+                  x0=None, y0=None, metric: str = "kkt", trace=None, trace_iters=(),
+                  omega0=None) -> Result:
     """Run the Halpern variant; ``trace(k, state)`` after every step k in trace_iters
     (after the evaluation when k is a multiple of n_eval)."""
-    st = halpern_initial_state(S, x0, y0, metric)
+    st = halpern_initial_state(S, x0, y0, metric, omega0)
     AT = S.A.T.tocsr()
     U = _unscaled_lp(S)
     trace_iters = set(trace_iters)

@@ -46,10 +46,10 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class uc_solve_opts(C.Structure):
     _fields_ = [("tol_rel_kkt", C.c_double), ("tol_abs_feas", C.c_double), ("max_iter", C.c_int),
                 ("n_eval", C.c_int), ("use_graph", C.c_int), ("kernel_timing", C.c_int),
-                ("timeout_ms", C.c_double), ("warm_x", _d), ("warm_y", _d),
+                ("timeout_ms", C.c_double), ("warm_x", _d), ("warm_y", _d), ("warm_omega", C.c_double),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("spmv_kernel", C.c_int), ("cta_rows", C.c_int), ("rows_per_thread", _P(C.c_int)),
-                ("algorithm", C.c_int),
+                ("no_reorder", C.c_int), ("no_pdl", C.c_int), ("algorithm", C.c_int),
                 ("restart_metric", C.c_int),
                 ("cancel", _P(C.c_int))]
 
@@ -97,7 +97,7 @@ _SIGS = {
     "uc_session_run": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int)]),
     "uc_session_status": (C.c_int, [C.c_void_p, C.c_int]),
     "uc_session_result": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_void_p)]),
-    "uc_session_set_start": (C.c_int, [C.c_void_p, C.c_int, _d, _d]),
+    "uc_session_set_start": (C.c_int, [C.c_void_p, C.c_int, _d, _d, C.c_double]),
     "uc_session_update_lp": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "uc_session_device_bytes": (C.c_size_t, [C.c_void_p]),
     "uc_session_free": (None, [C.c_void_p]),
@@ -289,10 +289,10 @@ def _torch_stream_and_allocator():
 
 
 def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use_graph: bool = True,
-               kernel_timing: bool = False, timeout_ms: float = 0.0, warm_x=None, warm_y=None,
+               kernel_timing: bool = False, timeout_ms: float = 0.0, warm_x=None, warm_y=None, warm_omega=0.0,
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
                restart_metric: str = "kkt", cta_rows: int = 0,
-               rows_per_thread=None) -> tuple[uc_solve_opts, list]:
+               rows_per_thread=None, pdl: bool = True, reorder: bool = True) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -302,8 +302,11 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.use_graph = int(bool(use_graph))
     o.kernel_timing = int(bool(kernel_timing))
     o.timeout_ms = float(timeout_ms)
+    o.warm_omega = float(warm_omega or 0.0)
     o.spmv_kernel = int(spmv_kernel)
     o.cta_rows = int(cta_rows)
+    o.no_pdl = 0 if pdl else 1
+    o.no_reorder = 0 if reorder else 1
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)
@@ -421,11 +424,11 @@ class Session:
             raise UCError(rc, "uc_session_result")
         return ResultHandle(out.value, keep=self.ps[i]), rc
 
-    def set_start(self, i: int, x=None, y=None):
+    def set_start(self, i: int, x=None, y=None, omega: float = 0.0):
         xa = _f64(x) if x is not None else None
         ya = _f64(y) if y is not None else None
-        _check(lib.uc_session_set_start(self.ptr, int(i), _ptr(xa, C.c_double), _ptr(ya, C.c_double)),
-               "uc_session_set_start")
+        _check(lib.uc_session_set_start(self.ptr, int(i), _ptr(xa, C.c_double), _ptr(ya, C.c_double),
+                                        float(omega or 0.0)), "uc_session_set_start")
 
     def update_lp(self, i: int, ps):
         _check(lib.uc_session_update_lp(self.ptr, int(i), ps.ptr), "uc_session_update_lp")

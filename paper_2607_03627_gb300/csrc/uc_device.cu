@@ -146,12 +146,24 @@ __device__ __forceinline__ void halpern_weights(const Bufs &b, const Scalars *S,
 // ---------------------------------------------------------------------------
 // iteration kernels (one thread per row of A^T or A)
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: an iteration kernel launched with the PDL
+// attribute may start while its predecessor (the other iteration kernel) is
+// still finishing.  Everything it reads before pdl_wait() was written two or
+// more launches earlier (every kernel triggers its dependent only after its
+// own wait), so only the predecessor's output -- the gathered vector -- is
+// read after the wait.  Without the attribute both calls are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr int kPre = 3;   // row entries whose index and value are loaded before the wait
+
 // ALGO = ALG_AVERAGE: x+ = clip(x - tau (c - A^T y), l, u), running sum of x+.
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
 // the last step of a block (and at the iteration limit).
+// at least 1280 resident threads per SM (51 registers) keep enough loads in flight
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+__global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
@@ -159,73 +171,115 @@ __global__ void __launch_bounds__(BS) k_primal(const Seg *__restrict__ segs, Buf
     const double tau = S->tau;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
+    double w = 0.0, w1 = 0.0;
+    if (ALGO == ALG_HALPERN) halpern_weights(b, S, it, w, w1);
+    bool waited = false;
     for (int t = 0; t < sg.rpt; t++) {
-    const int j = sg.begin + t * BS + threadIdx.x;
-    if (j >= sg.end) return;
-    const double xin = b.x[src][j];
-    const double cj = b.c[j];
-    const long long lk = b.lkey[j], uk = b.ukey[j];
-    const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : b.xa[j];
-    double acc = 0.0;
-    const int k1 = b.AT_rp[j + 1];
-    for (int kk = b.AT_rp[j]; kk < k1; kk++) acc += widen(v[kk]) * y[b.AT_ci[kk]];
-    const double xv = clip_keys(xin - tau * (cj - acc), lk, uk);
-    if (ALGO == ALG_AVERAGE) {
-        b.x[src ^ 1][j] = xv;
-        b.xsum[j] = aux + xv;
-    } else {
-        double w, w1;
-        halpern_weights(b, S, it, w, w1);
-        const double xb = 2.0 * xv - xin;
-        b.xsum[j] = xb;
-        b.x[src ^ 1][j] = w * xb + w1 * aux;
-        if (it == S->n_eval - 1 || k == S->max_iter - 1) b.xret[j] = xv;
+        const int j = sg.begin + t * BS + threadIdx.x;
+        if (j >= sg.end) break;
+        // independent of the dual kernel that precedes this one
+        const double xin = b.x[src][j];
+        const double cj = b.c[j];
+        const long long lk = b.lkey[j], uk = b.ukey[j];
+        const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : b.xa[j];
+        const int k0 = b.AT_rp[j], k1 = b.AT_rp[j + 1];
+        int ci[kPre];
+        double av[kPre];
+#pragma unroll
+        for (int q = 0; q < kPre; q++) {
+            ci[q] = 0;
+            av[q] = 0.0;
+            if (k0 + q < k1) { ci[q] = b.AT_ci[k0 + q]; av[q] = widen(v[k0 + q]); }
+        }
+        if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
+        double acc = 0.0;
+        // a step of the unrolled loop issues only if some lane of the warp needs it
+        const unsigned lanes = __activemask();
+#pragma unroll
+        for (int q = 0; q < kPre; q++) {
+            if (!__any_sync(lanes, k0 + q < k1)) break;
+            if (k0 + q < k1) acc = fma(av[q], y[ci[q]], acc);
+        }
+        for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(v[kk]), y[b.AT_ci[kk]], acc);
+        const double xv = clip_keys(fma(-tau, cj - acc, xin), lk, uk);
+        if (ALGO == ALG_AVERAGE) {
+            b.x[src ^ 1][j] = xv;
+            b.xsum[j] = aux + xv;
+        } else {
+            const double xb = fma(2.0, xv, -xin);
+            b.xsum[j] = xb;
+            b.x[src ^ 1][j] = fma(w, xb, w1 * aux);
+            if (it == S->n_eval - 1 || k == S->max_iter - 1) b.xret[j] = xv;
+        }
     }
-    }
+    if (!waited) { pdl_wait(); pdl_trigger(); }
 }
 
 // ALGO = ALG_AVERAGE: y+ = proj(y + sigma (q - A (2 x+ - x))), running sum.
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
     if (S->status != RUNNING || k >= S->max_iter) return;
     const double sigma = S->sigma;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    double w = 0.0, w1 = 0.0;
+    if (ALGO == ALG_HALPERN) halpern_weights(b, S, it, w, w1);
+    bool waited = false;
     for (int t = 0; t < sg.rpt; t++) {
-    const int i = sg.begin + t * BS + threadIdx.x;
-    if (i >= sg.end) return;
-    const double yin = b.y[src][i];
-    const double qi = b.q[i];
-    const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : b.ya[i];
-    double acc = 0.0;
-    const int k1 = b.A_rp[i + 1];
-    if (ALGO == ALG_AVERAGE) {
-        const double *__restrict__ xn = b.x[src ^ 1];
-        const double *__restrict__ xo = b.x[src];
-        for (int kk = b.A_rp[i]; kk < k1; kk++) {
-            const int j = b.A_ci[kk];
-            acc += widen(v[kk]) * (2.0 * xn[j] - xo[j]);
+        const int i = sg.begin + t * BS + threadIdx.x;
+        if (i >= sg.end) break;
+        const double yin = b.y[src][i];
+        const double qi = b.q[i];
+        const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : b.ya[i];
+        const int k0 = b.A_rp[i], k1 = b.A_rp[i + 1];
+        int ci[kPre];
+        double av[kPre];
+#pragma unroll
+        for (int q = 0; q < kPre; q++) {
+            ci[q] = 0;
+            av[q] = 0.0;
+            if (k0 + q < k1) { ci[q] = b.A_ci[k0 + q]; av[q] = widen(v[k0 + q]); }
         }
-    } else {
-        const double *__restrict__ xb = b.xsum;
-        for (int kk = b.A_rp[i]; kk < k1; kk++) acc += widen(v[kk]) * xb[b.A_ci[kk]];
+        if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
+        double acc = 0.0;
+        if (ALGO == ALG_AVERAGE) {
+            const double *__restrict__ xn = b.x[src ^ 1];
+            const double *__restrict__ xo = b.x[src];
+            const unsigned lanes = __activemask();
+#pragma unroll
+            for (int q = 0; q < kPre; q++) {
+                if (!__any_sync(lanes, k0 + q < k1)) break;
+                if (k0 + q < k1) acc = fma(av[q], fma(2.0, xn[ci[q]], -xo[ci[q]]), acc);
+            }
+            for (int kk = k0 + kPre; kk < k1; kk++) {
+                const int j = b.A_ci[kk];
+                acc = fma(widen(v[kk]), fma(2.0, xn[j], -xo[j]), acc);
+            }
+        } else {
+            const double *__restrict__ xb = b.xsum;
+            const unsigned lanes = __activemask();
+#pragma unroll
+            for (int q = 0; q < kPre; q++) {
+                if (!__any_sync(lanes, k0 + q < k1)) break;
+                if (k0 + q < k1) acc = fma(av[q], xb[ci[q]], acc);
+            }
+            for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(v[kk]), xb[b.A_ci[kk]], acc);
+        }
+        double yv = fma(sigma, qi - acc, yin);
+        if (i >= sg.aux) yv = nonneg(yv);
+        if (ALGO == ALG_AVERAGE) {
+            b.y[src ^ 1][i] = yv;
+            b.ysum[i] = aux + yv;
+        } else {
+            b.y[src ^ 1][i] = fma(w, fma(2.0, yv, -yin), w1 * aux);
+            if (it == S->n_eval - 1 || k == S->max_iter - 1) b.yret[i] = yv;
+        }
     }
-    double yv = yin + sigma * (qi - acc);
-    if (i >= sg.aux) yv = nonneg(yv);
-    if (ALGO == ALG_AVERAGE) {
-        b.y[src ^ 1][i] = yv;
-        b.ysum[i] = aux + yv;
-    } else {
-        double w, w1;
-        halpern_weights(b, S, it, w, w1);
-        b.y[src ^ 1][i] = w * (2.0 * yv - yin) + w1 * aux;
-        if (it == S->n_eval - 1 || k == S->max_iter - 1) b.yret[i] = yv;
-    }
-    }
+    if (!waited) { pdl_wait(); pdl_trigger(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -584,12 +638,17 @@ struct uc_session {
     int k = 0, vb = 64;
     int kernel = 1;               // 1 thread per row
     int cta = 256;                // rows (= threads) per CTA of the row kernels
+    bool pdl = true;              // programmatic dependent launch between iteration kernels
+    cudaError_t launch_err = cudaSuccess;
     int algo = 0;                 // ALG_HALPERN / ALG_AVERAGE (all LPs of a session)
     size_t vs = 8;
     uc_solve_opts o{};
     cudaStream_t s = nullptr;
     bool own_stream = false;
-    std::vector<std::shared_ptr<const uc::PsData>> P;
+    std::vector<std::shared_ptr<const uc::PsData>> P;    // LPs in their own (natural) order
+    std::vector<std::shared_ptr<const uc::PsData>> Pd;   // device views: rows/columns reordered
+    std::vector<std::vector<int32_t>> prow, pcol;        // device position -> natural index
+    bool reorder = true;
     std::vector<int64_t> roff, coff, zoff;
     int64_t M = 0, N = 0, Z = 0;
     int n_sp = 0, n_sd = 0, n_se = 0, n_sa = 0;
@@ -642,12 +701,95 @@ static void put(std::vector<char> &st, size_t off, const T *src, size_t count) {
     if (count) std::memcpy(st.data() + off, src, count * sizeof(T));
 }
 
-static Scalars make_scalars(const uc_session &X, const PsData &p) {
+// Device view of an LP.  Warps work on 32 consecutive rows and issue as many
+// FMA iterations as their longest row, so rows are reordered, within windows
+// of kOrderWindow rows, by decreasing length (stable; equality rows stay
+// first).  Columns are reordered the same way by their A^T row length.  Each
+// row keeps its entries in their original order, so every dot product sums in
+// the same order as in the natural layout.
+constexpr int kOrderWindow = 1024;
+
+static void window_order(const std::vector<int32_t> &rp, int begin, int end, std::vector<int32_t> &out) {
+    for (int w0 = begin; w0 < end; w0 += kOrderWindow) {
+        const int w1 = std::min(end, w0 + kOrderWindow);
+        const size_t base = out.size();
+        for (int r = w0; r < w1; r++) out.push_back(r);
+        std::stable_sort(out.begin() + base, out.end(), [&](int32_t a, int32_t b) {
+            return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+        });
+    }
+}
+
+static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsData> &src, bool reorder,
+                                                 std::vector<int32_t> &prow, std::vector<int32_t> &pcol) {
+    const PsData &p = *src;
+    const int m = p.m(), n = p.n();
+    prow.clear();
+    pcol.clear();
+    if (!reorder) {
+        prow.resize(m); pcol.resize(n);
+        for (int i = 0; i < m; i++) prow[i] = i;
+        for (int j = 0; j < n; j++) pcol[j] = j;
+        return src;
+    }
+    window_order(p.A.rowptr, 0, p.m_eq, prow);
+    window_order(p.A.rowptr, p.m_eq, m, prow);
+    window_order(p.AT.rowptr, 0, n, pcol);
+    std::vector<int32_t> irow(m), icol(n);
+    for (int i = 0; i < m; i++) irow[prow[i]] = i;
+    for (int j = 0; j < n; j++) icol[pcol[j]] = j;
+    auto d = std::make_shared<PsData>();
+    d->raw = p.raw;
+    d->m_eq = p.m_eq;
+    d->value_bits = p.value_bits;
+    d->eta = p.eta; d->omega0 = p.omega0; d->norm_A = p.norm_A; d->obj_const = p.obj_const;
+    d->q_inf = p.q_inf; d->c_inf = p.c_inf;
+    auto permute_csr = [](const Csr &A, const std::vector<float> &v32, const std::vector<int32_t> &order,
+                          const std::vector<int32_t> &inv_cols, Csr &out, std::vector<float> &o32) {
+        out.rows = A.rows; out.cols = A.cols;
+        out.rowptr.assign(1, 0);
+        out.colidx.reserve(A.colidx.size()); out.val.reserve(A.val.size());
+        if (!v32.empty()) o32.reserve(v32.size());
+        for (int32_t r : order) {
+            for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; k++) {
+                out.colidx.push_back(inv_cols[A.colidx[k]]);
+                out.val.push_back(A.val[k]);
+                if (!v32.empty()) o32.push_back(v32[k]);
+            }
+            out.rowptr.push_back((int32_t)out.colidx.size());
+        }
+    };
+    permute_csr(p.A, p.A_val32, prow, icol, d->A, d->A_val32);
+    permute_csr(p.AT, p.AT_val32, pcol, irow, d->AT, d->AT_val32);
+    auto gather = [](const std::vector<double> &v, const std::vector<int32_t> &order) {
+        std::vector<double> o(order.size());
+        for (size_t t = 0; t < order.size(); t++) o[t] = v[order[t]];
+        return o;
+    };
+    d->c = gather(p.c, pcol); d->l = gather(p.l, pcol); d->u = gather(p.u, pcol); d->Dc = gather(p.Dc, pcol);
+    d->q = gather(p.q, prow); d->Dr = gather(p.Dr, prow);
+    return d;
+}
+
+// natural-order vector -> device order (and back)
+static std::vector<double> to_device(const double *v, const std::vector<int32_t> &order) {
+    std::vector<double> o(order.size());
+    for (size_t t = 0; t < order.size(); t++) o[t] = v[order[t]];
+    return o;
+}
+static void to_natural(std::vector<double> &v, const std::vector<int32_t> &order) {
+    std::vector<double> o(v.size());
+    for (size_t t = 0; t < order.size(); t++) o[order[t]] = v[t];
+    v.swap(o);
+}
+
+static Scalars make_scalars(const uc_session &X, const PsData &p, double omega = 0.0) {
     Scalars s{};
+    const double w = omega > 0.0 ? omega : p.omega0;
     s.eta = p.eta;
-    s.omega = p.omega0;
-    s.tau = p.eta / p.omega0;
-    s.sigma = p.eta * p.omega0;
+    s.omega = w;
+    s.tau = p.eta / w;
+    s.sigma = p.eta * w;
     s.tol = X.o.tol_rel_kkt;
     s.q_inf = p.q_inf;
     s.c_inf = p.c_inf;
@@ -679,8 +821,14 @@ static void derived_vectors(const PsData &p, std::vector<double> &idc, std::vect
 }
 
 // start point, initial scalars and per-LP vectors of LP i into the staging image
-static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *wx, const double *wy) {
-    const PsData &p = *X.P[i];
+static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *wx_nat, const double *wy_nat,
+                     double womega) {
+    const PsData &p = *X.Pd[i];
+    std::vector<double> wxv, wyv;
+    if (wx_nat) wxv = to_device(wx_nat, X.pcol[i]);
+    if (wy_nat) wyv = to_device(wy_nat, X.prow[i]);
+    const double *wx = wx_nat ? wxv.data() : nullptr;
+    const double *wy = wy_nat ? wyv.data() : nullptr;
     const Layout &L = X.L;
     put(st, L.c + X.coff[i] * 8, p.c.data(), p.n());
     put(st, L.l + X.coff[i] * 8, p.l.data(), p.n());
@@ -704,7 +852,7 @@ static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *
         const double v = wy ? wy[r] : 0.0;
         y0[r] = r >= p.m_eq ? std::max(v, 0.0) : v;
     }
-    X.S_init[i] = make_scalars(X, p);
+    X.S_init[i] = make_scalars(X, p, womega);
     put(st, L.S_init + sizeof(Scalars) * i, &X.S_init[i], 1);
 }
 
@@ -717,15 +865,38 @@ static void launch_eval(uc_session &X, cudaStream_t s, int mode) {
 }
 
 // iteration kernels of the session's algorithm
+// Launch an iteration kernel; with `pdl` it may overlap the tail of the
+// iteration kernel before it (programmatic stream serialization).
+template <typename Kern>
+static cudaError_t launch_k(Kern kern, int grid, int block, cudaStream_t s, bool pdl, const Seg *segs,
+                            const Bufs &b, int it, int src) {
+    if (grid <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, segs, b, it, src);
+}
+
 template <int ALGO, int BS>
 static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
+    // the first primal kernel of a block follows the evaluation kernels: no overlap there
+    const bool pdl = X.pdl && (!primal || it > 0);
+    cudaError_t e;
     if (primal) {
-        if (X.vb == 32) k_primal<float, ALGO, BS><<<X.n_sp, BS, 0, s>>>(X.dsp, X.b, it, src);
-        else k_primal<double, ALGO, BS><<<X.n_sp, BS, 0, s>>>(X.dsp, X.b, it, src);
+        if (X.vb == 32) e = launch_k(k_primal<float, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
+        else e = launch_k(k_primal<double, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
     } else {
-        if (X.vb == 32) k_dual<float, ALGO, BS><<<X.n_sd, BS, 0, s>>>(X.dsd, X.b, it, src);
-        else k_dual<double, ALGO, BS><<<X.n_sd, BS, 0, s>>>(X.dsd, X.b, it, src);
+        if (X.vb == 32) e = launch_k(k_dual<float, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src);
+        else e = launch_k(k_dual<double, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src);
     }
+    if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
 }
 template <int ALGO>
 static void launch_iter_bs(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
@@ -772,6 +943,7 @@ static int capture(uc_session &X, int gi) {
     launch_eval(X, s, 1);
     launch_apply(X, s);
     if (err == cudaSuccess) err = cudaGetLastError();
+    if (err == cudaSuccess && X.launch_err != cudaSuccess) err = X.launch_err;
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s);
     cudaGraph_t g = nullptr;
@@ -799,6 +971,7 @@ static int launch_direct(uc_session &X) {
     launch_eval(X, s, 1);
     launch_apply(X, s);
     UC_CUDA(cudaGetLastError());
+    UC_CUDA(X.launch_err);
     UC_CUDA(cudaMemcpyAsync(X.h_status, b.status, sizeof(int) * X.k, cudaMemcpyDeviceToHost, s));
     return UC_OK;
 }
@@ -890,8 +1063,12 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         return UC_EINVAL;
     }
     X->cta = o.cta_rows ? o.cta_rows : 256;
+    X->pdl = o.no_pdl == 0;
     X->vs = X->vb == 32 ? 4 : 8;
     X->P.assign(owners, owners + k);
+    X->reorder = o.no_reorder == 0;
+    X->Pd.resize(k); X->prow.resize(k); X->pcol.resize(k);
+    for (int i = 0; i < k; i++) X->Pd[i] = device_view(X->P[i], X->reorder, X->prow[i], X->pcol[i]);
     for (int i = 1; i < k; i++)
         if (Pp[i]->value_bits != X->vb) { set_error("batched LPs must share value_bits"); return UC_EINVAL; }
     if (X->vb == 32)   // the kernels widen FP32 values by moving bits: normal, nonzero values only
@@ -959,7 +1136,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         int32_t *arp = (int32_t *)(st.data() + L.A_rp), *atrp = (int32_t *)(st.data() + L.AT_rp);
         int32_t *aci = (int32_t *)(st.data() + L.A_ci), *atci = (int32_t *)(st.data() + L.AT_ci);
         for (int i = 0; i < k; i++) {
-            const PsData &p = *Pp[i];
+            const PsData &p = *X->Pd[i];
             const int64_t ro = X->roff[i], co = X->coff[i], zo = X->zoff[i];
             for (int r = 0; r < p.m(); r++) arp[ro + r] = (int32_t)(p.A.rowptr[r] + zo);
             for (int c = 0; c < p.n(); c++) atrp[co + c] = (int32_t)(p.AT.rowptr[c] + zo);
@@ -974,7 +1151,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
                 put(st, L.A_v + zo * 8, p.A.val.data(), p.A.nnz());
                 put(st, L.AT_v + zo * 8, p.AT.val.data(), p.A.nnz());
             }
-            stage_lp(*X, st, i, (k == 1) ? o.warm_x : nullptr, (k == 1) ? o.warm_y : nullptr);
+            stage_lp(*X, st, i, (k == 1) ? o.warm_x : nullptr, (k == 1) ? o.warm_y : nullptr,
+                     (k == 1) ? o.warm_omega : 0.0);
         }
         arp[M] = (int32_t)Z;
         atrp[N] = (int32_t)Z;
@@ -1206,6 +1384,10 @@ static int session_result(uc_session &X, int i, uc_result **out) {
         for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
         if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
     }
+    if (X.reorder) {   // device order -> the LP's own order
+        for (auto *v : {&res->x_cur, &res->x_avg, &res->x_ret}) to_natural(*v, X.pcol[i]);
+        for (auto *v : {&res->y_cur, &res->y_avg, &res->y_ret}) to_natural(*v, X.prow[i]);
+    }
     uc_stats &o = res->stats;
     int status;
     if (S.status == OPTIMAL) status = UC_OK;
@@ -1237,13 +1419,15 @@ static int session_result(uc_session &X, int i, uc_result **out) {
 
 static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const PsData> &np) {
     if (i < 0 || i >= X.k) { set_error("LP index %d out of range", i); return UC_EINVAL; }
-    const PsData &a = *X.P[i], &c = *np;
-    if (a.n() != c.n() || a.m() != c.m() || a.m_eq != c.m_eq || a.A.rowptr != c.A.rowptr ||
-        a.A.colidx != c.A.colidx || a.A.val != c.A.val || a.value_bits != c.value_bits) {
+    const PsData &a = *X.P[i], &nn = *np;
+    if (a.n() != nn.n() || a.m() != nn.m() || a.m_eq != nn.m_eq || a.A.rowptr != nn.A.rowptr ||
+        a.A.colidx != nn.A.colidx || a.A.val != nn.A.val || a.value_bits != nn.value_bits) {
         set_error("update_lp: the new LP must have the same scaled matrix as slot %d", i);
         return UC_EINVAL;
     }
     X.P[i] = np;
+    X.Pd[i] = device_view(np, X.reorder, X.prow[i], X.pcol[i]);
+    const PsData &c = *X.Pd[i];
     const Layout &L = X.L;
     const size_t cx = X.coff[i] * 8, cy = X.roff[i] * 8;
     std::vector<double> x0(c.n()), y0(c.m(), 0.0);
@@ -1273,15 +1457,21 @@ static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const P
     return UC_OK;
 }
 
-static int session_set_start(uc_session &X, int i, const double *x, const double *y) {
+static int session_set_start(uc_session &X, int i, const double *x, const double *y, double omega) {
     if (i < 0 || i >= X.k) { set_error("LP index %d out of range", i); return UC_EINVAL; }
-    const PsData &p = *X.P[i];
+    const PsData &p = *X.Pd[i];
     std::vector<double> xs(p.n()), ys(p.m());
-    for (int c = 0; c < p.n(); c++) xs[c] = std::min(std::max(x ? x[c] : 0.0, p.l[c]), p.u[c]);
-    for (int r = 0; r < p.m(); r++) { const double v = y ? y[r] : 0.0; ys[r] = r >= p.m_eq ? std::max(v, 0.0) : v; }
+    for (int c = 0; c < p.n(); c++) xs[c] = std::min(std::max(x ? x[X.pcol[i][c]] : 0.0, p.l[c]), p.u[c]);
+    for (int r = 0; r < p.m(); r++) {
+        const double v = y ? y[X.prow[i][r]] : 0.0;
+        ys[r] = r >= p.m_eq ? std::max(v, 0.0) : v;
+    }
     if (p.n()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.x_init + X.coff[i] * 8, xs.data(), p.n() * 8, cudaMemcpyHostToDevice, X.s));
     if (p.m()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.y_init + X.roff[i] * 8, ys.data(), p.m() * 8, cudaMemcpyHostToDevice, X.s));
-    X.h2d += (long long)(p.n() + p.m()) * 8;
+    X.S_init[i] = make_scalars(X, p, omega);
+    UC_CUDA(cudaMemcpyAsync(X.D + X.L.S_init + sizeof(Scalars) * i, &X.S_init[i], sizeof(Scalars),
+                            cudaMemcpyHostToDevice, X.s));
+    X.h2d += (long long)(p.n() + p.m()) * 8 + (long long)sizeof(Scalars);
     UC_CUDA(cudaStreamSynchronize(X.s));
     return UC_OK;
 }
@@ -1471,9 +1661,9 @@ int uc_session_result(uc_session *s, int i, uc_result **out) {
     return dev::session_result(*s, i, out);
 }
 
-int uc_session_set_start(uc_session *s, int i, const double *x, const double *y) {
+int uc_session_set_start(uc_session *s, int i, const double *x, const double *y, double omega) {
     if (!s) { set_error("uc_session_set_start: null session"); return UC_EINVAL; }
-    return dev::session_set_start(*s, i, x, y);
+    return dev::session_set_start(*s, i, x, y, omega);
 }
 
 int uc_session_update_lp(uc_session *s, int i, const uc_presolved *ps) {

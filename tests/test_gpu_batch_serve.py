@@ -80,7 +80,7 @@ def test_server_results_same_alone_and_in_the_mix(B):
     base_ps = B.uc_presolve(B.uc_build_lp(base))
     for r in reqs:
         ps = B.uc_presolve_reuse(base_ps, B.uc_build_lp(r.problem))
-        res, rc = B.uc_solve(ps, tol=KKT_TOL, warm_x=r.start_x, warm_y=r.start_y)
+        res, rc = B.uc_solve(ps, tol=KKT_TOL, warm_x=r.start_x, warm_y=r.start_y, warm_omega=r.start_omega)
         assert rc == B.UC_OK
         n, m_, _, _ = B.uc_presolved_dims(ps)
         x, y = B.uc_get_iterate(res, 2, n, m_)

@@ -167,3 +167,23 @@ def test_other_evaluation_periods(B, n_eval, variant):
     ref = oracle_trace(S, [K], n_eval=n_eval, variant=variant)
     x, y, st = _device_iterates(B, ps, n, m, K, n_eval=n_eval, algorithm=variant)
     assert rel_inf(x, ref[K][0]) <= ITERATE_RTOL and rel_inf(y, ref[K][1]) <= ITERATE_RTOL
+
+
+def test_warm_start_with_primal_weight_per_iterate(B):
+    """A warm start (point and primal weight) follows the oracle iterate by iterate."""
+    P = ucgen.tiny(2)
+    raw, ps_o, S = oracle_pipeline(P)
+    ref_sol = pdhg.solve_halpern(S, tol=1e-3)                  # a nearby point and its weight
+    rng = np.random.default_rng(0)
+    x0 = ref_sol.x * (1 + 0.01 * rng.standard_normal(ref_sol.x.size))
+    y0 = ref_sol.y * (1 + 0.01 * rng.standard_normal(ref_sol.y.size))
+    ks = [1, 64, 65, 130, 200]
+    out = {}
+    pdhg.solve_halpern(S, tol=0.0, max_iter=200, x0=x0, y0=y0, omega0=ref_sol.omega,
+                       trace=lambda k, st: out.setdefault(k, (st.x.copy(), st.y.copy())), trace_iters=ks)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    for K in ks:
+        res, rc = B.uc_solve(ps, tol=0.0, max_iter=K, warm_x=x0, warm_y=y0, warm_omega=ref_sol.omega)
+        x, y = B.uc_get_iterate(res, 0, n, m)
+        assert rel_inf(x, out[K][0]) <= ITERATE_RTOL and rel_inf(y, out[K][1]) <= ITERATE_RTOL, K
