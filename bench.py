@@ -183,7 +183,13 @@ def run_ours(args):
     presolve_s = time.perf_counter() - t0
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
+    if args.rows_per_thread:
+        rpt = args.rows_per_thread
+    else:
+        from paper_2607_03627_gb300.tune import Tuner
+        rpt = Tuner().choose(ps, vbits)
     sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True, spmv_kernel=args.spmv_kernel,
+                     rows_per_thread=[rpt],
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
                      reorder=not args.no_reorder)
 
@@ -311,6 +317,7 @@ def run_ours(args):
             "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
                            tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
                            algorithm=args.algorithm, restart_metric=args.restart_metric,
+                           rows_per_thread=rpt,
                            l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
                            parallelism=f"replicas x{world}"),
             "time_to_1e-4_ms": ms_max / args.steps,
@@ -507,6 +514,8 @@ def main():
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")
+    ap.add_argument("--rows-per-thread", type=int, default=0,
+                    help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -309,6 +309,65 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[kPart], double 
     }
 }
 
+// Block reduction of an evaluation record with few FP64 instructions.  The 14
+// sum slots go through a transposed warp reduction: at each of five exchange
+// steps a lane keeps half of its remaining slots and adds its partner's copy,
+// so every FP64 add is useful (16 adds per lane instead of 5 per slot); lanes
+// 2s and 2s+1 end with the warp sum of slot s.  The 4 maxima of non-negative
+// values use integer shuffles.  Warps are combined in a fixed order, so the
+// result is deterministic.
+__host__ __device__ constexpr int sum_slot(int i) {   // i in [0, 14)
+    return (i < 7 ? 0 : kSlots) + ((i % 7) == 0 ? RP2 : (i % 7) == 1 ? QY : (i % 7) == 2 ? DY2 :
+                                   (i % 7) == 3 ? RD2 : (i % 7) == 4 ? CX : (i % 7) == 5 ? BND : DX2);
+}
+__host__ __device__ constexpr int max_slot(int i) {   // i in [0, 4)
+    return (i < 2 ? 0 : kSlots) + ((i & 1) ? RDU : RPU);
+}
+
+__device__ __forceinline__ void block_reduce_record(const double (&acc)[kPart], double *out) {
+    __shared__ double sh[kThreads / 32][16];
+    __shared__ long long shm[kThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 14; i++) v[i] = acc[sum_slot(i)];
+    v[14] = 0.0;
+    v[15] = 0.0;
+#pragma unroll
+    for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const double send = up ? v[i] : v[i + half];
+            const double keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    if ((lane & 1) == 0) sh[warp][lane >> 1] = v[0];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        long long m = __double_as_longlong(acc[max_slot(i)]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long other = __shfl_xor_sync(0xffffffffu, m, o);
+            m = other > m ? other : m;
+        }
+        if (lane == 0) shm[warp][i] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < 14) {
+        double t = sh[0][threadIdx.x];
+        for (int w = 1; w < kThreads / 32; w++) t += sh[w][threadIdx.x];
+        out[sum_slot(threadIdx.x)] = t;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+        const int i = threadIdx.x - 32;
+        long long m = shm[0][i];
+        for (int w = 1; w < kThreads / 32; w++) m = shm[w][i] > m ? shm[w][i] : m;
+        out[max_slot(i)] = __longlong_as_double(m);
+    }
+}
+
 // mode 0: the start point (candidate 0 only); mode 1: regular evaluation.
 // Average variant: candidate 0 = current point, candidate 1 = average since the
 // last restart.  Halpern variant: candidate 0 = the last map output
@@ -326,6 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                                   : (S->status == RUNNING && S->k_base + S->n_eval <= S->max_iter);
     if (live) {
         const bool halp = S->algo == ALG_HALPERN && mode == 1;
+        const bool fpr = halp && S->metric == METRIC_FPR;   // fixed-point residual terms needed
         const bool avg = S->algo == ALG_AVERAGE && mode == 1;
         const double inv_j = avg ? 1.0 / (double)(S->j_base + S->n_eval) : 0.0;
         const double *x = halp ? b.xret : b.x[0];
@@ -359,7 +419,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fabs(r1) * idr);
                     acc[kSlots + QY] += qi * y1;
                     acc[kSlots + DY2] += (y1 - yh) * (y1 - yh);
-                } else if (halp) {
+                } else if (fpr) {
                     const double d = b.y[1][i] - y0;
                     acc[kSlots + DY2] += d * d;
                 }
@@ -394,14 +454,14 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     a[BND] += bnd;
                     a[DX2] += (xs[cnd] - xh) * (xs[cnd] - xh);
                 }
-                if (halp) {
+                if (fpr) {
                     const double d = b.x[1][j] - x[j];
                     acc[kSlots + DX2] += d * d;
                 }
             }
         }
     }
-    block_reduce_store(acc, b.part + (size_t)blockIdx.x * kPart);
+    block_reduce_record(acc, b.part + (size_t)blockIdx.x * kPart);
 }
 
 // ---------------------------------------------------------------------------
@@ -1491,6 +1551,7 @@ static int max_replays(const uc_session &X) { return X.o.max_iter / X.o.n_eval +
 // 512 KiB) until the process exits.
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocSlots = 8;         // Slot entries RP2 .. BND (DY2 stays 0)
+constexpr int kNoAllocRows = 1024;       // rows or columns per CTA of the allocation-free evaluation
 constexpr int kNoAllocMaxBlocks = 8192;  // CTAs of 1024 rows or columns: n/1024 + m/1024 <= 8192
 
 static __device__ __align__(256) double g_kkt_scratch[kNoAllocMaxBlocks * kNoAllocSlots];
@@ -1526,7 +1587,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_partials_noalloc(uc_device_lp 
     for (int s = 0; s < kPart; s++) acc[s] = 0.0;
     const bool rows = (int)blockIdx.x < nbr;
     if (rows) {
-        const int b0 = blockIdx.x * kEvalRows, b1 = min(lp.m, b0 + kEvalRows);
+        const int b0 = blockIdx.x * kNoAllocRows, b1 = min(lp.m, b0 + kNoAllocRows);
         for (int i = b0 + threadIdx.x; i < b1; i += kThreads) {
             double ax = 0.0;
             for (int k = lp.A_rowptr[i]; k < lp.A_rowptr[i + 1]; k++) ax += lp.A_val[k] * x[lp.A_colidx[k]];
@@ -1538,7 +1599,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_partials_noalloc(uc_device_lp 
             acc[QY] += qi * y[i];
         }
     } else {
-        const int b0 = (blockIdx.x - nbr) * kEvalRows, b1 = min(lp.n, b0 + kEvalRows);
+        const int b0 = (blockIdx.x - nbr) * kNoAllocRows, b1 = min(lp.n, b0 + kNoAllocRows);
         for (int j = b0 + threadIdx.x; j < b1; j += kThreads) {
             double t = 0.0;
             for (int k = lp.AT_rowptr[j]; k < lp.AT_rowptr[j + 1]; k++) t += lp.AT_val[k] * y[lp.AT_colidx[k]];
@@ -1680,8 +1741,8 @@ int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, dou
         set_error("uc_kkt_noalloc: need n, m >= 0, 0 <= m_eq <= m and omega > 0");
         return UC_EINVAL;
     }
-    const int nbr = (lp->m + dev::kEvalRows - 1) / dev::kEvalRows;
-    const int nbc = (lp->n + dev::kEvalRows - 1) / dev::kEvalRows;
+    const int nbr = (lp->m + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
+    const int nbc = (lp->n + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
     const int nblocks = nbr + nbc;
     if (nblocks > dev::kNoAllocMaxBlocks) {
         set_error("uc_kkt_noalloc: LP too large for the fixed scratch: ceil(m/1024) + ceil(n/1024) = %d > %d "
