@@ -122,6 +122,21 @@ def _dist():
     return world, rank, local
 
 
+def reduce_max_sum(values, device):
+    """Across ranks: (max of values[0], sum of values[1]) -- the job's wall time
+    (slowest rank) and its total work.  Single process: returned as is."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(values[0]), float(values[1])
+    t = torch.tensor([float(values[0]), float(values[1])], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), tsum[1].item()
+
+
 def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
     """Algorithmic bytes of the primal (A^T y) and dual (A x-bar) kernels: the
     matrix and its row pointers once, every vector element touched once.
@@ -224,15 +239,7 @@ def run_ours(args):
     res, st = read_stats()
     # every timed solve starts cold from the same point and takes the same path
     iters = [st["iters"]] * args.steps
-    if world > 1:
-        t = torch.tensor([ms, float(sum(iters))], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_max, total_iters = tmax[0].item(), tsum[1].item()
-    else:
-        ms_max, total_iters = ms, float(sum(iters))
+    ms_max, total_iters = reduce_max_sum([ms, float(sum(iters))], "cuda")
     value = total_iters / (ms_max / 1e3)
     n_timed = st["timed_launches"] - nt0
     tp = (st["primal_kernel_ms"] * st["timed_launches"] - tp0) / max(n_timed, 1)
@@ -293,11 +300,7 @@ def run_ours(args):
             h2d += sol["stats"]["h2d_bytes"]
             d2h += sol["stats"]["d2h_bytes"]
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s, float(tot_it)], device="cuda", dtype=torch.float64)
-            tm = t.clone(); dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            ts = t.clone(); dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-            e2e_s, tot_it = tm[0].item(), ts[1].item()
+        e2e_s, tot_it = reduce_max_sum([e2e_s, float(tot_it)], "cuda")
         e2e = {"value": tot_it / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d // args.e2e_steps),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps),

@@ -121,6 +121,11 @@ __device__ __forceinline__ double nonneg(double v) {
 }
 
 __device__ __forceinline__ double widen(double v) { return v; }
+// read-once streams (matrix, row pointers, constant vectors, the input iterate)
+// are loaded evict-first so that the vector the previous kernel just wrote,
+// which this kernel gathers at random, stays in L2
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 __device__ __forceinline__ double widen(float f) {
     const unsigned long long u = __float_as_uint(f);
     const unsigned long long bits = ((u & 0x80000000ull) << 32) | (((u & 0x7fffffffull) << 29) + (896ull << 52));
@@ -178,18 +183,18 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict_
         const int j = sg.begin + t * BS + threadIdx.x;
         if (j >= sg.end) break;
         // independent of the dual kernel that precedes this one
-        const double xin = b.x[src][j];
-        const double cj = b.c[j];
-        const long long lk = b.lkey[j], uk = b.ukey[j];
-        const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : b.xa[j];
-        const int k0 = b.AT_rp[j], k1 = b.AT_rp[j + 1];
+        const double xin = ld_stream(b.x[src] + j);
+        const double cj = ld_stream(b.c + j);
+        const long long lk = ld_stream(b.lkey + j), uk = ld_stream(b.ukey + j);
+        const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : ld_stream(b.xa + j);
+        const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
         int ci[kPre];
         double av[kPre];
 #pragma unroll
         for (int q = 0; q < kPre; q++) {
             ci[q] = 0;
             av[q] = 0.0;
-            if (k0 + q < k1) { ci[q] = b.AT_ci[k0 + q]; av[q] = widen(v[k0 + q]); }
+            if (k0 + q < k1) { ci[q] = ld_stream(b.AT_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
         }
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
         double acc = 0.0;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict_
             if (!__any_sync(lanes, k0 + q < k1)) break;
             if (k0 + q < k1) acc = fma(av[q], y[ci[q]], acc);
         }
-        for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(v[kk]), y[b.AT_ci[kk]], acc);
+        for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), y[ld_stream(b.AT_ci + kk)], acc);
         const double xv = clip_keys(fma(-tau, cj - acc, xin), lk, uk);
         if (ALGO == ALG_AVERAGE) {
             b.x[src ^ 1][j] = xv;
@@ -232,17 +237,17 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ 
     for (int t = 0; t < sg.rpt; t++) {
         const int i = sg.begin + t * BS + threadIdx.x;
         if (i >= sg.end) break;
-        const double yin = b.y[src][i];
-        const double qi = b.q[i];
-        const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : b.ya[i];
-        const int k0 = b.A_rp[i], k1 = b.A_rp[i + 1];
+        const double yin = ld_stream(b.y[src] + i);
+        const double qi = ld_stream(b.q + i);
+        const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : ld_stream(b.ya + i);
+        const int k0 = ld_stream(b.A_rp + i), k1 = ld_stream(b.A_rp + i + 1);
         int ci[kPre];
         double av[kPre];
 #pragma unroll
         for (int q = 0; q < kPre; q++) {
             ci[q] = 0;
             av[q] = 0.0;
-            if (k0 + q < k1) { ci[q] = b.A_ci[k0 + q]; av[q] = widen(v[k0 + q]); }
+            if (k0 + q < k1) { ci[q] = ld_stream(b.A_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
         }
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
         double acc = 0.0;
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ 
                 if (!__any_sync(lanes, k0 + q < k1)) break;
                 if (k0 + q < k1) acc = fma(av[q], xb[ci[q]], acc);
             }
-            for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(v[kk]), xb[b.A_ci[kk]], acc);
+            for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), xb[ld_stream(b.A_ci + kk)], acc);
         }
         double yv = fma(sigma, qi - acc, yin);
         if (i >= sg.aux) yv = nonneg(yv);
