@@ -38,9 +38,12 @@ MAX_ITER = 100_000
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only for the device source it was taken on (sha256 of uc_device.cu).
 NCU_TRAFFIC = {
-    # ncu --set full, 6,049-bus LP, FP64 values, Halpern (profiles/pdhg_kernels_grid6049.md)
-    ("paper", "halpern", "k_primal"): {"src": "366872adccc224af", "bytes": (84.921600 + 5.372928) * 1e6},
-    ("paper", "halpern", "k_dual"): {"src": "366872adccc224af", "bytes": (63.294720 + 1.053184) * 1e6},
+    # ncu --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern,
+    # 2 rows per thread (profiles/pdhg_kernels_grid6049.md)
+    ("paper", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "bytes": 69867520 + 1521152},
+    ("paper", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "bytes": 48262144 + 534528},
+    ("paper-fp32", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "bytes": 59236864 + 352000},
+    ("paper-fp32", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "bytes": 37596672 + 81408},
 }
 
 
@@ -198,13 +201,13 @@ def run_ours(args):
     presolve_s = time.perf_counter() - t0
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
-    if args.rows_per_thread:
-        rpt = args.rows_per_thread
+    if args.rows_per_thread or args.cta_rows:
+        rpt, cta = args.rows_per_thread or 1, args.cta_rows
     else:
         from paper_2607_03627_gb300.tune import Tuner
-        rpt = Tuner().choose(ps, vbits)
+        cta, rpt = Tuner().choose_pair(ps, vbits)
     sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True, spmv_kernel=args.spmv_kernel,
-                     rows_per_thread=[rpt],
+                     rows_per_thread=[rpt], cta_rows=cta,
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
                      reorder=not args.no_reorder)
 
@@ -320,7 +323,7 @@ def run_ours(args):
             "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
                            tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
                            algorithm=args.algorithm, restart_metric=args.restart_metric,
-                           rows_per_thread=rpt,
+                           rows_per_thread=rpt, cta_rows=cta or 128,
                            l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
                            parallelism=f"replicas x{world}"),
             "time_to_1e-4_ms": ms_max / args.steps,
@@ -517,6 +520,7 @@ def main():
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")
+    ap.add_argument("--cta-rows", type=int, default=0, help="threads per CTA of the iteration kernels (0: 256)")
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])

@@ -104,7 +104,7 @@ typedef struct {
     uc_free_fn free;
     void *alloc_ctx;
     int spmv_kernel;             /* iteration kernels: 0 or 1, one thread per row (the only variant) */
-    int cta_rows;                /* threads per CTA of the iteration kernels: 0 (default 256), 128,
+    int cta_rows;                /* threads per CTA of the iteration kernels: 0 (default 128), 128,
                                     256 or 512; results do not depend on it (tuning knob) */
     const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or
                                     4 (default 1); results do not depend on it (autotuned per size

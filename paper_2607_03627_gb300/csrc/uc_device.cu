@@ -702,7 +702,7 @@ struct Layout {
 struct uc_session {
     int k = 0, vb = 64;
     int kernel = 1;               // 1 thread per row
-    int cta = 256;                // rows (= threads) per CTA of the row kernels
+    int cta = 128;                // rows (= threads) per CTA of the row kernels
     bool pdl = true;              // programmatic dependent launch between iteration kernels
     cudaError_t launch_err = cudaSuccess;
     int algo = 0;                 // ALG_HALPERN / ALG_AVERAGE (all LPs of a session)
@@ -1127,7 +1127,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         set_error("cta_rows must be 0, 128, 256 or 512");
         return UC_EINVAL;
     }
-    X->cta = o.cta_rows ? o.cta_rows : 256;
+    X->cta = o.cta_rows ? o.cta_rows : 128;
     X->pdl = o.no_pdl == 0;
     X->vs = X->vb == 32 ? 4 : 8;
     X->P.assign(owners, owners + k);

@@ -16,6 +16,7 @@ import threading
 from . import binding as B
 
 CHOICES = (1, 2, 4)
+CTA_CHOICES = (128, 256)
 # nonzero-count buckets: [lo, hi)
 BUCKETS = ((0, 1 << 17), (1 << 17, 1 << 19), (1 << 19, 1 << 21), (1 << 21, 1 << 62))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
@@ -49,11 +50,13 @@ class Tuner:
     def key(self, nnz: int, value_bits: int) -> str:
         return f"{self._gpu_name()}|bucket{bucket_of(nnz)}|fp{value_bits}"
 
-    def time_choice(self, ps, rpt: int) -> float:
-        """Milliseconds per PDHG iteration of `ps` with `rpt` rows per thread."""
+    def time_choice(self, ps, rpt: int, cta: int = 0) -> float:
+        """Milliseconds per PDHG iteration of `ps` with `rpt` rows per thread
+        and `cta` threads per CTA (0: the library default)."""
         import torch
         n_eval = 64
-        sess = B.Session([ps], tol=0.0, max_iter=n_eval * self.trial_replays, rows_per_thread=[rpt])
+        sess = B.Session([ps], tol=0.0, max_iter=n_eval * self.trial_replays, rows_per_thread=[rpt],
+                         cta_rows=cta)
         sess.reset(-1)
         sess.run()                       # warm-up (graph already captured)
         s = torch.cuda.current_stream()
@@ -77,6 +80,26 @@ class Tuner:
         best = min(times, key=times.get)
         with self._lock:
             self.cache[k] = {"rows_per_thread": best, "ms_per_iter": times, "nnz_sample": nnz}
+            if self.cache_path:
+                tmp = self.cache_path + f".tmp{os.getpid()}"
+                with open(tmp, "w") as f:
+                    json.dump(self.cache, f, indent=1)
+                os.replace(tmp, self.cache_path)
+        return best
+
+    def choose_pair(self, ps, value_bits: int) -> tuple[int, int]:
+        """(threads per CTA, rows per thread) for a session holding `ps` alone."""
+        nnz = B.uc_presolved_dims(ps)[3]
+        k = "pair|" + self.key(nnz, value_bits)
+        with self._lock:
+            if k in self.cache:
+                e = self.cache[k]
+                return int(e["cta_rows"]), int(e["rows_per_thread"])
+        times = {(c, r): self.time_choice(ps, r, c) for c in CTA_CHOICES for r in CHOICES if r <= 2}
+        best = min(times, key=times.get)
+        with self._lock:
+            self.cache[k] = {"cta_rows": best[0], "rows_per_thread": best[1],
+                             "ms_per_iter": {f"{c}x{r}": t for (c, r), t in times.items()}, "nnz_sample": nnz}
             if self.cache_path:
                 tmp = self.cache_path + f".tmp{os.getpid()}"
                 with open(tmp, "w") as f:
