@@ -36,14 +36,15 @@ TOL = 1e-4
 MAX_ITER = 100_000
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
-# only for the device source it was taken on (sha256 of uc_device.cu).
+# only for the device source it was taken on (sha256 of uc_device.cu) and the
+# launch shape (threads per CTA, rows per thread) it was taken with.
 NCU_TRAFFIC = {
     # ncu --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern,
     # 2 rows per thread (profiles/pdhg_kernels_grid6049.md)
-    ("paper", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "bytes": 69867520 + 1521152},
-    ("paper", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "bytes": 48262144 + 534528},
-    ("paper-fp32", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "bytes": 59236864 + 352000},
-    ("paper-fp32", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "bytes": 37596672 + 81408},
+    ("paper", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 69867520 + 1521152},
+    ("paper", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 48262144 + 534528},
+    ("paper-fp32", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 59236864 + 352000},
+    ("paper-fp32", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 37596672 + 81408},
 }
 
 
@@ -272,7 +273,7 @@ def run_ours(args):
     main = dk["alu_fp64"] if bound == "alu" else dk["hbm"]
     traffic = None
     rec = NCU_TRAFFIC.get((args.config, args.algorithm, dom))
-    if rec and rec["src"] == _src_hash():
+    if rec and rec["src"] == _src_hash() and tuple(rec["launch"]) == (cta or 128, rpt):
         traffic = rec["bytes"]
     roofline = {"bound": bound, "kernel": dom, "achieved": main["achieved"], "peak": main["peak"],
                 "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
