@@ -94,7 +94,8 @@ typedef struct {
     int max_iter;                /* iteration limit (default 100000, Sec. II-D) */
     int n_eval;                  /* iterations between KKT / restart evaluations (default 64, even) */
     int use_graph;               /* 1: replay CUDA graphs of n_eval iterations (default 1) */
-    int kernel_timing;           /* 1: time one primal and one dual kernel per replay with events */
+    int kernel_timing;           /* 1: time the primal and dual kernel of the middle iteration of every
+                                    replay with events (graph path only) */
     double timeout_ms;           /* 0: none */
     const double *warm_x;        /* nullable [n] presolved-space primal start (scaled) */
     const double *warm_y;        /* nullable [m] presolved-space dual start (scaled) */

@@ -166,28 +166,26 @@ constexpr int kPre = 3;   // row entries whose index and value are loaded before
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
 // the last step of a block (and at the iteration limit).
-// at least 1280 resident threads per SM (51 registers) keep enough loads in flight
+// 1152 resident threads per SM (56 registers for 128-thread CTAs): measured a
+// little faster than 1280 threads at 48 registers, which spilled
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+__global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
     if (S->status != RUNNING || k >= S->max_iter) return;
-    const double tau = S->tau;
+    const bool keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
-    double w = 0.0, w1 = 0.0;
-    if (ALGO == ALG_HALPERN) halpern_weights(b, S, it, w, w1);
     bool waited = false;
     for (int t = 0; t < sg.rpt; t++) {
         const int j = sg.begin + t * BS + threadIdx.x;
         if (j >= sg.end) break;
         // independent of the dual kernel that precedes this one
+        const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
         const double xin = ld_stream(b.x[src] + j);
-        const double cj = ld_stream(b.c + j);
         const long long lk = ld_stream(b.lkey + j), uk = ld_stream(b.ukey + j);
         const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : ld_stream(b.xa + j);
-        const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
         int ci[kPre];
         double av[kPre];
 #pragma unroll
@@ -196,8 +194,9 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict_
             av[q] = 0.0;
             if (k0 + q < k1) { ci[q] = ld_stream(b.AT_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
         }
+        // the accumulator starts at -c, so it ends at A^T y - c
+        double acc = -ld_stream(b.c + j);
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
-        double acc = 0.0;
         // a step of the unrolled loop issues only if some lane of the warp needs it
         const unsigned lanes = __activemask();
 #pragma unroll
@@ -206,15 +205,17 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict_
             if (k0 + q < k1) acc = fma(av[q], y[ci[q]], acc);
         }
         for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), y[ld_stream(b.AT_ci + kk)], acc);
-        const double xv = clip_keys(fma(-tau, cj - acc, xin), lk, uk);
+        const double xv = clip_keys(fma(S->tau, acc, xin), lk, uk);
         if (ALGO == ALG_AVERAGE) {
             b.x[src ^ 1][j] = xv;
             b.xsum[j] = aux + xv;
         } else {
+            double w, w1;
+            halpern_weights(b, S, it, w, w1);
             const double xb = fma(2.0, xv, -xin);
             b.xsum[j] = xb;
             b.x[src ^ 1][j] = fma(w, xb, w1 * aux);
-            if (it == S->n_eval - 1 || k == S->max_iter - 1) b.xret[j] = xv;
+            if (keep) b.xret[j] = xv;
         }
     }
     if (!waited) { pdl_wait(); pdl_trigger(); }
@@ -224,23 +225,20 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_primal(const Seg *__restrict_
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+__global__ void __launch_bounds__(BS, 1152 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
     if (S->status != RUNNING || k >= S->max_iter) return;
-    const double sigma = S->sigma;
+    const bool keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
-    double w = 0.0, w1 = 0.0;
-    if (ALGO == ALG_HALPERN) halpern_weights(b, S, it, w, w1);
     bool waited = false;
     for (int t = 0; t < sg.rpt; t++) {
         const int i = sg.begin + t * BS + threadIdx.x;
         if (i >= sg.end) break;
-        const double yin = ld_stream(b.y[src] + i);
-        const double qi = ld_stream(b.q + i);
-        const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : ld_stream(b.ya + i);
         const int k0 = ld_stream(b.A_rp + i), k1 = ld_stream(b.A_rp + i + 1);
+        const double yin = ld_stream(b.y[src] + i);
+        const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : ld_stream(b.ya + i);
         int ci[kPre];
         double av[kPre];
 #pragma unroll
@@ -249,8 +247,9 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ 
             av[q] = 0.0;
             if (k0 + q < k1) { ci[q] = ld_stream(b.A_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
         }
+        // the accumulator starts at -q, so it ends at A x - q
+        double acc = -ld_stream(b.q + i);
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
-        double acc = 0.0;
         if (ALGO == ALG_AVERAGE) {
             const double *__restrict__ xn = b.x[src ^ 1];
             const double *__restrict__ xo = b.x[src];
@@ -274,14 +273,16 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ 
             }
             for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), xb[ld_stream(b.A_ci + kk)], acc);
         }
-        double yv = fma(sigma, qi - acc, yin);
+        double yv = fma(-S->sigma, acc, yin);
         if (i >= sg.aux) yv = nonneg(yv);
         if (ALGO == ALG_AVERAGE) {
             b.y[src ^ 1][i] = yv;
             b.ysum[i] = aux + yv;
         } else {
+            double w, w1;
+            halpern_weights(b, S, it, w, w1);
             b.y[src ^ 1][i] = fma(w, fma(2.0, yv, -yin), w1 * aux);
-            if (it == S->n_eval - 1 || k == S->max_iter - 1) b.yret[i] = yv;
+            if (keep) b.yret[i] = yv;
         }
     }
     if (!waited) { pdl_wait(); pdl_trigger(); }
@@ -997,13 +998,16 @@ static int capture(uc_session &X, int gi) {
     auto rec = [&](int e) {
         if (timing && err == cudaSuccess) err = cudaEventRecordWithFlags(X.tev[gi][e], s, cudaEventRecordExternal);
     };
+    // the timed pair is a mid-block iteration: steady-state L2 contents, and
+    // only the event nodes around it break the programmatic overlap
+    const int timed_it = X.o.n_eval / 2;
     for (int it = 0; it < X.o.n_eval; it++) {
         const int src = it & 1;
-        if (it == 0) rec(0);
+        if (it == timed_it) rec(0);
         if (X.n_sp) launch_primal(X, s, it, src);
-        if (it == 0) rec(1);
+        if (it == timed_it) rec(1);
         if (X.n_sd) launch_dual(X, s, it, src);
-        if (it == 0) rec(2);
+        if (it == timed_it) rec(2);
     }
     launch_eval(X, s, 1);
     launch_apply(X, s);
