@@ -208,6 +208,7 @@ def run_ours(args):
         from paper_2607_03627_gb300.tune import Tuner
         cta, rpt = Tuner().choose_pair(ps, vbits)
     sess = B.Session([ps], tol=TOL, max_iter=args.max_iter, kernel_timing=True, spmv_kernel=args.spmv_kernel,
+                     stages=args.stages,
                      rows_per_thread=[rpt], cta_rows=cta,
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
                      reorder=not args.no_reorder)
@@ -517,7 +518,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spmv-kernel", type=int, default=0, help="0 default, 1 thread per row")
+    ap.add_argument("--spmv-kernel", type=int, default=0,
+                    help="0 default (thread per row), 1 thread per row, 2 staged")
+    ap.add_argument("--stages", type=int, default=0, help="staged kernels: chunks in flight per CTA (0: 2)")
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")

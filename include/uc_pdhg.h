@@ -104,7 +104,11 @@ typedef struct {
     uc_alloc_fn alloc;           /* nullable device allocator */
     uc_free_fn free;
     void *alloc_ctx;
-    int spmv_kernel;             /* iteration kernels: 0 or 1, one thread per row (the only variant) */
+    int spmv_kernel;             /* iteration kernels: 0 (default) or 1, one thread per row; 2 staged:
+                                    persistent CTAs that copy each 128-row chunk's matrix rows and
+                                    vectors into shared memory ahead of use (Halpern only, rows of at
+                                    most 640 entries, else UC_EINVAL).  All variants give identical
+                                    iterates. */
     int cta_rows;                /* threads per CTA of the iteration kernels: 0 (default 128), 128,
                                     256 or 512; results do not depend on it (tuning knob) */
     const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or
@@ -116,12 +120,14 @@ typedef struct {
     int no_pdl;                  /* 1: launch iteration kernels without programmatic dependent
                                     launch (no overlap of consecutive kernels); default 0 */
     int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
-                                    averaging with KKT restarts (both constant-step, see DESIGN) */
+                                    averaging with KKT restarts (both with constant step sizes) */
     int restart_metric;          /* Halpern restarts: 0 (default) weighted KKT of the map output,
                                     1 fixed-point residual of the last step */
     const volatile int *cancel;  /* nullable; a nonzero value (set from another thread) stops the
                                     solve at its next replay boundary with UC_ECANCELLED -- the
                                     "terminate the other solver" step of Alg. 1 */
+    int stages;                  /* staged kernels: chunks in flight per CTA, 2..8 (0: default 2);
+                                    results do not depend on it (tuning knob) */
 } uc_solve_opts;
 
 typedef struct {

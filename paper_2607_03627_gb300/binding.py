@@ -51,7 +51,7 @@ class uc_solve_opts(C.Structure):
                 ("spmv_kernel", C.c_int), ("cta_rows", C.c_int), ("rows_per_thread", _P(C.c_int)),
                 ("no_reorder", C.c_int), ("no_pdl", C.c_int), ("algorithm", C.c_int),
                 ("restart_metric", C.c_int),
-                ("cancel", _P(C.c_int))]
+                ("cancel", _P(C.c_int)), ("stages", C.c_int)]
 
 
 class uc_device_lp(C.Structure):
@@ -292,7 +292,8 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
                kernel_timing: bool = False, timeout_ms: float = 0.0, warm_x=None, warm_y=None, warm_omega=0.0,
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
                restart_metric: str = "kkt", cta_rows: int = 0,
-               rows_per_thread=None, pdl: bool = True, reorder: bool = True) -> tuple[uc_solve_opts, list]:
+               rows_per_thread=None, pdl: bool = True, reorder: bool = True,
+               stages: int = 0) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -307,6 +308,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.cta_rows = int(cta_rows)
     o.no_pdl = 0 if pdl else 1
     o.no_reorder = 0 if reorder else 1
+    o.stages = int(stages)
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)

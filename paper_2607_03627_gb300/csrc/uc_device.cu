@@ -31,6 +31,7 @@
 #include <cstring>
 #include <limits>
 #include <mutex>
+#include <queue>
 #include <vector>
 
 #include "uc_internal.h"
@@ -44,7 +45,8 @@ constexpr int kSlots = 9;          // reduction slots per candidate
 constexpr int kPart = 2 * kSlots;  // per-block partial record (current, average)
 
 enum Slot { RP2 = 0, RPU, QY, DY2, RD2, RDU, CX, BND, DX2 };
-enum Status { RUNNING = 0, OPTIMAL = 1, ITER_LIMIT = 2, NUMERIC = 3, NEEDS_INIT = 4 };
+enum Status { RUNNING = 0, OPTIMAL = 1, ITER_LIMIT = 2, NUMERIC = 3, NEEDS_INIT = 4,
+              STALLED = 5 };   // STALLED: a staged kernel gave up waiting for its copies
 enum Action { ACT_NONE = 0, ACT_RESTART = 1, ACT_FINISH = 2 };
 enum Algo { ALG_HALPERN = 0, ALG_AVERAGE = 1 };
 enum Metric { METRIC_KKT = 0, METRIC_FPR = 1 };
@@ -286,6 +288,261 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_dual(const Seg *__restrict__ 
         }
     }
     if (!waited) { pdl_wait(); pdl_trigger(); }
+}
+
+// ---------------------------------------------------------------------------
+// staged iteration kernels (Halpern): persistent CTAs walk a list of row
+// chunks; one thread stages each chunk's streamed data -- row pointers,
+// column indices and values of its matrix rows and the per-row vectors -- into
+// shared memory with bulk asynchronous copies several chunks ahead, so every
+// streamed byte is in flight long before it is used and the threads only
+// gather the iterate.  Per row the arithmetic is that of k_primal / k_dual,
+// operation for operation, so both kernels give identical iterates.
+// ---------------------------------------------------------------------------
+constexpr int kStRows = 128;     // rows per chunk = threads per CTA
+constexpr int kStEnts = 640;     // most matrix entries per chunk
+constexpr int kStMaxStages = 8;
+constexpr int kStHead = 128;     // bytes before the first stage (the stage barriers)
+
+struct Chunk {
+    int inst;    // LP index
+    int r0, r1;  // global rows [r0, r1) of A^T (primal) or A (dual)
+    int e0, e1;  // their entries [e0, e1)
+    int aux;     // dual: first ">=" row of the LP
+};
+
+// stage layout: the chunk's descriptor, NV 8-byte vector slices, row
+// pointers, column indices, values; every piece is a multiple of 16 bytes, as
+// the bulk copies require
+template <typename VT, int NV>
+struct StLayout {
+    static constexpr int kVs = kStRows + 2;                 // doubles per vector slice
+    static constexpr int kVec0 = 32;                        // after the descriptor
+    static constexpr int kRp = kVec0 + NV * kVs * 8;
+    static constexpr int kCi = kRp + (kStRows + 8) * 4;
+    static constexpr int kVal = kCi + (kStEnts + 8) * 4;
+    static constexpr int kBytes = kVal + (kStEnts + 8) * (int)sizeof(VT);
+    static_assert(sizeof(Chunk) <= kVec0 && kRp % 16 == 0 && kCi % 16 == 0 && kVal % 16 == 0 &&
+                  kBytes % 16 == 0, "16-byte pieces");
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for a stage, giving up after about a second (the copies are from
+// device memory and cannot stall that long unless something is broken)
+constexpr unsigned long long kStWaitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned n = 1;; n++) {
+        if (mbar_test(bar, parity)) return true;
+        if ((n & 255) == 0 && global_ns() - t0 > kStWaitNs) return false;
+    }
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completing on `bar`
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
+}
+
+// the copy window of a chunk: rows and entries rounded out to 16-byte boundaries
+template <typename VT>
+struct StWindow {
+    int r0a, rpa, cia, va;
+    uint32_t nv, nrp, nci, nva;   // bytes
+    __device__ __forceinline__ StWindow(const Chunk &ch) {
+        constexpr int VA = 16 / (int)sizeof(VT);
+        r0a = ch.r0 & ~1;
+        rpa = ch.r0 & ~3;
+        cia = ch.e0 & ~3;
+        va = ch.e0 & ~(VA - 1);
+        nv = (uint32_t)((ch.r1 - r0a + 1) & ~1) * 8u;
+        nrp = (uint32_t)((ch.r1 + 1 - rpa + 3) & ~3) * 4u;
+        nci = (uint32_t)((ch.e1 - cia + 3) & ~3) * 4u;
+        nva = (uint32_t)((ch.e1 - va + VA - 1) & ~(VA - 1)) * (uint32_t)sizeof(VT);
+    }
+};
+
+// what an iteration kernel needs of one LP at step `it` of the block: loaded
+// when a CTA's chunks move to another LP (each CTA's chunks are grouped by LP)
+struct StLp {
+    int inst = -1;
+    bool live = false, keep = false;
+    double step = 0.0, w = 0.0, w1 = 0.0;   // tau (primal) or -sigma (dual); Halpern weights
+};
+template <bool PRIMAL>
+__device__ __forceinline__ void st_load_lp(StLp &L, const Bufs &b, int inst, int it) {
+    const Scalars *S = b.S + inst;
+    const int k = S->k_base + it;
+    L.inst = inst;
+    L.live = S->status == RUNNING && k < S->max_iter;
+    if (!L.live) return;
+    L.keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
+    L.step = PRIMAL ? S->tau : -S->sigma;
+    halpern_weights(b, S, it, L.w, L.w1);
+}
+
+// PRIMAL = true: rows of A^T, vectors x, c, lkey, ukey, x0; gathers y.
+// PRIMAL = false: rows of A, vectors y, q, y0; gathers x-bar.
+// The descriptor goes into the stage header before the arrive, so the
+// threads that wait on the stage barrier see it.
+template <typename VT, bool PRIMAL>
+__device__ __forceinline__ void st_issue(const Chunk &ch, bool live, unsigned char *sb, uint64_t *bar,
+                                         const Bufs &b, int src, uint64_t pol) {
+    constexpr int NV = PRIMAL ? 5 : 3;
+    using Ly = StLayout<VT, NV>;
+    *reinterpret_cast<Chunk *>(sb) = ch;
+    if (!live) { mbar_arrive(bar); return; }
+    const StWindow<VT> w(ch);
+    mbar_expect_tx(bar, NV * w.nv + w.nrp + w.nci + w.nva);
+    unsigned char *v = sb + Ly::kVec0;
+    constexpr int VB = Ly::kVs * 8;
+    if (PRIMAL) {
+        bulk_load(v + 0 * VB, b.x[src] + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 1 * VB, b.c + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 2 * VB, b.lkey + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 3 * VB, b.ukey + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 4 * VB, b.xa + w.r0a, w.nv, bar, pol);
+        bulk_load(sb + Ly::kRp, b.AT_rp + w.rpa, w.nrp, bar, pol);
+        if (w.nci) bulk_load(sb + Ly::kCi, b.AT_ci + w.cia, w.nci, bar, pol);
+        if (w.nva) bulk_load(sb + Ly::kVal, static_cast<const VT *>(b.AT_v) + w.va, w.nva, bar, pol);
+    } else {
+        bulk_load(v + 0 * VB, b.y[src] + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 1 * VB, b.q + w.r0a, w.nv, bar, pol);
+        bulk_load(v + 2 * VB, b.ya + w.r0a, w.nv, bar, pol);
+        bulk_load(sb + Ly::kRp, b.A_rp + w.rpa, w.nrp, bar, pol);
+        if (w.nci) bulk_load(sb + Ly::kCi, b.A_ci + w.cia, w.nci, bar, pol);
+        if (w.nva) bulk_load(sb + Ly::kVal, static_cast<const VT *>(b.A_v) + w.va, w.nva, bar, pol);
+    }
+}
+
+template <typename VT, bool PRIMAL>
+__global__ void __launch_bounds__(kStRows, 8) k_iter_staged(const Chunk *__restrict__ chunks,
+                                                            const int *__restrict__ cta_ptr, Bufs b, int it, int src,
+                                                            int stages) {
+    constexpr int NV = PRIMAL ? 5 : 3;
+    using Ly = StLayout<VT, NV>;
+    constexpr int VS = Ly::kVs;
+    extern __shared__ __align__(128) unsigned char st_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(st_smem);
+    unsigned char *stage0 = st_smem + kStHead;
+    const int tid = threadIdx.x;
+    const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
+    const uint64_t pol = l2_evict_first();
+    if (tid == 0) {
+        for (int s = 0; s < stages; s++) mbar_init(bar + s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // producer state (thread 0): the next descriptor, loaded one chunk ahead,
+    // and the liveness of the LP it belongs to
+    Chunk nxt{};
+    StLp plp;
+    auto produce = [&](int j, int s) {   // chunk q0 + j into stage s
+        const Chunk ch = nxt;
+        if (q0 + j + 1 < q1) nxt = chunks[q0 + j + 1];
+        if (ch.inst != plp.inst) st_load_lp<PRIMAL>(plp, b, ch.inst, it);
+        st_issue<VT, PRIMAL>(ch, plp.live, stage0 + (size_t)s * Ly::kBytes, bar + s, b, src, pol);
+    };
+    // everything staged reads data written two or more launches back
+    if (tid == 0 && q0 < q1) {
+        nxt = chunks[q0];
+        for (int s = 0; s < stages && q0 + s < q1; s++) produce(s, s);
+    }
+    pdl_wait();
+    pdl_trigger();
+    const double *__restrict__ g = PRIMAL ? b.y[src] : b.xsum;   // gathered vector
+    StLp lp;
+    const int n = q1 - q0;
+    for (int i = 0; i < n; i++) {
+        const int s = i % stages;
+        const bool ok = mbar_wait(bar + s, (uint32_t)((i / stages) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a stage never arrived: flag the LP, let the copies still in
+            // flight land (each wait bounded again) and leave
+            if (tid == 0) {
+                b.S[chunks[q0 + i].inst].status = STALLED;
+                const int issued = (i == 0) ? stages : i + stages - 1;   // chunks [0, issued) were issued
+                for (int j = i; j < issued && j < n; j++) mbar_wait(bar + (j % stages), (uint32_t)((j / stages) & 1));
+            }
+            return;
+        }
+        // every thread is past chunk i-1: its stage can be refilled
+        if (tid == 0 && i > 0 && i - 1 + stages < n) produce(i - 1 + stages, (i - 1) % stages);
+        const unsigned char *sb = stage0 + (size_t)s * Ly::kBytes;
+        const Chunk ch = *reinterpret_cast<const Chunk *>(sb);
+        if (ch.inst != lp.inst) st_load_lp<PRIMAL>(lp, b, ch.inst, it);
+        const int r = ch.r0 + tid;
+        if (!lp.live || r >= ch.r1) continue;
+        const StWindow<VT> w(ch);
+        const int lr = r - w.r0a;
+        const int *srp = reinterpret_cast<const int *>(sb + Ly::kRp);
+        const int *sci = reinterpret_cast<const int *>(sb + Ly::kCi);
+        const VT *sv = reinterpret_cast<const VT *>(sb + Ly::kVal);
+        const double *vec = reinterpret_cast<const double *>(sb + Ly::kVec0);
+        const int k0 = srp[r - w.rpa], k1 = srp[r + 1 - w.rpa];
+        // the accumulator starts at -c (-q) and sums the row in entry order
+        double acc = -vec[1 * VS + lr];
+        const unsigned lanes = __activemask();
+        for (int e = k0; __any_sync(lanes, e < k1); e += 4) {
+            double gv[4];
+            VT av[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (e + u < k1) { av[u] = sv[e + u - w.va]; gv[u] = g[sci[e + u - w.cia]]; }
+            // an FMA step issues only if some lane of the warp needs it
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (!__any_sync(lanes, e + u < k1)) break;
+                if (e + u < k1) acc = fma(widen(av[u]), gv[u], acc);
+            }
+        }
+        const double zin = vec[lr];
+        if (PRIMAL) {
+            const long long *keys = reinterpret_cast<const long long *>(vec);
+            const double xv = clip_keys(fma(lp.step, acc, zin), keys[2 * VS + lr], keys[3 * VS + lr]);
+            const double xb = fma(2.0, xv, -zin);
+            b.xsum[r] = xb;
+            b.x[src ^ 1][r] = fma(lp.w, xb, lp.w1 * vec[4 * VS + lr]);
+            if (lp.keep) b.xret[r] = xv;
+        } else {
+            double yv = fma(lp.step, acc, zin);
+            if (r >= ch.aux) yv = nonneg(yv);
+            b.y[src ^ 1][r] = fma(lp.w, fma(2.0, yv, -zin), lp.w1 * vec[2 * VS + lr]);
+            if (lp.keep) b.yret[r] = yv;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -694,6 +951,8 @@ struct Layout {
     size_t c, l, u, Dc, q, Dr, inv_Dc, inv_Dr, lkey, ukey, x_init, y_init, S_init;
     // working state
     size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status;
+    // staged kernels: chunk lists and per-CTA ranges
+    size_t chunks_p, chunks_d, ctas_p, ctas_d;
     size_t upload_end, total;
 };
 
@@ -735,6 +994,15 @@ struct uc_session {
     std::vector<int> m_eq;        // equality rows of each LP
     std::vector<char> tabled;     // LPs whose CTAs are in the current tables and graph
     int cap_sp = 0, cap_sd = 0, cap_se = 0, cap_sa = 0;
+    // staged iteration kernels
+    bool staged = false;
+    int stages = 4;
+    int smem_p = 0, smem_d = 0;   // dynamic shared memory per CTA
+    int gmax_p = 0, gmax_d = 0;   // resident CTAs on the device
+    int g_p = 0, g_d = 0;         // CTAs of the current tables
+    int cap_cp = 0, cap_cd = 0;   // chunk capacities
+    const uc::dev::Chunk *dcp = nullptr, *dcd = nullptr;
+    const int *dgp = nullptr, *dgd = nullptr;
     int retables = 0;
     double tp_sum = 0.0, td_sum = 0.0;
     int timed = 0;
@@ -950,11 +1218,35 @@ static cudaError_t launch_k(Kern kern, int grid, int block, cudaStream_t s, bool
     return cudaLaunchKernelEx(&cfg, kern, segs, b, it, src);
 }
 
+template <typename VT, bool PRIMAL>
+static cudaError_t launch_staged(const uc_session &X, cudaStream_t s, bool pdl, int it, int src) {
+    const int grid = PRIMAL ? X.g_p : X.g_d;
+    if (grid <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kStRows);
+    cfg.dynamicSmemBytes = PRIMAL ? X.smem_p : X.smem_d;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_iter_staged<VT, PRIMAL>, PRIMAL ? X.dcp : X.dcd, PRIMAL ? X.dgp : X.dgd,
+                              X.b, it, src, X.stages);
+}
+
 template <int ALGO, int BS>
 static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
     // the first primal kernel of a block follows the evaluation kernels: no overlap there
     const bool pdl = X.pdl && (!primal || it > 0);
     cudaError_t e;
+    if (X.staged) {
+        if (X.vb == 32) e = primal ? launch_staged<float, true>(X, s, pdl, it, src) : launch_staged<float, false>(X, s, pdl, it, src);
+        else e = primal ? launch_staged<double, true>(X, s, pdl, it, src) : launch_staged<double, false>(X, s, pdl, it, src);
+        if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
+        return;
+    }
     if (primal) {
         if (X.vb == 32) e = launch_k(k_primal<float, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
         else e = launch_k(k_primal<double, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
@@ -1045,6 +1337,33 @@ static int launch_direct(uc_session &X) {
     return UC_OK;
 }
 
+// Shared memory and resident CTAs of the staged kernels for this session.
+template <typename VT>
+static int staged_setup_vt(uc_session &X) {
+    X.smem_p = kStHead + X.stages * StLayout<VT, 5>::kBytes;
+    X.smem_d = kStHead + X.stages * StLayout<VT, 3>::kBytes;
+    int dev = 0, sms = 0, bp = 0, bd = 0;
+    UC_CUDA(cudaGetDevice(&dev));
+    UC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // the attribute is per kernel, not per session: allow the largest stage count
+    const int max_p = kStHead + kStMaxStages * StLayout<VT, 5>::kBytes;
+    const int max_d = kStHead + kStMaxStages * StLayout<VT, 3>::kBytes;
+    UC_CUDA(cudaFuncSetAttribute(k_iter_staged<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_p));
+    UC_CUDA(cudaFuncSetAttribute(k_iter_staged<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_d));
+    UC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_iter_staged<VT, true>, kStRows, X.smem_p));
+    UC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_iter_staged<VT, false>, kStRows, X.smem_d));
+    if (bp < 1 || bd < 1) {
+        set_error("staged kernels: %d stages do not fit in shared memory", X.stages);
+        return UC_EINVAL;
+    }
+    X.gmax_p = bp * sms;
+    X.gmax_d = bd * sms;
+    return UC_OK;
+}
+static int staged_setup(uc_session &X) {
+    return X.vb == 32 ? staged_setup_vt<float>(X) : staged_setup_vt<double>(X);
+}
+
 // CTA tables of the LPs with mask[i]: every CTA works on a slice of one LP.
 // LPs outside the mask get no CTAs (and an empty evaluation range).
 static void build_tables(const uc_session &X, const std::vector<char> &mask, std::vector<Seg> &sp,
@@ -1070,6 +1389,53 @@ static void build_tables(const uc_session &X, const std::vector<char> &mask, std
     sa.insert(sa.end(), sd.begin(), sd.end());
 }
 
+// Chunk lists of the staged kernels for the LPs in `mask`: rows are cut into
+// chunks of at most kStRows rows and kStEnts entries, in device order; the
+// chunks are then dealt to at most `gmax` CTAs by longest-processing-time
+// first on their streamed bytes (so CTAs finish together), and each CTA's
+// chunks are kept in row order.  `ctas` gets the CTA ranges (size CTAs + 1).
+static void build_chunks(const uc_session &X, const std::vector<char> &mask, bool primal, int gmax,
+                         std::vector<Chunk> &out, std::vector<int> &ctas) {
+    std::vector<Chunk> all;
+    std::vector<double> cost;
+    const double per_row = primal ? 5 * 8 + 4 : 3 * 8 + 4, per_ent = 4 + (double)X.vs + 8;
+    for (int i = 0; i < X.k; i++) {
+        if (!mask[i]) continue;
+        const Csr &M = primal ? X.Pd[i]->AT : X.Pd[i]->A;
+        const int64_t base = primal ? X.coff[i] : X.roff[i], zo = X.zoff[i];
+        const int rows = M.rows;
+        const int aux = primal ? 0 : (int)(X.roff[i] + X.m_eq[i]);
+        for (int r = 0; r < rows;) {
+            int r1 = std::min(rows, r + kStRows);
+            while (M.rowptr[r1] - M.rowptr[r] > kStEnts) r1--;   // rows are no longer than kStEnts
+            all.push_back({i, (int)(base + r), (int)(base + r1), (int)(zo + M.rowptr[r]), (int)(zo + M.rowptr[r1]), aux});
+            cost.push_back(per_row * (r1 - r) + per_ent * (M.rowptr[r1] - M.rowptr[r]));
+            r = r1;
+        }
+    }
+    const int g = std::max(1, std::min<int>(gmax, (int)all.size()));
+    std::vector<int> order(all.size());
+    for (size_t t = 0; t < order.size(); t++) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < g; c++) heap.push({0.0, c});
+    std::vector<std::vector<int>> bins(g);
+    for (int t : order) {
+        Load l = heap.top();
+        heap.pop();
+        bins[l.second].push_back(t);
+        heap.push({l.first + cost[t], l.second});
+    }
+    out.clear();
+    ctas.assign(1, 0);
+    for (auto &bin : bins) {
+        std::sort(bin.begin(), bin.end());
+        for (int t : bin) out.push_back(all[t]);
+        ctas.push_back((int)out.size());
+    }
+}
+
 static int capture(uc_session &X, int gi);
 
 // Rebuild the tables for the LPs in `mask` and re-capture the graphs; the
@@ -1088,7 +1454,22 @@ static int retable(uc_session &X, const std::vector<char> &mask) {
     if (!rc) rc = up(L.segs_e, se.data(), sizeof(Seg) * se.size());
     if (!rc) rc = up(L.segs_a, sa.data(), sizeof(Seg) * sa.size());
     if (!rc) rc = up(L.ranges, ranges.data(), sizeof(InstRange) * ranges.size());
+    std::vector<Chunk> cp, cd;
+    std::vector<int> gp, gd;
+    if (X.staged) {
+        build_chunks(X, mask, true, X.gmax_p, cp, gp);
+        build_chunks(X, mask, false, X.gmax_d, cd, gd);
+        if (!rc) rc = up(L.chunks_p, cp.data(), sizeof(Chunk) * cp.size());
+        if (!rc) rc = up(L.chunks_d, cd.data(), sizeof(Chunk) * cd.size());
+        if (!rc) rc = up(L.ctas_p, gp.data(), sizeof(int) * gp.size());
+        if (!rc) rc = up(L.ctas_d, gd.data(), sizeof(int) * gd.size());
+    }
     if (rc) return rc;
+    if (X.staged) {
+        // no chunks at all (no LP tabled) leaves one empty CTA
+        X.g_p = cp.empty() ? 0 : (int)gp.size() - 1;
+        X.g_d = cd.empty() ? 0 : (int)gd.size() - 1;
+    }
     X.n_sp = (int)sp.size(); X.n_sd = (int)sd.size(); X.n_se = (int)se.size(); X.n_sa = (int)sa.size();
     X.tabled = mask;
     X.retables++;
@@ -1120,7 +1501,11 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     X->k = k;
     X->o = o;
     X->vb = Pp[0]->value_bits;
-    if (o.spmv_kernel < 0 || o.spmv_kernel > 1) { set_error("spmv_kernel must be 0 or 1"); return UC_EINVAL; }
+    if (o.spmv_kernel < 0 || o.spmv_kernel > 2) { set_error("spmv_kernel must be 0, 1 or 2"); return UC_EINVAL; }
+    if (o.stages != 0 && (o.stages < 2 || o.stages > kStMaxStages)) {
+        set_error("stages must be 0 or 2..%d", kStMaxStages);
+        return UC_EINVAL;
+    }
     if (o.algorithm < 0 || o.algorithm > 1 || o.restart_metric < 0 || o.restart_metric > 1) {
         set_error("algorithm and restart_metric must be 0 or 1");
         return UC_EINVAL;
@@ -1163,18 +1548,46 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         X->rpt[i] = r;
         X->m_eq[i] = Pp[i]->m_eq;
     }
+    // staged kernels (spmv_kernel 2; measured slower than the row kernels on
+    // the 6,049-bus LP, so opt-in): Halpern only, every matrix row within one chunk
+    X->staged = o.spmv_kernel == 2;
+    X->stages = o.stages ? o.stages : 2;
+    if (X->staged) {
+        int longest = 0;
+        for (int i = 0; i < k; i++)
+            for (const Csr *M : {&X->Pd[i]->A, &X->Pd[i]->AT})
+                for (int r = 0; r < M->rows; r++) longest = std::max(longest, M->rowptr[r + 1] - M->rowptr[r]);
+        if (X->algo != ALG_HALPERN || longest > kStEnts) {
+            set_error("staged kernels need the Halpern algorithm and rows of at most %d entries (longest %d)",
+                      kStEnts, longest);
+            return UC_EINVAL;
+        }
+        int rc = staged_setup(*X);
+        if (rc) return rc;
+    }
     // CTA tables for every LP (their sizes are the capacities of the device tables)
     std::vector<Seg> sp, sd, se, sa;
     std::vector<InstRange> ranges;
     std::vector<char> all(k, 1);
     build_tables(*X, all, sp, sd, se, sa, ranges);
     X->tabled = all;
+    std::vector<Chunk> cp, cd;
+    std::vector<int> gp, gd;
+    if (X->staged) {
+        build_chunks(*X, all, true, X->gmax_p, cp, gp);
+        build_chunks(*X, all, false, X->gmax_d, cd, gd);
+        X->cap_cp = (int)cp.size(); X->cap_cd = (int)cd.size();
+        X->g_p = cp.empty() ? 0 : (int)gp.size() - 1;
+        X->g_d = cd.empty() ? 0 : (int)gd.size() - 1;
+    }
     X->n_sp = X->cap_sp = (int)sp.size(); X->n_sd = X->cap_sd = (int)sd.size();
     X->n_se = X->cap_se = (int)se.size(); X->n_sa = X->cap_sa = (int)sa.size();
 
     Layout &L = X->L;
     size_t off = 0;
-    auto take = [&](size_t n) { size_t p = off; off += align_up(std::max<size_t>(n, 1), 256); return p; };
+    // 16 bytes of slack after every array: the staged kernels' copies round
+    // their windows out to 16-byte boundaries
+    auto take = [&](size_t n) { size_t p = off; off += align_up(std::max<size_t>(n, 1) + 16, 256); return p; };
     const size_t vs = X->vs;
     // +4 zero entries: a 16-byte load starting inside the array stays inside it
     L.A_rp = take((M + 1) * 4); L.A_ci = take((Z + 4) * 4); L.A_v = take((Z + 4) * vs);
@@ -1182,6 +1595,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     L.segs_p = take(sizeof(Seg) * X->n_sp); L.segs_d = take(sizeof(Seg) * X->n_sd);
     L.segs_e = take(sizeof(Seg) * X->n_se); L.segs_a = take(sizeof(Seg) * X->n_sa);
     L.ranges = take(sizeof(InstRange) * k);
+    L.chunks_p = take(sizeof(Chunk) * X->cap_cp); L.chunks_d = take(sizeof(Chunk) * X->cap_cd);
+    L.ctas_p = take(sizeof(int) * (X->gmax_p + 1)); L.ctas_d = take(sizeof(int) * (X->gmax_d + 1));
     const int nW = (int)std::min<long long>((long long)o.max_iter + 1, 1LL << 22);
     L.W = take(sizeof(double) * nW); L.W1 = take(sizeof(double) * nW);
     L.c = take(N * 8); L.l = take(N * 8); L.u = take(N * 8); L.Dc = take(N * 8);
@@ -1230,6 +1645,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         put(st, L.segs_e, se.data(), X->n_se);
         put(st, L.segs_a, sa.data(), X->n_sa);
         put(st, L.ranges, ranges.data(), k);
+        put(st, L.chunks_p, cp.data(), cp.size()); put(st, L.chunks_d, cd.data(), cd.size());
+        put(st, L.ctas_p, gp.data(), gp.size()); put(st, L.ctas_d, gd.data(), gd.size());
         // Halpern weights, computed as the reference computes them: w = (j+1)/(j+2), 1 - w
         double *W = (double *)(st.data() + L.W), *W1 = (double *)(st.data() + L.W1);
         for (int jj = 0; jj < nW; jj++) {
@@ -1257,6 +1674,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         }
     }
     char *D = X->D;
+    if ((uintptr_t)D & 255) { set_error("device allocation is not 256-byte aligned"); return UC_EINVAL; }
     UC_CUDA(cudaMemcpyAsync(D, st.data(), L.upload_end, cudaMemcpyHostToDevice, s));
     X->h2d = (long long)L.upload_end;
     Bufs &b = X->b;
@@ -1279,6 +1697,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     X->dsp = (const Seg *)(D + L.segs_p); X->dsd = (const Seg *)(D + L.segs_d);
     X->dse = (const Seg *)(D + L.segs_e); X->dsa = (const Seg *)(D + L.segs_a);
     X->drg = (const InstRange *)(D + L.ranges);
+    X->dcp = (const Chunk *)(D + L.chunks_p); X->dcd = (const Chunk *)(D + L.chunks_d);
+    X->dgp = (const int *)(D + L.ctas_p); X->dgd = (const int *)(D + L.ctas_d);
     // nothing runs until the first reset: mark every LP finished-as-idle
     UC_CUDA(cudaMemsetAsync(D + L.S, 0xff, sizeof(Scalars) * k, s));   // status -1: idle
     UC_CUDA(cudaMemsetAsync(D + L.status, 0xff, sizeof(int) * k, s));
@@ -1462,6 +1882,10 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     if (S.status == OPTIMAL) status = UC_OK;
     else if (S.status == ITER_LIMIT) status = UC_EITERLIMIT;
     else if (S.status == NUMERIC) status = UC_ENUMERIC;
+    else if (S.status == STALLED) {
+        status = UC_ECUDA;
+        set_error("a staged iteration kernel stopped waiting for its shared-memory copies");
+    }
     else status = X.host_status ? X.host_status : UC_EITERLIMIT;
     o.status = status;
     o.iters = (S.status == ITER_LIMIT) ? X.o.max_iter : S.k_base;
@@ -1722,6 +2146,7 @@ int uc_session_status(const uc_session *s, int i) {
         case dev::OPTIMAL: return UC_OK;
         case dev::ITER_LIMIT: return UC_EITERLIMIT;
         case dev::NUMERIC: return UC_ENUMERIC;
+        case dev::STALLED: return UC_ECUDA;
         default: return 1;
     }
 }
