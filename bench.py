@@ -35,17 +35,28 @@ UNIT = "PDHG iter/s"
 TOL = 1e-4
 MAX_ITER = 100_000
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture, valid
-# only for the device source it was taken on (sha256 of uc_device.cu) and the
-# launch shape (threads per CTA, rows per thread) it was taken with.
+# DRAM bytes per launch of the iteration kernels from one ncu capture with
+# --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern
+# (profiles/pdhg_kernels_grid6049.md): valid only for the kernel source they
+# were taken on (the hash of the row kernels' section of uc_device.cu) and the
+# launch shape (threads per CTA, rows per thread).
 NCU_TRAFFIC = {
-    # ncu --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern,
-    # 2 rows per thread (profiles/pdhg_kernels_grid6049.md)
-    ("paper", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 69867520 + 1521152},
-    ("paper", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 48262144 + 534528},
-    ("paper-fp32", "halpern", "k_primal"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 59236864 + 352000},
-    ("paper-fp32", "halpern", "k_dual"): {"src": "880570ae0cd825c4", "launch": (256, 2), "bytes": 37596672 + 81408},
+    ("paper", "halpern", "k_primal"): {"src": "ee559fc8db2dce5f", "launch": (128, 1), "bytes": 69798912 + 2111616},
+    ("paper", "halpern", "k_dual"): {"src": "ee559fc8db2dce5f", "launch": (128, 1), "bytes": 47886848 + 1255936},
 }
+NCU_TRAFFIC_RPT2 = {
+    ("paper", "halpern", "k_primal"): {"src": "ee559fc8db2dce5f", "launch": (128, 2), "bytes": 69840256 + 382464},
+    ("paper", "halpern", "k_dual"): {"src": "ee559fc8db2dce5f", "launch": (128, 2), "bytes": 47992832 + 194944},
+}
+
+
+def _src_hash():
+    """sha256 (16 hex digits) of the row kernels and their helpers in uc_device.cu."""
+    with open(os.path.join(ROOT, "paper_2607_03627_gb300", "csrc", "uc_device.cu")) as f:
+        src = f.read()
+    a = src.index("// FP64 is scarce on this GPU")
+    b = src.index("// staged iteration kernels (Halpern)")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def _peaks():
@@ -55,11 +66,6 @@ def _peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
-
-
-def _src_hash():
-    with open(os.path.join(ROOT, "paper_2607_03627_gb300", "csrc", "uc_device.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 class ClockSampler:
@@ -155,11 +161,14 @@ def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
 
 
 # FP64 instructions the device issues per row (FP64 FMA/add/mul each count 1;
-# selections, clipping and FP32 widening run on the integer pipe).
+# selections, clipping and FP32 widening run on the integer pipe; the
+# accumulators start at -c / -q, so the step is one FMA).  Halpern per column:
+# the row's FMAs, the step, the reflection, (1 - w) x0 and the combination;
+# averaging: the row's FMAs (dual: two per entry), the step and the sum.
 def fp64_inst_per_iter(n, m, nnz, algorithm="halpern"):
     if algorithm == "halpern":
-        return nnz + 5 * n, nnz + 5 * m
-    return nnz + 3 * n, 2 * nnz + 3 * m
+        return nnz + 4 * n, nnz + 4 * m
+    return nnz + 2 * n, 2 * nnz + 2 * m
 
 
 # GPU-wide FP64 pipe issue rate: 2 thread-instructions per SM per clock
@@ -273,8 +282,8 @@ def run_ours(args):
     bound = "alu" if dk["alu_fp64"]["frac"] >= dk["hbm"]["frac"] else "hbm"
     main = dk["alu_fp64"] if bound == "alu" else dk["hbm"]
     traffic = None
-    rec = NCU_TRAFFIC.get((args.config, args.algorithm, dom))
-    if rec and rec["src"] == _src_hash() and tuple(rec["launch"]) == (cta or 128, rpt):
+    rec = (NCU_TRAFFIC if rpt == 1 else NCU_TRAFFIC_RPT2).get((args.config, args.algorithm, dom))
+    if args.spmv_kernel != 2 and rec and rec["src"] == _src_hash() and tuple(rec["launch"]) == (cta or 128, rpt):
         traffic = rec["bytes"]
     roofline = {"bound": bound, "kernel": dom, "achieved": main["achieved"], "peak": main["peak"],
                 "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
@@ -468,6 +477,61 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lanes(args):
+    """Shared-matrix session: `--lanes` (2 or 4) load variants of the 6,049-bus
+    grid (served-request recipe, wave 0) presolved with the base scaling and
+    solved together with the matrix stored once and the vectors interleaved,
+    against the same LPs solved one at a time on the device (FP64)."""
+    import torch
+    import ucgen
+    torch.cuda.set_device(0)
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding as B
+    base = ucgen.paper_scale(0)
+    base_ps = B.uc_presolve(B.uc_build_lp(base))
+    pss = [B.uc_presolve_reuse(base_ps, B.uc_build_lp(ucgen.served_request(base, 0, r))) for r in range(args.lanes)]
+    n, m, _, nnz = B.uc_presolved_dims(pss[0])
+    sess = B.Session(pss, tol=TOL, max_iter=args.max_iter, lanes=True)
+    for _ in range(args.warmup):
+        sess.reset(-1); sess.run()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sess.reset(-1); sess.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = [B.uc_get_stats(sess.result(i)[0]) for i in range(args.lanes)]
+    sess.close()
+    lp_iters = sum(s["iters"] for s in st)
+    line = {"metric": METRIC, "value": lp_iters / (ms / 1e3), "unit": "LP-PDHG iter/s (summed over lanes)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.lanes} load variants (x0.80..) of the 6049-bus / 700-unit / 48-period LP, "
+                                   "one shared-matrix session", "n": n, "m": m, "nnz": nnz, "lanes": args.lanes,
+                       "tol_rel_kkt": TOL},
+            "per_lp": [{"iters": s["iters"], "status": s["status_name"], "objective": s["objective"]} for s in st],
+            "all_optimal": all(s["status"] == 0 for s in st), "clocks": clk.summary(), "impl": "ours"}
+    if not args.no_sequential:
+        tot = 0.0
+        seq = []
+        for p in pss:
+            s1 = B.Session([p], tol=TOL, max_iter=args.max_iter)
+            s1.reset(-1); s1.run()
+            a = torch.cuda.Event(enable_timing=True); b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream); s1.reset(-1); s1.run(); b_.record(stream); torch.cuda.synchronize()
+            tot += a.elapsed_time(b_)
+            seq.append(B.uc_get_stats(s1.result(0)[0])["iters"])
+            s1.close()
+        line["sequential_fp64"] = {"ms": tot, "iters": seq, "lp_iter_per_s": sum(seq) / (tot / 1e3)}
+        line["speedup_vs_sequential"] = tot / ms
+    print(json.dumps(line), flush=True)
+
+
 def run_served(args):
     """Served stream: requests on the 6,049-bus grid with loads scaled by
     {0.80..1.20} and AR(1) noise, Poisson arrivals at 2 req/s, continuous
@@ -509,7 +573,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="paper", choices=["paper", "paper-fp32", "tiny", "batch64", "served"])
+    ap.add_argument("--config", default="paper",
+                    choices=["paper", "paper-fp32", "tiny", "batch64", "served", "paper-lanes"])
+    ap.add_argument("--lanes", type=int, default=4, help="paper-lanes: LPs in the shared-matrix session (2 or 4)")
     ap.add_argument("--batch", type=int, default=64, help="batch64: number of LPs")
     ap.add_argument("--requests", type=int, default=45, help="served: requests (45 per wave)")
     ap.add_argument("--slots", type=int, default=4, help="served: session slots")
@@ -524,7 +590,7 @@ def main():
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")
-    ap.add_argument("--cta-rows", type=int, default=0, help="threads per CTA of the iteration kernels (0: 256)")
+    ap.add_argument("--cta-rows", type=int, default=0, help="threads per CTA of the iteration kernels (0: 128)")
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
@@ -535,6 +601,8 @@ def main():
         run_reference(args)
     elif args.config == "batch64":
         run_batch(args)
+    elif args.config == "paper-lanes":
+        run_lanes(args)
     elif args.config == "served":
         run_served(args)
     else:

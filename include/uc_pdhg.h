@@ -128,6 +128,11 @@ typedef struct {
                                     "terminate the other solver" step of Alg. 1 */
     int stages;                  /* staged kernels: chunks in flight per CTA, 2..8 (0: default 2);
                                     results do not depend on it (tuning knob) */
+    int lanes;                   /* 1: the session's 2 or 4 LPs share one scaled matrix (e.g. requests
+                                    on one grid presolved with uc_presolve_reuse); it is stored once
+                                    and the LPs' vectors are interleaved, so every row is read once
+                                    for all of them (Halpern, row kernels; UC_EINVAL otherwise).
+                                    Iterates are those of separate solves, bit for bit. */
 } uc_solve_opts;
 
 typedef struct {
@@ -289,9 +294,11 @@ typedef struct {
  * device work overlaps (several streams or host threads at once) race and
  * must be serialised by the caller; no part of it needs to start at zero.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before starting any stream capture.  No cudaMalloc, cudaFree or other
- * allocating call is made. */
+ * (cudaGetSymbolAddress) and loads the entry's two kernels
+ * (cudaFuncGetAttributes; under CUDA's lazy module loading the driver may take
+ * device memory for their code then) with that device current; make that
+ * first call before starting any stream capture.  No cudaMalloc, cudaFree or
+ * other allocating call is made. */
 int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, double omega, double *out,
                    void *stream);
 

@@ -51,7 +51,7 @@ class uc_solve_opts(C.Structure):
                 ("spmv_kernel", C.c_int), ("cta_rows", C.c_int), ("rows_per_thread", _P(C.c_int)),
                 ("no_reorder", C.c_int), ("no_pdl", C.c_int), ("algorithm", C.c_int),
                 ("restart_metric", C.c_int),
-                ("cancel", _P(C.c_int)), ("stages", C.c_int)]
+                ("cancel", _P(C.c_int)), ("stages", C.c_int), ("lanes", C.c_int)]
 
 
 class uc_device_lp(C.Structure):
@@ -293,7 +293,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
                restart_metric: str = "kkt", cta_rows: int = 0,
                rows_per_thread=None, pdl: bool = True, reorder: bool = True,
-               stages: int = 0) -> tuple[uc_solve_opts, list]:
+               stages: int = 0, lanes: bool = False) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -309,6 +309,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.no_pdl = 0 if pdl else 1
     o.no_reorder = 0 if reorder else 1
     o.stages = int(stages)
+    o.lanes = int(bool(lanes))
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)

@@ -546,6 +546,195 @@ __global__ void __launch_bounds__(kStRows, 8) k_iter_staged(const Chunk *__restr
 }
 
 // ---------------------------------------------------------------------------
+// shared-matrix ("lanes") iteration kernels (Halpern): K = 2 or 4 LPs with one
+// scaled matrix, stored once; their vectors are interleaved, element j of lane
+// r at j*K + r.  A row takes K/2 threads, each owning two lanes: its vector
+// loads, stores and gathers are 16 bytes wide, the row's entries are read once
+// for all lanes, and every thread carries two independent FMA chains.  Per
+// lane the arithmetic is that of k_primal / k_dual, operation for operation.
+// ---------------------------------------------------------------------------
+template <int K>
+struct LaneStep {   // per-lane data of one launch, shared by the CTA
+    double step[K], w[K], w1[K];
+    int live[K], keep[K];
+};
+
+template <int K, bool PRIMAL>
+__device__ __forceinline__ void load_lane_steps(LaneStep<K> &L, const Bufs &b, int it) {
+    const int r = threadIdx.x;
+    if (r < K) {
+        const Scalars *S = b.S + r;
+        const int k = S->k_base + it;
+        const bool live = S->status == RUNNING && k < S->max_iter;
+        double w = 0.0, w1 = 0.0;
+        if (live) halpern_weights(b, S, it, w, w1);
+        L.live[r] = live;
+        L.keep[r] = (it == S->n_eval - 1 || k == S->max_iter - 1);
+        L.w[r] = w;
+        L.w1[r] = w1;
+        L.step[r] = PRIMAL ? S->tau : -S->sigma;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void st_lanes(double *p, bool l0, bool l1, double v0, double v1) {
+    if (l0 && l1) *reinterpret_cast<double2 *>(p) = make_double2(v0, v1);
+    else if (l0) p[0] = v0;
+    else if (l1) p[1] = v1;
+}
+
+template <typename VT, int K, int BS>
+__global__ void __launch_bounds__(BS) k_primal_lanes(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+    constexpr int TPR = K / 2;   // threads per row
+    __shared__ LaneStep<K> L;
+    load_lane_steps<K, true>(L, b, it);
+    const Seg sg = segs[blockIdx.x];
+    const int j = sg.begin + (int)threadIdx.x / TPR;
+    const int p = (int)threadIdx.x % TPR;
+    const bool l0 = L.live[2 * p] != 0, l1 = L.live[2 * p + 1] != 0;
+    if (j >= sg.end || !(l0 || l1)) { pdl_wait(); pdl_trigger(); return; }
+    const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+    const size_t e = (size_t)j * K + 2 * p;   // this thread's first element
+    // independent of the dual kernel that precedes this one
+    const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
+    const double2 xin = ld_stream(reinterpret_cast<const double2 *>(b.x[src] + e));
+    const longlong2 lk = ld_stream(reinterpret_cast<const longlong2 *>(b.lkey + e));
+    const longlong2 uk = ld_stream(reinterpret_cast<const longlong2 *>(b.ukey + e));
+    const double2 x0 = ld_stream(reinterpret_cast<const double2 *>(b.xa + e));
+    int ci[kPre];
+    double av[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; q++) {
+        ci[q] = 0;
+        av[q] = 0.0;
+        if (k0 + q < k1) { ci[q] = ld_stream(b.AT_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
+    }
+    const double2 cc = ld_stream(reinterpret_cast<const double2 *>(b.c + e));
+    double acc0 = -cc.x, acc1 = -cc.y;   // the accumulators end at A^T y - c
+    pdl_wait();
+    pdl_trigger();
+    const double *__restrict__ y = b.y[src] + 2 * p;
+    const unsigned lanes = __activemask();
+#pragma unroll
+    for (int q = 0; q < kPre; q++) {
+        if (!__any_sync(lanes, k0 + q < k1)) break;
+        if (k0 + q < k1) {
+            const double2 g = *reinterpret_cast<const double2 *>(y + (size_t)ci[q] * K);
+            acc0 = fma(av[q], g.x, acc0);
+            acc1 = fma(av[q], g.y, acc1);
+        }
+    }
+    for (int kk = k0 + kPre; kk < k1; kk++) {
+        const double a = widen(ld_stream(v + kk));
+        const double2 g = *reinterpret_cast<const double2 *>(y + (size_t)ld_stream(b.AT_ci + kk) * K);
+        acc0 = fma(a, g.x, acc0);
+        acc1 = fma(a, g.y, acc1);
+    }
+    double xv0 = 0.0, xv1 = 0.0, xb0 = 0.0, xb1 = 0.0, xn0 = 0.0, xn1 = 0.0;
+    if (l0) {
+        const int r = 2 * p;
+        xv0 = clip_keys(fma(L.step[r], acc0, xin.x), lk.x, uk.x);
+        xb0 = fma(2.0, xv0, -xin.x);
+        xn0 = fma(L.w[r], xb0, L.w1[r] * x0.x);
+    }
+    if (l1) {
+        const int r = 2 * p + 1;
+        xv1 = clip_keys(fma(L.step[r], acc1, xin.y), lk.y, uk.y);
+        xb1 = fma(2.0, xv1, -xin.y);
+        xn1 = fma(L.w[r], xb1, L.w1[r] * x0.y);
+    }
+    st_lanes(b.xsum + e, l0, l1, xb0, xb1);
+    st_lanes(b.x[src ^ 1] + e, l0, l1, xn0, xn1);
+    st_lanes(b.xret + e, l0 && L.keep[2 * p], l1 && L.keep[2 * p + 1], xv0, xv1);
+}
+
+template <typename VT, int K, int BS>
+__global__ void __launch_bounds__(BS) k_dual_lanes(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+    constexpr int TPR = K / 2;
+    __shared__ LaneStep<K> L;
+    load_lane_steps<K, false>(L, b, it);
+    const Seg sg = segs[blockIdx.x];
+    const int i = sg.begin + (int)threadIdx.x / TPR;
+    const int p = (int)threadIdx.x % TPR;
+    const bool l0 = L.live[2 * p] != 0, l1 = L.live[2 * p + 1] != 0;
+    if (i >= sg.end || !(l0 || l1)) { pdl_wait(); pdl_trigger(); return; }
+    const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    const size_t e = (size_t)i * K + 2 * p;
+    const int k0 = ld_stream(b.A_rp + i), k1 = ld_stream(b.A_rp + i + 1);
+    const double2 yin = ld_stream(reinterpret_cast<const double2 *>(b.y[src] + e));
+    const double2 y0 = ld_stream(reinterpret_cast<const double2 *>(b.ya + e));
+    int ci[kPre];
+    double av[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; q++) {
+        ci[q] = 0;
+        av[q] = 0.0;
+        if (k0 + q < k1) { ci[q] = ld_stream(b.A_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
+    }
+    const double2 qq = ld_stream(reinterpret_cast<const double2 *>(b.q + e));
+    double acc0 = -qq.x, acc1 = -qq.y;   // the accumulators end at A x-bar - q
+    pdl_wait();
+    pdl_trigger();
+    const double *__restrict__ xb = b.xsum + 2 * p;
+    const unsigned lanes = __activemask();
+#pragma unroll
+    for (int q = 0; q < kPre; q++) {
+        if (!__any_sync(lanes, k0 + q < k1)) break;
+        if (k0 + q < k1) {
+            const double2 g = *reinterpret_cast<const double2 *>(xb + (size_t)ci[q] * K);
+            acc0 = fma(av[q], g.x, acc0);
+            acc1 = fma(av[q], g.y, acc1);
+        }
+    }
+    for (int kk = k0 + kPre; kk < k1; kk++) {
+        const double a = widen(ld_stream(v + kk));
+        const double2 g = *reinterpret_cast<const double2 *>(xb + (size_t)ld_stream(b.A_ci + kk) * K);
+        acc0 = fma(a, g.x, acc0);
+        acc1 = fma(a, g.y, acc1);
+    }
+    const bool ineq = i >= sg.aux;
+    double yv0 = 0.0, yv1 = 0.0, yn0 = 0.0, yn1 = 0.0;
+    if (l0) {
+        const int r = 2 * p;
+        yv0 = fma(L.step[r], acc0, yin.x);
+        if (ineq) yv0 = nonneg(yv0);
+        yn0 = fma(L.w[r], fma(2.0, yv0, -yin.x), L.w1[r] * y0.x);
+    }
+    if (l1) {
+        const int r = 2 * p + 1;
+        yv1 = fma(L.step[r], acc1, yin.y);
+        if (ineq) yv1 = nonneg(yv1);
+        yn1 = fma(L.w[r], fma(2.0, yv1, -yin.y), L.w1[r] * y0.y);
+    }
+    st_lanes(b.y[src ^ 1] + e, l0, l1, yn0, yn1);
+    st_lanes(b.yret + e, l0 && L.keep[2 * p], l1 && L.keep[2 * p + 1], yv0, yv1);
+}
+
+// lane `lane` of the interleaved state <- its start point (x_init, y_init)
+__global__ void k_lane_reset(Bufs b, const double *__restrict__ x_init, const double *__restrict__ y_init,
+                             int n, int m, int K, int lane) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (size_t)n) {
+        const size_t e = t * K + lane;
+        const double v = x_init[e];
+        b.x[0][e] = v; b.x[1][e] = v; b.xa[e] = v; b.xret[e] = v; b.xsum[e] = 0.0;
+    } else if (t < (size_t)n + m) {
+        const size_t e = (t - n) * K + lane;
+        const double v = y_init[e];
+        b.y[0][e] = v; b.y[1][e] = v; b.ya[e] = v; b.yret[e] = v; b.ysum[e] = 0.0;
+    }
+}
+
+// dst[t] <- src[t*K + lane] (gather = true) or dst[t*K + lane] <- src[t] (scatter)
+__global__ void k_lane_copy(double *__restrict__ dst, const double *__restrict__ src, int count, int K, int lane,
+                            int gather) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    if (gather) dst[t] = src[(size_t)t * K + lane];
+    else dst[(size_t)t * K + lane] = src[t];
+}
+
+// ---------------------------------------------------------------------------
 // evaluation: per-CTA FP64 partials of both candidates (fixed reduction order)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool slot_is_max(int s) { return (s % kSlots) == RPU || (s % kSlots) == RDU; }
@@ -637,10 +826,13 @@ __device__ __forceinline__ void block_reduce_record(const double (&acc)[kPart], 
 // (x_hat, y_hat); the record of candidate 1 only carries the fixed-point
 // residual ||x_in - x_hat||^2 (slot DX2) and ||y_in - y_hat||^2 (slot DY2),
 // x_in / y_in being the input of the last step (buffer 1, n_eval even).
-template <typename VT>
+// K > 1: shared-matrix session, vectors interleaved by lane; lane blockIdx.y.
+template <typename VT, int K>
 __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs, Bufs b, int mode) {
     const Seg sg = segs[blockIdx.x];
-    const Scalars *S = b.S + sg.inst;
+    const int lane = (K == 1) ? 0 : (int)blockIdx.y;
+    const Scalars *S = b.S + ((K == 1) ? sg.inst : lane);
+    auto at = [lane](int idx) { return (size_t)idx * K + lane; };
     double acc[kPart];
 #pragma unroll
     for (int s = 0; s < kPart; s++) acc[s] = 0.0;
@@ -660,16 +852,17 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
             for (int i = sg.begin + threadIdx.x; i < sg.end; i += kThreads) {
                 double ax0 = 0.0, ax1 = 0.0;
                 for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
-                    const int j = b.A_ci[k];
+                    const size_t j = at(b.A_ci[k]);
                     const double a = widen(v[k]);
                     ax0 += a * x[j];
                     if (avg) ax1 += a * (b.xsum[j] * inv_j);
                 }
-                const double qi = b.q[i], idr = b.inv_Dr[i], yh = b.ya[i];
+                const size_t ii = at(i);
+                const double qi = b.q[ii], idr = b.inv_Dr[ii], yh = b.ya[ii];
                 const bool ineq = i >= eq_end;
                 double r0 = ax0 - qi;
                 if (ineq) r0 = fmin(r0, 0.0);
-                const double y0 = y[i];
+                const double y0 = y[ii];
                 acc[RP2] += r0 * r0;
                 acc[RPU] = nnmax(acc[RPU], fabs(r0) * idr);
                 acc[QY] += qi * y0;
@@ -677,13 +870,13 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 if (avg) {
                     double r1 = ax1 - qi;
                     if (ineq) r1 = fmin(r1, 0.0);
-                    const double y1 = b.ysum[i] * inv_j;
+                    const double y1 = b.ysum[ii] * inv_j;
                     acc[kSlots + RP2] += r1 * r1;
                     acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fabs(r1) * idr);
                     acc[kSlots + QY] += qi * y1;
                     acc[kSlots + DY2] += (y1 - yh) * (y1 - yh);
                 } else if (fpr) {
-                    const double d = b.y[1][i] - y0;
+                    const double d = b.y[1][ii] - y0;
                     acc[kSlots + DY2] += d * d;
                 }
             }
@@ -692,15 +885,16 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
             for (int j = sg.begin + threadIdx.x; j < sg.end; j += kThreads) {
                 double t0 = 0.0, t1 = 0.0;
                 for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) {
-                    const int i = b.AT_ci[k];
+                    const size_t i = at(b.AT_ci[k]);
                     const double a = widen(v[k]);
                     t0 += a * y[i];
                     if (avg) t1 += a * (b.ysum[i] * inv_j);
                 }
-                const double cj = b.c[j], lj = b.l[j], uj = b.u[j], idc = b.inv_Dc[j], xh = b.xa[j];
+                const size_t jj = at(j);
+                const double cj = b.c[jj], lj = b.l[jj], uj = b.u[jj], idc = b.inv_Dc[jj], xh = b.xa[jj];
                 const bool lf = isfinite(lj), uf = isfinite(uj);
                 const double lam[2] = {cj - t0, cj - t1};
-                const double xs[2] = {x[j], avg ? b.xsum[j] * inv_j : 0.0};
+                const double xs[2] = {x[jj], avg ? b.xsum[jj] * inv_j : 0.0};
 #pragma unroll
                 for (int cnd = 0; cnd < 2; cnd++) {
                     if (cnd == 1 && !avg) break;
@@ -718,13 +912,14 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     a[DX2] += (xs[cnd] - xh) * (xs[cnd] - xh);
                 }
                 if (fpr) {
-                    const double d = b.x[1][j] - x[j];
+                    const double d = b.x[1][jj] - x[jj];
                     acc[kSlots + DX2] += d * d;
                 }
             }
         }
     }
-    block_reduce_record(acc, b.part + (size_t)blockIdx.x * kPart);
+    const size_t rec = (K == 1) ? blockIdx.x : (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_record(acc, b.part + rec * kPart);
 }
 
 // ---------------------------------------------------------------------------
@@ -896,15 +1091,18 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
 // Average variant: restart (current <- candidate, anchor <- candidate,
 // sums <- 0) or finish (returned point <- chosen candidate).  Halpern variant:
 // restart (current <- map output, anchor <- map output).
-template <int BS>
+// K > 1: shared-matrix session, lane blockIdx.y, vectors interleaved by lane.
+template <int BS, int K>
 __global__ void __launch_bounds__(BS) k_apply(const Seg *__restrict__ segs, int ncol_blocks, Bufs b) {
     const Seg sg = segs[blockIdx.x];
-    const Scalars *S = b.S + sg.inst;
+    const int lane = (K == 1) ? 0 : (int)blockIdx.y;
+    const Scalars *S = b.S + ((K == 1) ? sg.inst : lane);
     const int act = S->action;
     if (act == ACT_NONE) return;
     for (int t = 0; t < sg.rpt; t++) {
-    const int idx = sg.begin + t * BS + threadIdx.x;
-    if (idx >= sg.end) return;
+    const int row = sg.begin + t * BS + threadIdx.x;
+    if (row >= sg.end) return;
+    const size_t idx = (size_t)row * K + lane;
     const bool col = blockIdx.x < (unsigned)ncol_blocks;
     double *cur = col ? b.x[0] : b.y[0];
     double *sum = col ? b.xsum : b.ysum;
@@ -953,6 +1151,8 @@ struct Layout {
     size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status;
     // staged kernels: chunk lists and per-CTA ranges
     size_t chunks_p, chunks_d, ctas_p, ctas_d;
+    // lanes sessions: contiguous staging for one LP's vectors (3 (n + m) doubles)
+    size_t lane_stage;
     size_t upload_end, total;
 };
 
@@ -994,6 +1194,10 @@ struct uc_session {
     std::vector<int> m_eq;        // equality rows of each LP
     std::vector<char> tabled;     // LPs whose CTAs are in the current tables and graph
     int cap_sp = 0, cap_sd = 0, cap_se = 0, cap_sa = 0;
+    // shared-matrix ("lanes") sessions: K LPs with one scaled matrix, stored
+    // once, vectors interleaved (element j of LP r at j*K + r); K = 1 otherwise
+    int K = 1;
+    int64_t Mr = 0, Nr = 0;       // rows of A and of A^T as stored
     // staged iteration kernels
     bool staged = false;
     int stages = 4;
@@ -1105,6 +1309,12 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     return d;
 }
 
+// same scaled matrix (structure, values as stored, equality rows)
+static bool same_matrix(const PsData &a, const PsData &b) {
+    return a.n() == b.n() && a.m() == b.m() && a.m_eq == b.m_eq && a.value_bits == b.value_bits &&
+           a.A.rowptr == b.A.rowptr && a.A.colidx == b.A.colidx && a.A.val == b.A.val && a.A_val32 == b.A_val32;
+}
+
 // natural-order vector -> device order (and back)
 static std::vector<double> to_device(const double *v, const std::vector<int32_t> &order) {
     std::vector<double> o(order.size());
@@ -1164,36 +1374,56 @@ static void stage_lp(uc_session &X, std::vector<char> &st, int i, const double *
     const double *wx = wx_nat ? wxv.data() : nullptr;
     const double *wy = wy_nat ? wyv.data() : nullptr;
     const Layout &L = X.L;
-    put(st, L.c + X.coff[i] * 8, p.c.data(), p.n());
-    put(st, L.l + X.coff[i] * 8, p.l.data(), p.n());
-    put(st, L.u + X.coff[i] * 8, p.u.data(), p.n());
-    put(st, L.Dc + X.coff[i] * 8, p.Dc.data(), p.n());
-    put(st, L.q + X.roff[i] * 8, p.q.data(), p.m());
-    put(st, L.Dr + X.roff[i] * 8, p.Dr.data(), p.m());
+    // 8-byte vector elements of LP i: contiguous from its offset, or every
+    // K-th element from lane i in a lanes session
+    auto putv = [&](size_t base, int64_t off, const void *src, int count) {
+        if (X.K == 1) {
+            if (count) std::memcpy(st.data() + base + off * 8, src, (size_t)count * 8);
+            return;
+        }
+        for (int t = 0; t < count; t++)
+            std::memcpy(st.data() + base + ((size_t)t * X.K + i) * 8, (const char *)src + (size_t)t * 8, 8);
+    };
+    putv(L.c, X.coff[i], p.c.data(), p.n());
+    putv(L.l, X.coff[i], p.l.data(), p.n());
+    putv(L.u, X.coff[i], p.u.data(), p.n());
+    putv(L.Dc, X.coff[i], p.Dc.data(), p.n());
+    putv(L.q, X.roff[i], p.q.data(), p.m());
+    putv(L.Dr, X.roff[i], p.Dr.data(), p.m());
     {
         std::vector<double> idc, idr;
         std::vector<long long> lk, uk;
         derived_vectors(p, idc, idr, lk, uk);
-        put(st, L.inv_Dc + X.coff[i] * 8, idc.data(), p.n());
-        put(st, L.inv_Dr + X.roff[i] * 8, idr.data(), p.m());
-        put(st, L.lkey + X.coff[i] * 8, lk.data(), p.n());
-        put(st, L.ukey + X.coff[i] * 8, uk.data(), p.n());
+        putv(L.inv_Dc, X.coff[i], idc.data(), p.n());
+        putv(L.inv_Dr, X.roff[i], idr.data(), p.m());
+        putv(L.lkey, X.coff[i], lk.data(), p.n());
+        putv(L.ukey, X.coff[i], uk.data(), p.n());
     }
-    double *x0 = (double *)(st.data() + L.x_init) + X.coff[i];
-    double *y0 = (double *)(st.data() + L.y_init) + X.roff[i];
+    std::vector<double> x0(p.n()), y0(p.m());
     for (int c = 0; c < p.n(); c++) x0[c] = std::min(std::max(wx ? wx[c] : 0.0, p.l[c]), p.u[c]);
     for (int r = 0; r < p.m(); r++) {
         const double v = wy ? wy[r] : 0.0;
         y0[r] = r >= p.m_eq ? std::max(v, 0.0) : v;
     }
+    putv(L.x_init, X.coff[i], x0.data(), p.n());
+    putv(L.y_init, X.roff[i], y0.data(), p.m());
     X.S_init[i] = make_scalars(X, p, womega);
     put(st, L.S_init + sizeof(Scalars) * i, &X.S_init[i], 1);
 }
 
 // evaluation, record reduction and controller (mode 0: start point, 1: regular)
 static void launch_eval(uc_session &X, cudaStream_t s, int mode) {
-    if (X.vb == 32) k_eval<float><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, mode);
-    else k_eval<double><<<X.n_se, kThreads, 0, s>>>(X.dse, X.b, mode);
+    const dim3 grid(X.n_se, X.K);
+    if (X.K == 1) {
+        if (X.vb == 32) k_eval<float, 1><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+        else k_eval<double, 1><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+    } else if (X.K == 2) {
+        if (X.vb == 32) k_eval<float, 2><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+        else k_eval<double, 2><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+    } else {
+        if (X.vb == 32) k_eval<float, 4><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+        else k_eval<double, 4><<<grid, kThreads, 0, s>>>(X.dse, X.b, mode);
+    }
     k_reduce<<<X.k * kPart, kThreads, 0, s>>>(X.drg, X.b, mode);
     k_control<<<(X.k + 127) / 128, 128, 0, s>>>(X.b, mode, X.k);
 }
@@ -1241,6 +1471,19 @@ static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool pri
     // the first primal kernel of a block follows the evaluation kernels: no overlap there
     const bool pdl = X.pdl && (!primal || it > 0);
     cudaError_t e;
+    if (X.K > 1) {   // lanes session: 128-thread CTAs, K/2 threads per row
+        const int grid = primal ? X.n_sp : X.n_sd;
+        const Seg *segs = primal ? X.dsp : X.dsd;
+        if (X.vb == 32) {
+            if (X.K == 2) e = launch_k(primal ? k_primal_lanes<float, 2, 128> : k_dual_lanes<float, 2, 128>, grid, 128, s, pdl, segs, X.b, it, src);
+            else e = launch_k(primal ? k_primal_lanes<float, 4, 128> : k_dual_lanes<float, 4, 128>, grid, 128, s, pdl, segs, X.b, it, src);
+        } else {
+            if (X.K == 2) e = launch_k(primal ? k_primal_lanes<double, 2, 128> : k_dual_lanes<double, 2, 128>, grid, 128, s, pdl, segs, X.b, it, src);
+            else e = launch_k(primal ? k_primal_lanes<double, 4, 128> : k_dual_lanes<double, 4, 128>, grid, 128, s, pdl, segs, X.b, it, src);
+        }
+        if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
+        return;
+    }
     if (X.staged) {
         if (X.vb == 32) e = primal ? launch_staged<float, true>(X, s, pdl, it, src) : launch_staged<float, false>(X, s, pdl, it, src);
         else e = primal ? launch_staged<double, true>(X, s, pdl, it, src) : launch_staged<double, false>(X, s, pdl, it, src);
@@ -1274,10 +1517,16 @@ static void launch_dual(uc_session &X, cudaStream_t s, int it, int src) {
 }
 static void launch_apply(uc_session &X, cudaStream_t s) {
     if (!X.n_sa) return;
+    if (X.K > 1) {   // lanes session: 128-thread segments, one grid row per lane
+        const int ncol = (int)((X.Nr + 127) / 128);
+        if (X.K == 2) k_apply<128, 2><<<dim3(X.n_sa, 2), 128, 0, s>>>(X.dsa, ncol, X.b);
+        else k_apply<128, 4><<<dim3(X.n_sa, 4), 128, 0, s>>>(X.dsa, ncol, X.b);
+        return;
+    }
     switch (X.cta) {
-        case 128: k_apply<128><<<X.n_sa, 128, 0, s>>>(X.dsa, X.n_sp, X.b); break;
-        case 512: k_apply<512><<<X.n_sa, 512, 0, s>>>(X.dsa, X.n_sp, X.b); break;
-        default: k_apply<256><<<X.n_sa, 256, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        case 128: k_apply<128, 1><<<X.n_sa, 128, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        case 512: k_apply<512, 1><<<X.n_sa, 512, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        default: k_apply<256, 1><<<X.n_sa, 256, 0, s>>>(X.dsa, X.n_sp, X.b); break;
     }
 }
 
@@ -1371,6 +1620,21 @@ static void build_tables(const uc_session &X, const std::vector<char> &mask, std
                          std::vector<InstRange> &ranges) {
     sp.clear(); sd.clear(); se.clear(); sa.clear();
     ranges.assign(X.k, InstRange{0, 0});
+    if (X.K > 1) {
+        // lanes session: one structure; K/2 threads per row in the iteration
+        // kernels, one thread per element in the apply kernel (grid.y = lane)
+        const int rows = X.cta / (X.K / 2);
+        const int eq_end = X.m_eq[0];
+        for (int64_t s = 0; s < X.Nr; s += rows) sp.push_back({0, (int)s, (int)std::min<int64_t>(s + rows, X.Nr), 0, 1});
+        for (int64_t s = 0; s < X.Mr; s += rows) sd.push_back({0, (int)s, (int)std::min<int64_t>(s + rows, X.Mr), eq_end, 1});
+        for (int64_t s = 0; s < X.Mr; s += kEvalRows) se.push_back({0, (int)s, (int)std::min<int64_t>(s + kEvalRows, X.Mr), eq_end << 1, 1});
+        for (int64_t s = 0; s < X.Nr; s += kEvalRows) se.push_back({0, (int)s, (int)std::min<int64_t>(s + kEvalRows, X.Nr), 1, 1});
+        if (se.empty()) se.push_back({0, 0, 0, 0, 1});
+        for (int i = 0; i < X.k; i++) ranges[i] = {i * (int)se.size(), (i + 1) * (int)se.size()};
+        for (int64_t s = 0; s < X.Nr; s += X.cta) sa.push_back({0, (int)s, (int)std::min<int64_t>(s + X.cta, X.Nr), 0, 1});
+        for (int64_t s = 0; s < X.Mr; s += X.cta) sa.push_back({0, (int)s, (int)std::min<int64_t>(s + X.cta, X.Mr), 0, 1});
+        return;
+    }
     for (int i = 0; i < X.k; i++) {
         if (!mask[i]) continue;
         const int64_t c0 = X.coff[i], c1 = X.coff[i + 1], r0 = X.roff[i], r1 = X.roff[i + 1];
@@ -1529,13 +1793,35 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         for (int i = 0; i < k; i++)
             for (float f : Pp[i]->A_val32)
                 if (!std::isnormal(f)) { set_error("FP32 matrix value %g is zero, subnormal or not finite", (double)f); return UC_EINVAL; }
-    X->roff.assign(k + 1, 0); X->coff.assign(k + 1, 0); X->zoff.assign(k + 1, 0);
-    for (int i = 0; i < k; i++) {
-        X->roff[i + 1] = X->roff[i] + Pp[i]->m();
-        X->coff[i + 1] = X->coff[i] + Pp[i]->n();
-        X->zoff[i + 1] = X->zoff[i] + Pp[i]->A.nnz();
+    if (o.lanes) {
+        if (k != 2 && k != 4) { set_error("lanes sessions hold 2 or 4 LPs (got %d)", k); return UC_EINVAL; }
+        if (X->algo != ALG_HALPERN || o.spmv_kernel == 2) {
+            set_error("lanes sessions run the Halpern algorithm on the row kernels");
+            return UC_EINVAL;
+        }
+        for (int i = 1; i < k; i++)
+            if (!same_matrix(*X->Pd[i], *X->Pd[0])) {
+                set_error("lanes sessions need LPs with one scaled matrix (LP %d differs from LP 0)", i);
+                return UC_EINVAL;
+            }
+        X->K = k;
+        X->cta = 128;   // the lanes kernels are built for 128-thread CTAs
     }
-    X->M = X->roff[k]; X->N = X->coff[k]; X->Z = X->zoff[k];
+    X->roff.assign(k + 1, 0); X->coff.assign(k + 1, 0); X->zoff.assign(k + 1, 0);
+    if (X->K > 1) {
+        // one structure: every LP starts at row, column and entry 0
+        X->M = (int64_t)Pp[0]->m() * X->K; X->N = (int64_t)Pp[0]->n() * X->K; X->Z = Pp[0]->A.nnz();
+        X->Mr = Pp[0]->m(); X->Nr = Pp[0]->n();
+        X->roff[k] = X->Mr; X->coff[k] = X->Nr; X->zoff[k] = X->Z;
+    } else {
+        for (int i = 0; i < k; i++) {
+            X->roff[i + 1] = X->roff[i] + Pp[i]->m();
+            X->coff[i + 1] = X->coff[i] + Pp[i]->n();
+            X->zoff[i + 1] = X->zoff[i] + Pp[i]->A.nnz();
+        }
+        X->M = X->roff[k]; X->N = X->coff[k]; X->Z = X->zoff[k];
+        X->Mr = X->M; X->Nr = X->N;
+    }
     const int64_t M = X->M, N = X->N, Z = X->Z;
     // row indices are also stored shifted left by one bit in the evaluation table
     if (M >= (1LL << 30) || N >= INT32_MAX || Z >= INT32_MAX) { set_error("batch too large for int32 indices"); return UC_EINVAL; }
@@ -1590,8 +1876,9 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     auto take = [&](size_t n) { size_t p = off; off += align_up(std::max<size_t>(n, 1) + 16, 256); return p; };
     const size_t vs = X->vs;
     // +4 zero entries: a 16-byte load starting inside the array stays inside it
-    L.A_rp = take((M + 1) * 4); L.A_ci = take((Z + 4) * 4); L.A_v = take((Z + 4) * vs);
-    L.AT_rp = take((N + 1) * 4); L.AT_ci = take((Z + 4) * 4); L.AT_v = take((Z + 4) * vs);
+    const int64_t Mr = X->Mr, Nr = X->Nr;   // rows of A and A^T as stored
+    L.A_rp = take((Mr + 1) * 4); L.A_ci = take((Z + 4) * 4); L.A_v = take((Z + 4) * vs);
+    L.AT_rp = take((Nr + 1) * 4); L.AT_ci = take((Z + 4) * 4); L.AT_v = take((Z + 4) * vs);
     L.segs_p = take(sizeof(Seg) * X->n_sp); L.segs_d = take(sizeof(Seg) * X->n_sd);
     L.segs_e = take(sizeof(Seg) * X->n_se); L.segs_a = take(sizeof(Seg) * X->n_sa);
     L.ranges = take(sizeof(InstRange) * k);
@@ -1607,7 +1894,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     L.x0 = take(N * 8); L.x1 = take(N * 8); L.y0 = take(M * 8); L.y1 = take(M * 8);
     L.xsum = take(N * 8); L.ysum = take(M * 8); L.xa = take(N * 8); L.ya = take(M * 8);
     L.xret = take(N * 8); L.yret = take(M * 8);
-    L.part = take(sizeof(double) * kPart * X->n_se);
+    L.part = take(sizeof(double) * kPart * X->n_se * X->K);
+    L.lane_stage = take(X->K > 1 ? (size_t)3 * (Nr + Mr) * 8 : 0);
     L.red = take(sizeof(double) * kPart * k);
     L.S = take(sizeof(Scalars) * k);
     L.status = take(sizeof(int) * k);
@@ -1622,6 +1910,10 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         for (int i = 0; i < k; i++) {
             const PsData &p = *X->Pd[i];
             const int64_t ro = X->roff[i], co = X->coff[i], zo = X->zoff[i];
+            if (X->K > 1 && i > 0) {   // lanes session: the matrix is stored once
+                stage_lp(*X, st, i, nullptr, nullptr, 0.0);
+                continue;
+            }
             for (int r = 0; r < p.m(); r++) arp[ro + r] = (int32_t)(p.A.rowptr[r] + zo);
             for (int c = 0; c < p.n(); c++) atrp[co + c] = (int32_t)(p.AT.rowptr[c] + zo);
             for (int64_t z = 0; z < p.A.nnz(); z++) {
@@ -1638,8 +1930,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
             stage_lp(*X, st, i, (k == 1) ? o.warm_x : nullptr, (k == 1) ? o.warm_y : nullptr,
                      (k == 1) ? o.warm_omega : 0.0);
         }
-        arp[M] = (int32_t)Z;
-        atrp[N] = (int32_t)Z;
+        arp[Mr] = (int32_t)Z;
+        atrp[Nr] = (int32_t)Z;
         put(st, L.segs_p, sp.data(), X->n_sp);
         put(st, L.segs_d, sd.data(), X->n_sd);
         put(st, L.segs_e, se.data(), X->n_se);
@@ -1647,7 +1939,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         put(st, L.ranges, ranges.data(), k);
         put(st, L.chunks_p, cp.data(), cp.size()); put(st, L.chunks_d, cd.data(), cd.size());
         put(st, L.ctas_p, gp.data(), gp.size()); put(st, L.ctas_d, gd.data(), gd.size());
-        // Halpern weights, computed as the reference computes them: w = (j+1)/(j+2), 1 - w
+        // Halpern weights, computed as the oracle's Halpern step computes them: w = (j+1)/(j+2), 1 - w
         double *W = (double *)(st.data() + L.W), *W1 = (double *)(st.data() + L.W1);
         for (int jj = 0; jj < nW; jj++) {
             W[jj] = ((double)jj + 1.0) / ((double)jj + 2.0);
@@ -1722,6 +2014,25 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     return UC_OK;
 }
 
+// lanes sessions: LP `lane`'s elements of an interleaved vector <-> contiguous
+// `count` elements at `host` (through the session's staging area, stream-ordered)
+static int lane_upload(uc_session &X, double *dev_vec, int lane, const void *host, int count) {
+    if (!count) return UC_OK;
+    double *stage = (double *)(X.D + X.L.lane_stage);
+    UC_CUDA(cudaMemcpyAsync(stage, host, (size_t)count * 8, cudaMemcpyHostToDevice, X.s));
+    k_lane_copy<<<(count + 255) / 256, 256, 0, X.s>>>(dev_vec, stage, count, X.K, lane, 0);
+    UC_CUDA(cudaGetLastError());
+    return UC_OK;
+}
+static int lane_download(uc_session &X, void *host, const double *dev_vec, int lane, int count, size_t stage_off) {
+    if (!count) return UC_OK;
+    double *stage = (double *)(X.D + X.L.lane_stage) + stage_off;
+    k_lane_copy<<<(count + 255) / 256, 256, 0, X.s>>>(stage, dev_vec, count, X.K, lane, 1);
+    UC_CUDA(cudaGetLastError());
+    UC_CUDA(cudaMemcpyAsync(host, stage, (size_t)count * 8, cudaMemcpyDeviceToHost, X.s));
+    return UC_OK;
+}
+
 // state of LP i (or all, i < 0) <- its start point; then the anchor KKT on the device
 static int session_reset(uc_session &X, int which) {
     cudaStream_t s = X.s;
@@ -1732,12 +2043,18 @@ static int session_reset(uc_session &X, int which) {
     for (int i = i0; i < i1; i++) {
         const size_t cx = X.coff[i] * 8, nx = (X.coff[i + 1] - X.coff[i]) * 8;
         const size_t cy = X.roff[i] * 8, ny = (X.roff[i + 1] - X.roff[i]) * 8;
-        if (nx) {
+        if (X.K > 1) {
+            const int n = (int)X.Nr, m = (int)X.Mr;
+            if (n + m > 0)
+                k_lane_reset<<<(n + m + 255) / 256, 256, 0, s>>>(X.b, (const double *)(D + L.x_init),
+                                                                 (const double *)(D + L.y_init), n, m, X.K, i);
+            UC_CUDA(cudaGetLastError());
+        } else if (nx) {
             for (size_t dst : {L.x0, L.x1, L.xa, L.xret})
                 UC_CUDA(cudaMemcpyAsync(D + dst + cx, D + L.x_init + cx, nx, cudaMemcpyDeviceToDevice, s));
             UC_CUDA(cudaMemsetAsync(D + L.xsum + cx, 0, nx, s));
         }
-        if (ny) {
+        if (X.K == 1 && ny) {
             for (size_t dst : {L.y0, L.y1, L.ya, L.yret})
                 UC_CUDA(cudaMemcpyAsync(D + dst + cy, D + L.y_init + cy, ny, cudaMemcpyDeviceToDevice, s));
             UC_CUDA(cudaMemsetAsync(D + L.ysum + cy, 0, ny, s));
@@ -1803,7 +2120,7 @@ static int session_run(uc_session &X, int max_replays) {
                 live += want[i];
                 tab += X.tabled[i];
             }
-            if (live > 0 && 4 * live <= 3 * tab) {
+            if (X.K == 1 && live > 0 && 4 * live <= 3 * tab) {   // lanes sessions keep one table
                 // drain the replay still in flight, then rebuild for the live LPs only
                 UC_CUDA(cudaStreamSynchronize(s));
                 checked = launched;
@@ -1856,17 +2173,30 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     if (S.status == ITER_LIMIT && part) j_now = S.j_base + part;
     res->x_cur.resize(n); res->y_cur.resize(m); res->x_avg.resize(n); res->y_avg.resize(m);
     const size_t cx = X.coff[i], cy = X.roff[i];
-    UC_CUDA(cudaMemcpyAsync(res->x_cur.data(), X.b.x[cur] + cx, n * 8, cudaMemcpyDeviceToHost, s));
-    UC_CUDA(cudaMemcpyAsync(res->y_cur.data(), X.b.y[cur] + cy, m * 8, cudaMemcpyDeviceToHost, s));
+    // LP i's elements of a device vector (contiguous, or lane i of a lanes
+    // session through its staging area: up to six vectors, 3 (n + m) doubles)
+    size_t stage_off = 0;
+    auto d2h = [&](std::vector<double> &dst, const double *base, size_t off, int count) -> int {
+        if (X.K == 1) {
+            if (count) UC_CUDA(cudaMemcpyAsync(dst.data(), base + off, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
+            return UC_OK;
+        }
+        int rc = lane_download(X, dst.data(), base, i, count, stage_off);
+        stage_off += (size_t)count;
+        return rc;
+    };
+    int rc = d2h(res->x_cur, X.b.x[cur], cx, n);
+    if (!rc) rc = d2h(res->y_cur, X.b.y[cur], cy, m);
     const bool halp = X.algo == ALG_HALPERN;
     // Halpern: "average" slot = epoch anchor; returned point = last map output
-    UC_CUDA(cudaMemcpyAsync(res->x_avg.data(), (halp ? X.b.xa : X.b.xsum) + cx, n * 8, cudaMemcpyDeviceToHost, s));
-    UC_CUDA(cudaMemcpyAsync(res->y_avg.data(), (halp ? X.b.ya : X.b.ysum) + cy, m * 8, cudaMemcpyDeviceToHost, s));
-    if (S.status == OPTIMAL || halp) {
+    if (!rc) rc = d2h(res->x_avg, halp ? X.b.xa : X.b.xsum, cx, n);
+    if (!rc) rc = d2h(res->y_avg, halp ? X.b.ya : X.b.ysum, cy, m);
+    if (!rc && (S.status == OPTIMAL || halp)) {
         res->x_ret.resize(n); res->y_ret.resize(m);
-        UC_CUDA(cudaMemcpyAsync(res->x_ret.data(), X.b.xret + cx, n * 8, cudaMemcpyDeviceToHost, s));
-        UC_CUDA(cudaMemcpyAsync(res->y_ret.data(), X.b.yret + cy, m * 8, cudaMemcpyDeviceToHost, s));
+        rc = d2h(res->x_ret, X.b.xret, cx, n);
+        if (!rc) rc = d2h(res->y_ret, X.b.yret, cy, m);
     }
+    if (rc) return rc;
     UC_CUDA(cudaStreamSynchronize(s));
     if (!halp) {
         for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
@@ -1926,6 +2256,7 @@ static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const P
     std::vector<double> x0(c.n()), y0(c.m(), 0.0);
     for (int j = 0; j < c.n(); j++) x0[j] = std::min(std::max(0.0, c.l[j]), c.u[j]);
     auto h2d = [&](size_t base, size_t off, const std::vector<double> &v) -> int {
+        if (X.K > 1) return lane_upload(X, (double *)(X.D + base), i, v.data(), (int)v.size());
         if (!v.empty()) UC_CUDA(cudaMemcpyAsync(X.D + base + off, v.data(), v.size() * 8, cudaMemcpyHostToDevice, X.s));
         return UC_OK;
     };
@@ -1937,9 +2268,13 @@ static int session_update_lp(uc_session &X, int i, const std::shared_ptr<const P
     derived_vectors(c, idc, idr, lk, uk);
     rc |= h2d(L.inv_Dc, cx, idc); rc |= h2d(L.inv_Dr, cy, idr);
     if (!lk.empty()) {
-        if (cudaMemcpyAsync(X.D + L.lkey + cx, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess ||
-            cudaMemcpyAsync(X.D + L.ukey + cx, uk.data(), uk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess)
+        if (X.K > 1) {
+            rc |= lane_upload(X, (double *)(X.D + L.lkey), i, lk.data(), (int)lk.size());
+            rc |= lane_upload(X, (double *)(X.D + L.ukey), i, uk.data(), (int)uk.size());
+        } else if (cudaMemcpyAsync(X.D + L.lkey + cx, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess ||
+                   cudaMemcpyAsync(X.D + L.ukey + cx, uk.data(), uk.size() * 8, cudaMemcpyHostToDevice, X.s) != cudaSuccess) {
             rc = 1;
+        }
     }
     if (rc) { set_error("update_lp: host-to-device copy failed"); return UC_ECUDA; }
     X.S_init[i] = make_scalars(X, c);
@@ -1959,8 +2294,14 @@ static int session_set_start(uc_session &X, int i, const double *x, const double
         const double v = y ? y[X.prow[i][r]] : 0.0;
         ys[r] = r >= p.m_eq ? std::max(v, 0.0) : v;
     }
-    if (p.n()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.x_init + X.coff[i] * 8, xs.data(), p.n() * 8, cudaMemcpyHostToDevice, X.s));
-    if (p.m()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.y_init + X.roff[i] * 8, ys.data(), p.m() * 8, cudaMemcpyHostToDevice, X.s));
+    if (X.K > 1) {
+        int rc = lane_upload(X, (double *)(X.D + X.L.x_init), i, xs.data(), p.n());
+        if (!rc) rc = lane_upload(X, (double *)(X.D + X.L.y_init), i, ys.data(), p.m());
+        if (rc) return rc;
+    } else {
+        if (p.n()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.x_init + X.coff[i] * 8, xs.data(), p.n() * 8, cudaMemcpyHostToDevice, X.s));
+        if (p.m()) UC_CUDA(cudaMemcpyAsync(X.D + X.L.y_init + X.roff[i] * 8, ys.data(), p.m() * 8, cudaMemcpyHostToDevice, X.s));
+    }
     X.S_init[i] = make_scalars(X, p, omega);
     UC_CUDA(cudaMemcpyAsync(X.D + X.L.S_init + sizeof(Scalars) * i, &X.S_init[i], sizeof(Scalars),
                             cudaMemcpyHostToDevice, X.s));
@@ -1988,28 +2329,6 @@ constexpr int kNoAllocRows = 1024;       // rows or columns per CTA of the alloc
 constexpr int kNoAllocMaxBlocks = 8192;  // CTAs of 1024 rows or columns: n/1024 + m/1024 <= 8192
 
 static __device__ __align__(256) double g_kkt_scratch[kNoAllocMaxBlocks * kNoAllocSlots];
-
-// per-device address of g_kkt_scratch, looked up once per device
-static std::mutex g_kkt_scratch_mu;
-static void *g_kkt_scratch_ptr[128];
-
-static int kkt_scratch_address(double **out) {
-    int dev = 0;
-    UC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) { set_error("device ordinal %d unsupported", dev); return UC_EINVAL; }
-    std::lock_guard<std::mutex> lock(g_kkt_scratch_mu);
-    if (!g_kkt_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(scratch) failed on device %d: %s", dev, cudaGetErrorString(e));
-            return UC_ECUDA;
-        }
-        g_kkt_scratch_ptr[dev] = p;
-    }
-    *out = (double *)g_kkt_scratch_ptr[dev];
-    return UC_OK;
-}
 
 // CTA b < nbr: rows [1024 b, ...); else columns.  Same per-thread order and
 // block reduction as k_eval, current point only.
@@ -2094,6 +2413,37 @@ __global__ void __launch_bounds__(kThreads) k_kkt_finish_noalloc(int nblocks, co
     out[5] = dobj;
     out[6] = T[RPU];
     out[7] = 0.0;
+}
+
+// per-device address of g_kkt_scratch, looked up once per device
+static std::mutex g_kkt_scratch_mu;
+static void *g_kkt_scratch_ptr[128];
+
+static int kkt_scratch_address(double **out) {
+    int dev = 0;
+    UC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) { set_error("device ordinal %d unsupported", dev); return UC_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_kkt_scratch_mu);
+    if (!g_kkt_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(scratch) failed on device %d: %s", dev, cudaGetErrorString(e));
+            return UC_ECUDA;
+        }
+        // load the entry's kernels now: under lazy module loading the driver
+        // may take device memory for their code on first use
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_kkt_partials_noalloc);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_kkt_finish_noalloc);
+        if (e != cudaSuccess) {
+            set_error("loading the KKT kernels failed on device %d: %s", dev, cudaGetErrorString(e));
+            return UC_ECUDA;
+        }
+        g_kkt_scratch_ptr[dev] = p;
+    }
+    *out = (double *)g_kkt_scratch_ptr[dev];
+    return UC_OK;
 }
 
 

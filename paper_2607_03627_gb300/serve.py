@@ -12,7 +12,10 @@ slots is capped by an HBM budget.  Host presolve (uc_presolve_reuse: the
 base LP's scaling is reused) runs on a thread pool as requests arrive.
 
 Because every slot's arithmetic is independent and deterministic, a request
-returns the same iterates and solution alone or in the mix (tested).
+returns the same iterates and solution alone or in the mix (tested).  With 2
+or 4 slots the session is a shared-matrix ("lanes") session: the base matrix
+is stored once, the slots' vectors are interleaved, and every matrix row is
+read once for all slots.
 """
 from __future__ import annotations
 
@@ -55,7 +58,7 @@ class Server:
     def __init__(self, base_problem, slots: int = 8, hbm_budget_gb: float = 150.0, tol: float = 1e-4,
                  max_iter: int = 100_000, value_bits: int = 64, warm_start: bool = True,
                  replays_per_step: int = 4, presolve_workers: int = 8, keep_solutions: bool = False,
-                 warm_policy: str = "dual"):
+                 warm_policy: str = "dual", lanes: bool | None = None):
         if warm_policy not in ("dual", "full"):
             raise ValueError("warm_policy must be 'dual' or 'full'")
         self.warm_policy = warm_policy
@@ -73,7 +76,10 @@ class Server:
         fit = max(1, int(hbm_budget_gb * 1e9 // per_slot))
         self.slots = max(1, min(slots, fit))
         self.bytes_per_slot = per_slot
-        self.sess = B.Session([self.base_ps] * self.slots, tol=tol, max_iter=max_iter)
+        # 2 or 4 slots share one stored matrix and interleave their vectors
+        # (a lanes session) unless told otherwise
+        self.lanes = (self.slots in (2, 4)) if lanes is None else (bool(lanes) and self.slots in (2, 4))
+        self.sess = B.Session([self.base_ps] * self.slots, tol=tol, max_iter=max_iter, lanes=self.lanes)
         self.pool = cf.ThreadPoolExecutor(max_workers=presolve_workers)
         self.library: list[tuple] = []   # (load, x, y, rid, omega) of solved requests
 
@@ -179,7 +185,7 @@ class Server:
                         sim_t = max(sim_t, reqs[nxt].arrival)
         lat = np.array([r.latency for r in reqs])
         span = max(r.finished for r in reqs) - min(r.arrival for r in reqs)
-        return {"requests": len(reqs), "slots": self.slots, "bytes_per_slot": self.bytes_per_slot,
+        return {"requests": len(reqs), "slots": self.slots, "lanes": self.lanes, "bytes_per_slot": self.bytes_per_slot,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "throughput_req_per_s": len(reqs) / span,
                 "makespan_s": span, "gpu_busy_s": gpu_busy,

@@ -95,7 +95,13 @@ class Tuner:
             if k in self.cache:
                 e = self.cache[k]
                 return int(e["cta_rows"]), int(e["rows_per_thread"])
-        times = {(c, r): self.time_choice(ps, r, c) for c in CTA_CHOICES for r in CHOICES if r <= 2}
+        # two rounds, interleaved, best of both: the choices differ by a few
+        # percent, about as much as one short timing varies
+        pairs = [(c, r) for c in CTA_CHOICES for r in CHOICES if r <= 2]
+        times = {p: float("inf") for p in pairs}
+        for _ in range(2):
+            for c, r in pairs:
+                times[(c, r)] = min(times[(c, r)], self.time_choice(ps, r, c))
         best = min(times, key=times.get)
         with self._lock:
             self.cache[k] = {"cta_rows": best[0], "rows_per_thread": best[1],

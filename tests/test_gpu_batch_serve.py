@@ -68,14 +68,16 @@ def test_presolve_reuse_matches_full_presolve(B):
         B.uc_presolve_reuse(ps0, B.uc_build_lp(other))
 
 
-def test_server_results_same_alone_and_in_the_mix(B):
+@pytest.mark.parametrize("slots", [3, 4])   # block-diagonal slots; a shared-matrix (lanes) session
+def test_server_results_same_alone_and_in_the_mix(B, slots):
     from paper_2607_03627_gb300.serve import Request, Server
     base = ucgen.tiny(0)
     reqs = [Request(rid=r, problem=ucgen.served_request(base, 0, r), arrival=0.05 * r) for r in range(8)]
-    srv = Server(base, slots=3, tol=KKT_TOL, keep_solutions=True, replays_per_step=2, presolve_workers=4)
+    srv = Server(base, slots=slots, tol=KKT_TOL, keep_solutions=True, replays_per_step=2, presolve_workers=4)
     m = srv.serve(reqs, realtime=False)
     srv.close()
-    assert m["all_optimal"] and m["slots"] == 3 and m["warm_started"] >= 1
+    assert m["all_optimal"] and m["slots"] == slots and m["warm_started"] >= 1
+    assert m["lanes"] == (slots == 4)
     assert any(r.admitted > 0 and r.slot >= 0 for r in reqs)
     base_ps = B.uc_presolve(B.uc_build_lp(base))
     for r in reqs:
