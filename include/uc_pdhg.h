@@ -38,7 +38,8 @@ extern "C" {
 #define UC_OK 0
 #define UC_EINVAL (-1)       /* bad sizes or indices, non-positive reactance, self loop */
 #define UC_ENOMEM (-2)       /* host or device allocation failed / budget exceeded */
-#define UC_EINFEASIBLE (-3)  /* presolve proved the LP infeasible */
+#define UC_EINFEASIBLE (-3)  /* presolve, or a Farkas direction found by the Halpern solve, proved
+                                the LP infeasible */
 #define UC_EUNBOUNDED (-4)   /* presolve proved the LP unbounded */
 #define UC_EITERLIMIT (-5)   /* max_iter reached before the tolerance (result valid) */
 #define UC_ETIMEOUT (-6)     /* timeout_ms elapsed (result valid, last iterate) */
@@ -136,7 +137,8 @@ typedef struct {
 } uc_solve_opts;
 
 typedef struct {
-    int status;                  /* UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ENUMERIC, UC_ECANCELLED */
+    int status;                  /* UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ENUMERIC, UC_ECANCELLED,
+                                    UC_EINFEASIBLE */
     int iters;                   /* PDHG iterations taken */
     int restarts;
     int evals;
@@ -255,7 +257,11 @@ int uc_get_solution(const uc_result *res, double *p, double *u, double *v, doubl
 int uc_get_raw_solution(const uc_result *res, double *x, double *y);
 /* Presolved-space, SCALED iterates: which = 0 current iterate, 1 the average
  * since the last restart (averaging variant) or the restart anchor (Halpern
- * variant), 2 returned point (Halpern: the last PDHG map output); x [n], y [m]. */
+ * variant), 2 returned point (Halpern: the last PDHG map output), 3 (status
+ * UC_EINFEASIBLE only) the Farkas direction that proved the LP infeasible:
+ * y_hat - y_in of the last step, x zeros; x [n], y [m].  Unscaled, the
+ * direction is D_r y: y_I >= 0, -A^T D_r y lies in the cone the bounds allow
+ * and its dual objective is positive, each up to a relative 1e-8. */
 int uc_get_iterate(const uc_result *res, int which, double *x, double *y);
 
 /* Device view of a presolved, scaled LP as uc_presolved_export returns it,

@@ -19,6 +19,14 @@ feasibility tolerance of 1e-5 (Sec. II-D).  The relative criterion is PDLP's
 
 The weighted error that drives restarts is
   KKT_w = sqrt(w^2 ||r_p||^2 + ||r_d||^2 / w^2 + (c.x - dual)^2).
+
+Primal infeasibility (Farkas): the LP has no feasible point if some direction
+y of the dual problem with c = 0 has y_I >= 0, a reduced cost lam = -A^T y
+that the bounds allow (lam_proj = lam) and a positive dual objective
+q.y + sum_j l_j max(lam_j, 0) + u_j min(lam_j, 0).  A numerical direction is
+accepted when that objective is positive and the largest violation (of
+lam = lam_proj and of y_I >= 0, infinity norm) is at most eps times it
+(PDLP's primal-infeasibility test, eps = 1e-8).
 """
 from __future__ import annotations
 
@@ -82,6 +90,29 @@ def relative_kkt(lp, x, y):
 
 def weighted_kkt(rp_sq: float, rd_sq: float, gap: float, omega: float) -> float:
     return float(np.sqrt(omega * omega * rp_sq + rd_sq / (omega * omega) + gap * gap))
+
+
+INFEASIBLE_EPS = 1e-8
+
+
+def farkas_ray(lp, y):
+    """(objective, violation) of y as a primal-infeasibility direction of the
+    LP object (fields A, q, l, u, m_eq); see the module docstring."""
+    lam = -(lp.A.T @ y)
+    lp_ = project_reduced_cost(lam, lp.l, lp.u)
+    lf = np.isfinite(lp.l)
+    uf = np.isfinite(lp.u)
+    obj = float(np.dot(lp.q, y))
+    obj += float(np.sum(lp.l[lf] * np.maximum(lp_[lf], 0.0)))
+    obj += float(np.sum(lp.u[uf] * np.minimum(lp_[uf], 0.0)))
+    viol = max(float(np.max(np.abs(lam - lp_), initial=0.0)),
+               float(np.max(np.maximum(-y[lp.m_eq:], 0.0), initial=0.0)))
+    return obj, viol
+
+
+def is_infeasibility_certificate(lp, y, eps: float = INFEASIBLE_EPS) -> bool:
+    obj, viol = farkas_ray(lp, y)
+    return obj > 0.0 and viol <= eps * obj
 
 
 def abs_primal_inf(lp, x) -> float:

@@ -41,6 +41,16 @@ constant step.  With T the PDHG map above and z = (x, y):
           on restart: omega from dx = ||x_hat - x0||, dy = ||y_hat - y0||,
           z = z0 = z_hat, j = 0, r_anchor = r re-weighted with the new omega.
 The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr".
+
+Infeasibility detection (Halpern variant).  When the LP has no feasible point,
+the map has no fixed point and the step residual T(z) - z tends to a nonzero
+direction (the infimal displacement vector of the nonexpansive PDHG map).  At
+every 4th evaluation, after the stopping test and before the restart test,
+the dual part of the last step's residual, y_hat - y_in (mapped to the
+unscaled LP), is tested as a Farkas direction (kkt.farkas_ray); when it passes,
+the solve stops with status "infeasible".  The UC LP's feasible set is
+bounded (every column has finite bounds or is tied to bounded columns), so
+its objective cannot be unbounded and only this test is needed.
 """
 from __future__ import annotations
 
@@ -80,7 +90,7 @@ class Result:
     x: np.ndarray          # scaled presolved primal (returned point)
     y: np.ndarray          # scaled presolved dual
     iters: int
-    status: str            # "optimal" | "iteration_limit"
+    status: str            # "optimal" | "iteration_limit" | "infeasible" (Halpern)
     rel: tuple             # (rel_p, rel_d, rel_gap) of the returned point
     restarts: int
     omega: float
@@ -235,6 +245,10 @@ class HState:
     k: int
     metric: str
     restarts: int = 0
+    evals: int = 0
+
+
+INFEAS_EVERY = 4      # evaluations between infeasibility tests
 
 
 def halpern_initial_state(S, x0=None, y0=None, metric: str = "kkt", omega0=None) -> HState:
@@ -271,10 +285,17 @@ def halpern_step(S, st: HState, AT=None):
 
 
 def halpern_evaluate(S, st: HState, U, tol: float):
-    """Evaluation after an n_eval block: (done, point, rel); applies a restart."""
+    """Evaluation after an n_eval block: (status, point, rel) with status None
+    (continue), "optimal" or "infeasible" (point = the Farkas direction, scaled
+    dual space); applies a restart."""
+    st.evals += 1
     rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)
     if max(rel) <= tol:
-        return True, (st.xh.copy(), st.yh.copy()), rel
+        return "optimal", (st.xh.copy(), st.yh.copy()), rel
+    if st.evals % INFEAS_EVERY == 0:
+        ray = st.yh - st.y_in
+        if kkt.is_infeasibility_certificate(U, S.Dr * ray):
+            return "infeasible", (np.zeros_like(st.xh), ray), rel
     w = st.omega
     fx2 = float(np.dot(st.x_in - st.xh, st.x_in - st.xh))
     fy2 = float(np.dot(st.y_in - st.yh, st.y_in - st.yh))
@@ -300,7 +321,7 @@ def halpern_evaluate(S, st: HState, U, tol: float):
         st.restarts += 1
     else:
         st.r_prev = r
-    return False, None, rel
+    return None, None, rel
 
 
 def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
@@ -315,10 +336,11 @@ def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N
     while st.k < max_iter:
         halpern_step(S, st, AT)
         if st.k % n_eval == 0:
-            done, pt, rel = halpern_evaluate(S, st, U, tol)
-            if done:
-                return Result(x=pt[0], y=pt[1], iters=st.k, status="optimal", rel=rel,
-                              restarts=st.restarts, omega=st.omega, state=st, which="map")
+            status, pt, rel = halpern_evaluate(S, st, U, tol)
+            if status is not None:
+                return Result(x=pt[0], y=pt[1], iters=st.k, status=status, rel=rel,
+                              restarts=st.restarts, omega=st.omega, state=st,
+                              which="map" if status == "optimal" else "ray")
         if trace is not None and st.k in trace_iters:
             trace(st.k, st)
     rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)

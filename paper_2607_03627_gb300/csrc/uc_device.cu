@@ -46,7 +46,14 @@ constexpr int kPart = 2 * kSlots;  // per-block partial record (current, average
 
 enum Slot { RP2 = 0, RPU, QY, DY2, RD2, RDU, CX, BND, DX2 };
 enum Status { RUNNING = 0, OPTIMAL = 1, ITER_LIMIT = 2, NUMERIC = 3, NEEDS_INIT = 4,
-              STALLED = 5 };   // STALLED: a staged kernel gave up waiting for its copies
+              STALLED = 5,     // a staged kernel gave up waiting for its copies
+              INFEASIBLE = 6 };  // a Farkas direction proved the LP primal infeasible
+// Halpern variant: every kInfeasEvery-th evaluation tests the dual part of the
+// last step's residual, y_hat - y_in, as a primal-infeasibility (Farkas)
+// direction; accepted when its objective is positive and its largest
+// violation is at most kInfeasEps times that objective (PDLP's test)
+constexpr int kInfeasEvery = 4;
+constexpr double kInfeasEps = 1e-8;
 enum Action { ACT_NONE = 0, ACT_RESTART = 1, ACT_FINISH = 2 };
 enum Algo { ALG_HALPERN = 0, ALG_AVERAGE = 1 };
 enum Metric { METRIC_KKT = 0, METRIC_FPR = 1 };
@@ -123,9 +130,11 @@ __device__ __forceinline__ double nonneg(double v) {
 }
 
 __device__ __forceinline__ double widen(double v) { return v; }
-// read-once streams (matrix, row pointers, constant vectors, the input iterate)
-// are loaded evict-first so that the vector the previous kernel just wrote,
-// which this kernel gathers at random, stays in L2
+// read-once streams (matrix entries, constant vectors, the input iterate) are
+// loaded evict-first so that the vector the previous kernel just wrote, which
+// this kernel gathers at random, stays in L2.  The row pointers (4 bytes a row)
+// are loaded with normal priority and stay in L2 from one iteration to the
+// next: they head each row's chain of dependent loads.
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 __device__ __forceinline__ double widen(float f) {
@@ -168,8 +177,9 @@ constexpr int kPre = 3;   // row entries whose index and value are loaded before
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
 // the last step of a block (and at the iteration limit).
-// 1152 resident threads per SM (56 registers for 128-thread CTAs): measured a
-// little faster than 1280 threads at 48 registers, which spilled
+// 1152 resident threads per SM (56 registers for 128-thread CTAs) for the
+// primal kernel and 1280 (48 registers) for the dual kernel: the fastest pair
+// of a sweep over 1024, 1152 and 1280 threads
 template <typename VT, int ALGO, int BS>
 __global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict_
         const int j = sg.begin + t * BS + threadIdx.x;
         if (j >= sg.end) break;
         // independent of the dual kernel that precedes this one
-        const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
+        const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
         const double xin = ld_stream(b.x[src] + j);
         const long long lk = ld_stream(b.lkey + j), uk = ld_stream(b.ukey + j);
         const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : ld_stream(b.xa + j);
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict_
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1152 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
+__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
     const Seg sg = segs[blockIdx.x];
     const Scalars *S = b.S + sg.inst;
     const int k = S->k_base + it;
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_dual(const Seg *__restrict__ 
     for (int t = 0; t < sg.rpt; t++) {
         const int i = sg.begin + t * BS + threadIdx.x;
         if (i >= sg.end) break;
-        const int k0 = ld_stream(b.A_rp + i), k1 = ld_stream(b.A_rp + i + 1);
+        const int k0 = __ldg(b.A_rp + i), k1 = __ldg(b.A_rp + i + 1);
         const double yin = ld_stream(b.y[src] + i);
         const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : ld_stream(b.ya + i);
         int ci[kPre];
@@ -596,7 +606,7 @@ __global__ void __launch_bounds__(BS) k_primal_lanes(const Seg *__restrict__ seg
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const size_t e = (size_t)j * K + 2 * p;   // this thread's first element
     // independent of the dual kernel that precedes this one
-    const int k0 = ld_stream(b.AT_rp + j), k1 = ld_stream(b.AT_rp + j + 1);
+    const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
     const double2 xin = ld_stream(reinterpret_cast<const double2 *>(b.x[src] + e));
     const longlong2 lk = ld_stream(reinterpret_cast<const longlong2 *>(b.lkey + e));
     const longlong2 uk = ld_stream(reinterpret_cast<const longlong2 *>(b.ukey + e));
@@ -660,7 +670,7 @@ __global__ void __launch_bounds__(BS) k_dual_lanes(const Seg *__restrict__ segs,
     if (i >= sg.end || !(l0 || l1)) { pdl_wait(); pdl_trigger(); return; }
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
     const size_t e = (size_t)i * K + 2 * p;
-    const int k0 = ld_stream(b.A_rp + i), k1 = ld_stream(b.A_rp + i + 1);
+    const int k0 = __ldg(b.A_rp + i), k1 = __ldg(b.A_rp + i + 1);
     const double2 yin = ld_stream(reinterpret_cast<const double2 *>(b.y[src] + e));
     const double2 y0 = ld_stream(reinterpret_cast<const double2 *>(b.ya + e));
     int ci[kPre];
@@ -841,6 +851,10 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
     if (live) {
         const bool halp = S->algo == ALG_HALPERN && mode == 1;
         const bool fpr = halp && S->metric == METRIC_FPR;   // fixed-point residual terms needed
+        // infeasibility direction dy = y_hat - y_in: q.dy in slot QY, the bound part
+        // of its objective in BND, the y_I < 0 and reduced-cost cone violations
+        // (unscaled) as maxima in RPU and RDU, all of the second record
+        const bool ray = halp && (S->evals + 1) % kInfeasEvery == 0;
         const bool avg = S->algo == ALG_AVERAGE && mode == 1;
         const double inv_j = avg ? 1.0 / (double)(S->j_base + S->n_eval) : 0.0;
         const double *x = halp ? b.xret : b.x[0];
@@ -879,16 +893,22 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     const double d = b.y[1][ii] - y0;
                     acc[kSlots + DY2] += d * d;
                 }
+                if (ray) {
+                    const double dy = y0 - b.y[1][ii];
+                    acc[kSlots + QY] += qi * dy;
+                    if (ineq) acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fmax(-dy, 0.0) * b.Dr[ii]);
+                }
             }
         } else {
             const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
             for (int j = sg.begin + threadIdx.x; j < sg.end; j += kThreads) {
-                double t0 = 0.0, t1 = 0.0;
+                double t0 = 0.0, t1 = 0.0, tr = 0.0;
                 for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) {
                     const size_t i = at(b.AT_ci[k]);
                     const double a = widen(v[k]);
                     t0 += a * y[i];
                     if (avg) t1 += a * (b.ysum[i] * inv_j);
+                    if (ray) tr += a * (y[i] - b.y[1][i]);
                 }
                 const size_t jj = at(j);
                 const double cj = b.c[jj], lj = b.l[jj], uj = b.u[jj], idc = b.inv_Dc[jj], xh = b.xa[jj];
@@ -914,6 +934,15 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 if (fpr) {
                     const double d = b.x[1][jj] - x[jj];
                     acc[kSlots + DX2] += d * d;
+                }
+                if (ray) {   // reduced cost of the direction: lam = -A^T dy
+                    const double lm = -tr;
+                    const double lp = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
+                    double bnd = 0.0;
+                    if (lf) bnd += lj * fmax(lp, 0.0);
+                    if (uf) bnd += uj * fmin(lp, 0.0);
+                    acc[kSlots + BND] += bnd;
+                    acc[kSlots + RDU] = nnmax(acc[kSlots + RDU], fabs(lm - lp) * idc);
                 }
             }
         }
@@ -1012,6 +1041,15 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
             S->which = 0;
             b.status[inst] = S->status;
             return;
+        }
+        if (S->evals % kInfeasEvery == 0) {
+            const double obj = T[kSlots + QY] + T[kSlots + BND];
+            const double viol = fmax(T[kSlots + RPU], T[kSlots + RDU]);
+            if (obj > 0.0 && viol <= kInfeasEps * obj) {
+                S->status = INFEASIBLE;
+                b.status[inst] = S->status;
+                return;
+            }
         }
         const double r = (S->metric == METRIC_KKT) ? K[0] : sqrt(w * fx2 + fy2 / w);
         const bool restart = (r <= 0.2 * S->kkt_anchor) ||
@@ -2196,8 +2234,19 @@ static int session_result(uc_session &X, int i, uc_result **out) {
         rc = d2h(res->x_ret, X.b.xret, cx, n);
         if (!rc) rc = d2h(res->y_ret, X.b.yret, cy, m);
     }
+    // infeasible: the Farkas direction y_hat - y_in (y_in = buffer 1 at a block end)
+    std::vector<double> y_in;
+    if (!rc && S.status == INFEASIBLE) {
+        y_in.resize(m);
+        rc = d2h(y_in, X.b.y[1], cy, m);
+    }
     if (rc) return rc;
     UC_CUDA(cudaStreamSynchronize(s));
+    if (S.status == INFEASIBLE) {
+        res->y_ray.resize(m);
+        for (int r = 0; r < m; r++) res->y_ray[r] = res->y_ret[r] - y_in[r];
+        if (X.reorder) to_natural(res->y_ray, X.prow[i]);
+    }
     if (!halp) {
         for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
         for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
@@ -2212,6 +2261,7 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     if (S.status == OPTIMAL) status = UC_OK;
     else if (S.status == ITER_LIMIT) status = UC_EITERLIMIT;
     else if (S.status == NUMERIC) status = UC_ENUMERIC;
+    else if (S.status == INFEASIBLE) status = UC_EINFEASIBLE;
     else if (S.status == STALLED) {
         status = UC_ECUDA;
         set_error("a staged iteration kernel stopped waiting for its shared-memory copies");
@@ -2496,6 +2546,7 @@ int uc_session_status(const uc_session *s, int i) {
         case dev::OPTIMAL: return UC_OK;
         case dev::ITER_LIMIT: return UC_EITERLIMIT;
         case dev::NUMERIC: return UC_ENUMERIC;
+        case dev::INFEASIBLE: return UC_EINFEASIBLE;
         case dev::STALLED: return UC_ECUDA;
         default: return 1;
     }

@@ -698,7 +698,12 @@ int uc_get_iterate(const uc_result *res, int which, double *x, double *y) {
         case 0: xs = &res->x_cur; ys = &res->y_cur; break;
         case 1: xs = &res->x_avg; ys = &res->y_avg; break;
         case 2: xs = &res->x_ret; ys = &res->y_ret; break;
-        default: set_error("uc_get_iterate: which must be 0, 1 or 2"); return UC_EINVAL;
+        case 3:   // the Farkas direction of an infeasible result (x: zeros)
+            if (res->y_ray.empty()) { set_error("uc_get_iterate: the result holds no infeasibility direction"); return UC_EINVAL; }
+            if (x) std::memset(x, 0, res->x_ret.size() * 8);
+            if (y) std::memcpy(y, res->y_ray.data(), res->y_ray.size() * 8);
+            return UC_OK;
+        default: set_error("uc_get_iterate: which must be 0, 1, 2 or 3"); return UC_EINVAL;
     }
     if (x) std::memcpy(x, xs->data(), xs->size() * 8);
     if (y) std::memcpy(y, ys->data(), ys->size() * 8);

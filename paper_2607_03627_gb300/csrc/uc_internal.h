@@ -86,5 +86,6 @@ struct uc_result {
     std::vector<double> x_ret, y_ret;   // returned point (scaled presolved)
     std::vector<double> x_cur, y_cur;   // current iterate
     std::vector<double> x_avg, y_avg;   // average since the last restart
+    std::vector<double> y_ray;          // primal infeasibility direction (infeasible status only)
     uc_stats stats{};
 };
