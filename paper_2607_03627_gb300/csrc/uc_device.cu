@@ -1189,7 +1189,8 @@ struct Layout {
     size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status;
     // staged kernels: chunk lists and per-CTA ranges
     size_t chunks_p, chunks_d, ctas_p, ctas_d;
-    // lanes sessions: contiguous staging for one LP's vectors (3 (n + m) doubles)
+    // lanes sessions: contiguous staging for one LP's vectors (4 (n + m) doubles:
+    // the seven vectors a result may download)
     size_t lane_stage;
     size_t upload_end, total;
 };
@@ -1933,7 +1934,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     L.xsum = take(N * 8); L.ysum = take(M * 8); L.xa = take(N * 8); L.ya = take(M * 8);
     L.xret = take(N * 8); L.yret = take(M * 8);
     L.part = take(sizeof(double) * kPart * X->n_se * X->K);
-    L.lane_stage = take(X->K > 1 ? (size_t)3 * (Nr + Mr) * 8 : 0);
+    L.lane_stage = take(X->K > 1 ? (size_t)4 * (Nr + Mr) * 8 : 0);
     L.red = take(sizeof(double) * kPart * k);
     L.S = take(sizeof(Scalars) * k);
     L.status = take(sizeof(int) * k);
@@ -2064,6 +2065,10 @@ static int lane_upload(uc_session &X, double *dev_vec, int lane, const void *hos
 }
 static int lane_download(uc_session &X, void *host, const double *dev_vec, int lane, int count, size_t stage_off) {
     if (!count) return UC_OK;
+    if (stage_off + (size_t)count > (size_t)4 * (X.Nr + X.Mr)) {
+        set_error("lanes staging area too small");
+        return UC_ECUDA;
+    }
     double *stage = (double *)(X.D + X.L.lane_stage) + stage_off;
     k_lane_copy<<<(count + 255) / 256, 256, 0, X.s>>>(stage, dev_vec, count, X.K, lane, 1);
     UC_CUDA(cudaGetLastError());
@@ -2212,7 +2217,8 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     res->x_cur.resize(n); res->y_cur.resize(m); res->x_avg.resize(n); res->y_avg.resize(m);
     const size_t cx = X.coff[i], cy = X.roff[i];
     // LP i's elements of a device vector (contiguous, or lane i of a lanes
-    // session through its staging area: up to six vectors, 3 (n + m) doubles)
+    // session through its staging area: up to seven vectors, 3 n + 4 m doubles,
+    // within its 4 (n + m))
     size_t stage_off = 0;
     auto d2h = [&](std::vector<double> &dst, const double *base, size_t off, int count) -> int {
         if (X.K == 1) {
