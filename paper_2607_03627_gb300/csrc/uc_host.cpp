@@ -12,6 +12,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -98,6 +101,81 @@ static double sumsq(const std::vector<double> &v, int threads) {
     for (double p : part) s += p;
     return s;
 }
+
+// Worker threads kept for a loop of many parallel steps (the power
+// iteration): run(n, fn) splits [0, n) into the same fixed 16384-element
+// chunks as parallel_for and returns when every chunk is done, so results do
+// not depend on the number of threads.
+class Pool {
+public:
+    explicit Pool(int threads) {
+        for (int t = 1; t < threads; t++) th_.emplace_back([this] { loop(); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+            gen_++;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    void run(int64_t n, const std::function<void(int64_t, int64_t)> &fn) {
+        const int64_t chunk = 1 << 14;
+        const int64_t nch = (n + chunk - 1) / chunk;
+        if (th_.empty() || nch <= 1) {
+            if (n > 0) fn(0, n);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            fn_ = &fn;
+            n_ = n;
+            nch_ = nch;
+            next_.store(0);
+            busy_ = (int)th_.size();
+            gen_++;
+        }
+        cv_.notify_all();
+        work();
+        std::unique_lock<std::mutex> g(mu_);
+        done_.wait(g, [this] { return busy_ == 0; });
+    }
+
+private:
+    void work() {
+        const int64_t chunk = 1 << 14;
+        for (;;) {
+            const int64_t c = next_.fetch_add(1);
+            if (c >= nch_) return;
+            (*fn_)(c * chunk, std::min(n_, (c + 1) * chunk));
+        }
+    }
+    void loop() {
+        int seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> g(mu_);
+                cv_.wait(g, [&] { return gen_ != seen; });
+                seen = gen_;
+                if (stop_) return;
+            }
+            work();
+            {
+                std::lock_guard<std::mutex> g(mu_);
+                if (--busy_ == 0) done_.notify_one();
+            }
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int64_t, int64_t)> *fn_ = nullptr;
+    int64_t n_ = 0, nch_ = 0;
+    std::atomic<int64_t> next_{0};
+    int busy_ = 0, gen_ = 0;
+    bool stop_ = false;
+};
 
 static void spmv(const Csr &A, const std::vector<double> &x, std::vector<double> &y, int threads) {
     y.resize(A.rows);
@@ -408,18 +486,45 @@ static void scale_lp(PsData &ps, const uc_presolve_opts &o, int threads) {
     }
 }
 
-// ||A||_2 by power iteration on A^T A from the unit vector 1/sqrt(n)
+// ||A||_2 by power iteration on A^T A from the unit vector 1/sqrt(n).  Every
+// step runs on one pool of workers; the sum of squares adds fixed 16384-element
+// chunk partials in order, so the result does not depend on the thread count.
 static double power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, int threads) {
-    const int n = A.cols;
-    if (n == 0 || A.rows == 0) return 0.0;
-    std::vector<double> v(n, 1.0 / std::sqrt((double)n)), t, w;
+    const int n = A.cols, m = A.rows;
+    if (n == 0 || m == 0) return 0.0;
+    std::vector<double> v(n, 1.0 / std::sqrt((double)n)), t(m), w(n);
+    const int64_t chunk = 1 << 14;
+    const int64_t nch = ((int64_t)n + chunk - 1) / chunk;
+    std::vector<double> part((size_t)nch, 0.0);
+    Pool pool(threads);
+    auto mul = [](const Csr &M, const std::vector<double> &x, std::vector<double> &y) {
+        return [&M, &x, &y](int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; i++) {
+                double s = 0.0;
+                for (int32_t k = M.rowptr[i]; k < M.rowptr[i + 1]; k++) s += M.val[k] * x[M.colidx[k]];
+                y[i] = s;
+            }
+        };
+    };
+    const std::function<void(int64_t, int64_t)> fa = mul(A, v, t), fat = mul(AT, t, w);
     double lam = 0.0, prev = 0.0;
+    const std::function<void(int64_t, int64_t)> fsq = [&](int64_t b, int64_t e) {
+        double s = 0.0;
+        for (int64_t i = b; i < e; i++) s += w[i] * w[i];
+        part[b / chunk] = s;
+    };
+    const std::function<void(int64_t, int64_t)> fdiv = [&](int64_t b, int64_t e) {
+        for (int64_t j = b; j < e; j++) v[j] = w[j] / lam;
+    };
     for (int it = 0; it < max_iter; it++) {
-        spmv(A, v, t, threads);
-        spmv(AT, t, w, threads);
-        lam = std::sqrt(sumsq(w, threads));
+        pool.run(m, fa);
+        pool.run(n, fat);
+        pool.run(n, fsq);
+        double s = 0.0;
+        for (double p : part) s += p;
+        lam = std::sqrt(s);
         if (lam == 0.0) return 0.0;
-        for (int j = 0; j < n; j++) v[j] = w[j] / lam;
+        pool.run(n, fdiv);
         if (std::fabs(lam - prev) <= tol * lam) break;
         prev = lam;
     }
