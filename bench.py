@@ -561,7 +561,10 @@ def run_served(args):
             "data": "synthetic", "config": {"workload": f"{len(reqs)} requests on the 6049-bus / 700-unit / 48-period grid, "
                                             "load x{0.80..1.20} + AR(1) 5%, Poisson 2 req/s",
                                             "slots": m["slots"], "hbm_budget_gb": 150.0, "tol_rel_kkt": TOL},
-            "served": m, "clocks": clk.summary(), "impl": "ours"}
+            "served": m, "clocks": clk.summary(), "impl": "ours",
+            "per_request": [{"rid": r.rid, "iters": r.iters, "status": r.status, "warm_from": r.warm_from,
+                             "latency_s": r.latency, "omega": r.omega, "start_omega": r.start_omega}
+                            for r in sorted(reqs, key=lambda r: r.rid)]}
     if not args.no_sequential:
         line["sequential_fp64_cold"] = sequential_baseline(reqs, base, tol=TOL, max_iter=args.max_iter)
     print(json.dumps(line), flush=True)

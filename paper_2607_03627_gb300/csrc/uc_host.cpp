@@ -123,8 +123,8 @@ public:
     void run(int64_t n, const std::function<void(int64_t, int64_t)> &fn) {
         const int64_t chunk = 1 << 14;
         const int64_t nch = (n + chunk - 1) / chunk;
-        if (th_.empty() || nch <= 1) {
-            if (n > 0) fn(0, n);
+        if (th_.empty() || nch <= 1) {   // the same chunks, in order, on this thread
+            for (int64_t c = 0; c < nch; c++) fn(c * chunk, std::min(n, (c + 1) * chunk));
             return;
         }
         {

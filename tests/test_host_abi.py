@@ -111,3 +111,16 @@ def test_presolve_reports_infeasible(B):
     P.fmax[:] = 0.0                             # f fixed at 0 -> balance row empty with rhs 5
     with pytest.raises(B.UCError, match="infeasible"):
         B.uc_presolve(B.uc_build_lp(P))
+
+
+def test_presolve_does_not_depend_on_the_thread_count(B):
+    # large enough that every parallel loop (scaling, power iteration) runs many chunks
+    P = ucgen.make_problem(2, B=400, L=530, G=48, T=24, lo=0.5, hi=0.85, noise=0.05, zero_pmin_frac=0.1)
+    lp = B.uc_build_lp(P)
+    ref = B.uc_presolved_export(B.uc_presolve(lp, threads=1))
+    for th in (2, 3, 8):
+        d = B.uc_presolved_export(B.uc_presolve(lp, threads=th))
+        for k in ("rowptr", "colidx", "val", "q", "c", "l", "u", "Dr", "Dc"):
+            np.testing.assert_array_equal(d[k], ref[k], err_msg=f"{k} threads={th}")
+        for k in ("eta", "omega0", "norm_A"):
+            assert d[k] == ref[k], (k, th)
