@@ -201,19 +201,22 @@ int uc_presolved_export(const uc_presolved *ps, int32_t *rowptr, int32_t *colidx
  * LP) or at max_iter.  `stream` is a cudaStream_t (NULL: legacy default).
  * The solve is synchronous: it returns when the device work has finished.
  * Returns the solve status; *out is set (and must be freed) whenever the
- * status is UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ECANCELLED or UC_ENUMERIC. */
+ * status is UC_OK, UC_EITERLIMIT, UC_ETIMEOUT, UC_ECANCELLED, UC_ENUMERIC or
+ * UC_EINFEASIBLE (a Farkas direction was found; see uc_get_iterate). */
 int uc_solve(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc_result **out);
 
 /* Solve k presolved LPs at once: their matrices are packed block-diagonally
- * and every iteration launches one primal and one dual kernel for all of
- * them; each LP keeps its own step sizes, restarts and stopping test and
- * freezes when it converges.  outs[i] receives LP i's result.  Returns UC_OK
- * if every LP reached the tolerance, else the first non-OK status. */
+ * (or, with opts->lanes, stored once for 2 or 4 LPs that share it) and every
+ * iteration launches one primal and one dual kernel for all of them; each LP
+ * keeps its own step sizes, restarts and stopping test and freezes when it
+ * converges.  outs[i] receives LP i's result.  Returns UC_OK if every LP
+ * reached the tolerance, else the first non-OK status. */
 int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
                    uc_result **outs);
 
 /* Device-resident sessions.  A session uploads k presolved LPs once (matrices
- * block-diagonal, per-LP vectors, start points, CUDA graph of n_eval
+ * block-diagonal, or one shared matrix with interleaved vectors when
+ * opts->lanes is set; per-LP vectors, start points, CUDA graph of n_eval
  * iterations) and then solves them any number of times; it is what uc_solve
  * and uc_solve_batch use internally, and what a server uses to keep
  * instances resident, warm-start re-solves and refill finished slots while

@@ -1200,7 +1200,6 @@ struct Layout {
 
 struct uc_session {
     int k = 0, vb = 64;
-    int kernel = 1;               // 1 thread per row
     int cta = 128;                // rows (= threads) per CTA of the row kernels
     bool pdl = true;              // programmatic dependent launch between iteration kernels
     cudaError_t launch_err = cudaSuccess;
@@ -1813,7 +1812,6 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         set_error("algorithm and restart_metric must be 0 or 1");
         return UC_EINVAL;
     }
-    X->kernel = 1;
     X->algo = o.algorithm;
     if (o.cta_rows != 0 && o.cta_rows != 128 && o.cta_rows != 256 && o.cta_rows != 512) {
         set_error("cta_rows must be 0, 128, 256 or 512");
