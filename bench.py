@@ -323,7 +323,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(P, args.cpu_iters)
+        cpu = cpu_baseline(P, args.cpu_iters, desc["workload"], simplex=args.config == "tiny")
 
     if rank == 0:
         line = {
@@ -356,10 +356,12 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(P, iters):
+def cpu_baseline(P, iters, workload, simplex=False):
     """The oracle PDHG as it stands, single core, on a bounded sample of the
     workload: `iters` iterations (evaluations every 64 included) on the same LP
-    the oracle builds, presolves and scales itself (that set-up is not timed)."""
+    the oracle builds, presolves and scales itself (that set-up is not timed).
+    With `simplex` (the 30-bus workload only) the oracle's dense simplex is
+    timed on the presolved LP as well."""
     from oracle import lp as olp, pdhg, presolve as ops
     raw = olp.build_lp(P)
     ps = ops.presolve(raw)
@@ -373,10 +375,17 @@ def cpu_baseline(P, iters):
         if st.k % pdhg.N_EVAL == 0:
             pdhg.halpern_evaluate(S, st, U, TOL)
     dt = time.perf_counter() - t0
-    return {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} PDHG iterations (with {iters // 64} KKT/restart evaluations) of the oracle "
-                      f"on the same 6049-bus LP; oracle build/presolve/scaling not timed",
-            "seconds": dt}
+    out = {"value": iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{iters} PDHG iterations (with {iters // 64} KKT/restart evaluations) of the oracle "
+                     f"on the same LP ({workload}); oracle build/presolve/scaling not timed",
+           "seconds": dt}
+    if simplex:
+        from oracle import simplex as osx
+        t0 = time.perf_counter()
+        r = osx.solve_lp(ps.lp)
+        out["simplex"] = {"seconds": time.perf_counter() - t0, "status": r.status, "objective": r.obj,
+                          "iterations": r.iters, "note": "oracle dense bounded simplex, one core"}
+    return out
 
 
 def run_reference(args):
