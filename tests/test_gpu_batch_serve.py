@@ -103,3 +103,24 @@ def test_server_respects_hbm_budget(B):
     srv = Server(base, slots=8, hbm_budget_gb=2.5 * per / 1e9)
     assert srv.slots == 2
     srv.close()
+
+
+@pytest.mark.parametrize("vbits", [64, 32])
+@pytest.mark.parametrize("K", [1, 64, 65, 200])
+def test_two_rows_per_thread_equal_one_row(B, K, vbits):
+    # the row split changes which thread does a row, never its arithmetic
+    for P in (ucgen.tiny(0), ucgen.make_problem(3, B=300, L=396, G=36, T=24, lo=0.5, hi=0.85, noise=0.05,
+                                                zero_pmin_frac=0.1)):
+        ps = B.uc_presolve(B.uc_build_lp(P), value_bits=vbits)
+        n, m, _, _ = B.uc_presolved_dims(ps)
+        for cta in (128, 256):
+            r1, rc1 = B.uc_solve(ps, tol=0.0, max_iter=K, rows_per_thread=[1], cta_rows=cta)
+            r2, rc2 = B.uc_solve(ps, tol=0.0, max_iter=K, rows_per_thread=[2], cta_rows=cta)
+            assert rc1 == rc2 == B.UC_EITERLIMIT
+            for which in (0, 1, 2):
+                x1, y1 = B.uc_get_iterate(r1, which, n, m)
+                x2, y2 = B.uc_get_iterate(r2, which, n, m)
+                np.testing.assert_array_equal(x1, x2)
+                np.testing.assert_array_equal(y1, y2)
+            s1, s2 = B.uc_get_stats(r1), B.uc_get_stats(r2)
+            assert (s1["restarts"], s1["omega"]) == (s2["restarts"], s2["omega"])
