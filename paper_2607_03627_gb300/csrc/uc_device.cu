@@ -173,6 +173,17 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 constexpr int kPre = 3;   // row entries whose index and value are loaded before the wait
 
+// A session of one LP has uniform tables: CTA c covers rows [c B, c B + B) of
+// B = BS * rpt rows, so its slice follows from blockIdx without loading the
+// table entry (n > 0 marks it; aux = first ">=" row for the dual kernel).
+struct Uniform { int n, aux, rpt; };
+template <int BS>
+__device__ __forceinline__ Seg row_slice(const Seg *__restrict__ segs, const Uniform &u) {
+    if (u.n <= 0) return segs[blockIdx.x];
+    const int begin = (int)blockIdx.x * BS * u.rpt;
+    return Seg{0, begin, min(begin + BS * u.rpt, u.n), u.aux, u.rpt};
+}
+
 // ALGO = ALG_AVERAGE: x+ = clip(x - tau (c - A^T y), l, u), running sum of x+.
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
@@ -180,16 +191,17 @@ constexpr int kPre = 3;   // row entries whose index and value are loaded before
 // 1152 resident threads per SM (56 registers for 128-thread CTAs) for the
 // primal kernel and 1280 (48 registers) for the dual kernel: the fastest pair
 // of a sweep over 1024, 1152 and 1280 threads
+// The loads of a row are issued before the LP's state is read (the addresses
+// are valid either way), so that read overlaps them instead of heading the
+// chain of dependent loads.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src) {
-    const Seg sg = segs[blockIdx.x];
+__global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src,
+                                                           Uniform u) {
+    const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
-    const int k = S->k_base + it;
-    if (S->status != RUNNING || k >= S->max_iter) return;
-    const bool keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
-    bool waited = false;
+    bool waited = false, keep = false;
     for (int t = 0; t < sg.rpt; t++) {
         const int j = sg.begin + t * BS + threadIdx.x;
         if (j >= sg.end) break;
@@ -208,6 +220,11 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict_
         }
         // the accumulator starts at -c, so it ends at A^T y - c
         double acc = -ld_stream(b.c + j);
+        if (t == 0) {   // the LP's state, read while the row's loads are in flight
+            const int k = S->k_base + it;
+            if (S->status != RUNNING || k >= S->max_iter) return;
+            keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
+        }
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
         // a step of the unrolled loop issues only if some lane of the warp needs it
         const unsigned lanes = __activemask();
@@ -237,14 +254,12 @@ __global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict_
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src) {
-    const Seg sg = segs[blockIdx.x];
+__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src,
+                                                         Uniform u) {
+    const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
-    const int k = S->k_base + it;
-    if (S->status != RUNNING || k >= S->max_iter) return;
-    const bool keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
-    bool waited = false;
+    bool waited = false, keep = false;
     for (int t = 0; t < sg.rpt; t++) {
         const int i = sg.begin + t * BS + threadIdx.x;
         if (i >= sg.end) break;
@@ -261,6 +276,11 @@ __global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ 
         }
         // the accumulator starts at -q, so it ends at A x - q
         double acc = -ld_stream(b.q + i);
+        if (t == 0) {   // the LP's state, read while the row's loads are in flight
+            const int k = S->k_base + it;
+            if (S->status != RUNNING || k >= S->max_iter) return;
+            keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
+        }
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
         if (ALGO == ALG_AVERAGE) {
             const double *__restrict__ xn = b.x[src ^ 1];
@@ -1469,9 +1489,8 @@ static void launch_eval(uc_session &X, cudaStream_t s, int mode) {
 // iteration kernels of the session's algorithm
 // Launch an iteration kernel; with `pdl` it may overlap the tail of the
 // iteration kernel before it (programmatic stream serialization).
-template <typename Kern>
-static cudaError_t launch_k(Kern kern, int grid, int block, cudaStream_t s, bool pdl, const Seg *segs,
-                            const Bufs &b, int it, int src) {
+template <typename Kern, typename... Args>
+static cudaError_t launch_k(Kern kern, int grid, int block, cudaStream_t s, bool pdl, Args... args) {
     if (grid <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1483,7 +1502,7 @@ static cudaError_t launch_k(Kern kern, int grid, int block, cudaStream_t s, bool
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, segs, b, it, src);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <typename VT, bool PRIMAL>
@@ -1529,11 +1548,13 @@ static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool pri
         return;
     }
     if (primal) {
-        if (X.vb == 32) e = launch_k(k_primal<float, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
-        else e = launch_k(k_primal<double, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src);
+        const Uniform u = X.k == 1 ? Uniform{(int)X.Nr, 0, X.rpt[0]} : Uniform{0, 0, 0};
+        if (X.vb == 32) e = launch_k(k_primal<float, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
+        else e = launch_k(k_primal<double, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
     } else {
-        if (X.vb == 32) e = launch_k(k_dual<float, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src);
-        else e = launch_k(k_dual<double, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src);
+        const Uniform u = X.k == 1 ? Uniform{(int)X.Mr, X.m_eq[0], X.rpt[0]} : Uniform{0, 0, 0};
+        if (X.vb == 32) e = launch_k(k_dual<float, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
+        else e = launch_k(k_dual<double, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
     }
     if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
 }

@@ -30,7 +30,7 @@ def bucket_of(nnz: int) -> int:
 
 
 class Tuner:
-    def __init__(self, cache_path: str | None = DEFAULT_CACHE, trial_replays: int = 3):
+    def __init__(self, cache_path: str | None = DEFAULT_CACHE, trial_replays: int = 16):
         self.cache_path = cache_path
         self.trial_replays = trial_replays
         self._lock = threading.Lock()
@@ -52,23 +52,26 @@ class Tuner:
 
     def time_choice(self, ps, rpt: int, cta: int = 0) -> float:
         """Milliseconds per PDHG iteration of `ps` with `rpt` rows per thread
-        and `cta` threads per CTA (0: the library default)."""
+        and `cta` threads per CTA (0: the library default): `trial_replays`
+        graph replays of 64 iterations after a warm-up solve, timed on the
+        device."""
         import torch
         n_eval = 64
-        sess = B.Session([ps], tol=0.0, max_iter=n_eval * self.trial_replays, rows_per_thread=[rpt],
-                         cta_rows=cta)
+        replays = max(2, self.trial_replays)
+        sess = B.Session([ps], tol=0.0, max_iter=n_eval * replays, rows_per_thread=[rpt], cta_rows=cta)
         sess.reset(-1)
         sess.run()                       # warm-up (graph already captured)
         s = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         sess.reset(-1)
+        sess.run(1)                      # the reset's start-point evaluation and one replay
         e0.record(s)
-        sess.run()
+        sess.run()                       # the remaining replays, steady state
         e1.record(s)
         torch.cuda.synchronize()
         sess.close()
-        return e0.elapsed_time(e1) / (n_eval * self.trial_replays)
+        return e0.elapsed_time(e1) / (n_eval * (replays - 1))
 
     def choose(self, ps, value_bits: int) -> int:
         nnz = B.uc_presolved_dims(ps)[3]
@@ -96,7 +99,7 @@ class Tuner:
                 e = self.cache[k]
                 return int(e["cta_rows"]), int(e["rows_per_thread"])
         # two rounds, interleaved, best of both: the choices differ by a few
-        # percent, about as much as one short timing varies
+        # percent, so each trial times 15 steady-state replays
         pairs = [(c, r) for c in CTA_CHOICES for r in CHOICES if r <= 2]
         times = {p: float("inf") for p in pairs}
         for _ in range(2):
