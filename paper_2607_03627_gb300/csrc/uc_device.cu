@@ -188,14 +188,15 @@ __device__ __forceinline__ Seg row_slice(const Seg *__restrict__ segs, const Uni
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
 // the last step of a block (and at the iteration limit).
-// 1152 resident threads per SM (56 registers for 128-thread CTAs) for the
-// primal kernel and 1280 (48 registers) for the dual kernel: the fastest pair
-// of a sweep over 1024, 1152 and 1280 threads
+// 1536 resident threads per SM (40 registers, 12 bytes spilled to L1) for the
+// primal kernel and 1280 (48 registers, no spills) for the dual kernel: the
+// fastest pair of a sweep over 1024 to 2048 threads.  Both kernels wait on
+// memory latency, so more resident rows outweigh the primal kernel's spills.
 // The loads of a row are issued before the LP's state is read (the addresses
 // are valid either way), so that read overlaps them instead of heading the
 // chain of dependent loads.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1152 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src,
+__global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src,
                                                            Uniform u) {
     const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
