@@ -207,7 +207,8 @@ def run_ours(args):
     P, desc, vbits = make_workload(args.config, rank)
     t0 = time.perf_counter()
     lp = B.uc_build_lp(P)
-    ps = B.uc_presolve(lp, value_bits=vbits)
+    pw_dev = 0 if args.power_host else 1
+    ps = B.uc_presolve(lp, value_bits=vbits, power_device=pw_dev)
     presolve_s = time.perf_counter() - t0
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
@@ -306,7 +307,7 @@ def run_ours(args):
         h2d = d2h = 0
         for _ in range(args.e2e_steps):
             lp2 = B.uc_build_lp(P)
-            ps2 = B.uc_presolve(lp2, value_bits=vbits)
+            ps2 = B.uc_presolve(lp2, value_bits=vbits, power_device=pw_dev)
             r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter, algorithm=args.algorithm,
                                  restart_metric=args.restart_metric)
             sol = B.uc_get_solution(r2, P.T, P.B, P.L, P.G)
@@ -319,7 +320,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d // args.e2e_steps),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps),
                "seconds_per_lp": e2e_s / args.e2e_steps,
-               "includes": "uc_build_lp + uc_presolve + uc_solve (upload, solve, download) + uc_get_solution"}
+               "includes": "uc_build_lp + uc_presolve (power iteration for ||A|| on the %s) + uc_solve "
+                           "(upload, solve, download) + uc_get_solution" % ("host" if args.power_host else "device")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -343,7 +345,7 @@ def run_ours(args):
             "objective": st["objective"], "restarts": st["restarts"],
             "pdhg_iters_per_s_per_gpu": total_iters / world / (ms_max / 1e3),
             "algorithmic_GBps": alg_gbs, "bytes_per_iter": bp + bd,
-            "presolve_s": presolve_s,
+            "presolve_s": presolve_s, "power_iteration": "host" if args.power_host else "device",
             "roofline": roofline,
             "clocks": clk_sum,
             "gpu_launches": st["kernel_launches"] - launches0,
@@ -594,6 +596,8 @@ def main():
     ap.add_argument("--no-sequential", action="store_true", help="batch64/served: skip the one-at-a-time baseline")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--power-host", action="store_true",
+                    help="presolve's power iteration for ||A|| on host threads instead of the device")
     ap.add_argument("--cpu-iters", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-kernel", type=int, default=0,

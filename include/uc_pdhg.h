@@ -81,6 +81,11 @@ typedef struct {
     double power_tol;            /* relative change that stops it (default 1e-10) */
     int value_bits;              /* 64: FP64 matrix values on device; 32: FP32 (default 64) */
     int threads;                 /* host threads for presolve (0 = hardware concurrency) */
+    int power_device;            /* 1: run the power iteration for ||A_s||_2 on the current CUDA
+                                    device (same steps and stopping rule, fixed-order device
+                                    reductions; A_s and A_s^T are copied to device memory for the
+                                    duration of the call); UC_ECUDA without a device.  0: host
+                                    threads (default) */
 } uc_presolve_opts;
 
 /* Device memory callback: return `bytes` bytes of device memory usable on
@@ -175,8 +180,9 @@ int uc_lp_export(const uc_lp *lp, int32_t *rowptr, int32_t *colidx, double *val,
 
 /* Presolve (Sec. II-D, reduced form: fixed columns, singleton rows to bounds,
  * empty rows / columns; surviving rows and columns keep their order), then
- * scaling and the step size.  Host only.  UC_EINFEASIBLE / UC_EUNBOUNDED
- * when presolve proves it. */
+ * scaling and the step size.  Host only, except the power iteration with
+ * opts.power_device = 1.  UC_EINFEASIBLE / UC_EUNBOUNDED when presolve
+ * proves it. */
 int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **out);
 /* Presolve `lp` reusing the scaling, scaled matrices and step size of `base`:
  * for an LP with the same grid and units as `base` (only loads differ), whose

@@ -36,7 +36,8 @@ class uc_problem(C.Structure):
 
 class uc_presolve_opts(C.Structure):
     _fields_ = [("ruiz_iters", C.c_int), ("pock_chambolle", C.c_int), ("power_max_iter", C.c_int),
-                ("power_tol", C.c_double), ("value_bits", C.c_int), ("threads", C.c_int)]
+                ("power_tol", C.c_double), ("value_bits", C.c_int), ("threads", C.c_int),
+                ("power_device", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -208,7 +209,10 @@ def uc_lp_export(lp) -> dict:
 def default_presolve_opts(**kw) -> uc_presolve_opts:
     o = uc_presolve_opts()
     lib.uc_default_presolve_opts(C.byref(o))
+    fields = {f[0] for f in uc_presolve_opts._fields_}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError(f"unknown presolve option {k!r}")
         setattr(o, k, v)
     return o
 

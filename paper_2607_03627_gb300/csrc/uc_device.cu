@@ -2523,6 +2523,163 @@ static int kkt_scratch_address(double **out) {
 }
 
 
+// ---------------------------------------------------------------------------
+// ||A||_2 for presolve on the device: power iteration on A^T A
+// ---------------------------------------------------------------------------
+// State: st[0] = lambda, st[1] = previous lambda; *done: 0 running, 1 converged,
+// 2 lambda == 0.  Every kernel returns at once when *done is set, so a fixed
+// number of launches can be queued and the host only polls.
+constexpr int kPwThreads = 128;
+
+// y = M x, one thread per row; with part, CTA b also writes sum of y_i^2 over
+// its rows (warp shuffles, then warps in order: a fixed order).
+__global__ void __launch_bounds__(kPwThreads) k_pw_spmv(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                        const double *__restrict__ val, int rows,
+                                                        const double *__restrict__ x, double *__restrict__ y,
+                                                        double *__restrict__ part, const int *__restrict__ done) {
+    if (*done) return;
+    const int i = blockIdx.x * kPwThreads + threadIdx.x;
+    double s = 0.0;
+    if (i < rows) {
+        for (int k = rp[i]; k < rp[i + 1]; k++) s += val[k] * x[ci[k]];
+        y[i] = s;
+    }
+    if (!part) return;
+    double sq = s * s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    __shared__ double sh[kPwThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = sh[0];
+        for (int w = 1; w < kPwThreads / 32; w++) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// lambda = sqrt(sum of the CTA partials), one CTA of 1024 threads (strided
+// partial sums, then a tree: a fixed order); the stopping test of the step.
+__global__ void __launch_bounds__(1024) k_pw_norm(const double *__restrict__ part, int np, double *st, int *done,
+                                                  double tol) {
+    if (*done) return;
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int p = threadIdx.x; p < np; p += 1024) s += part[p];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double lam = sqrt(sh[0]);
+        st[0] = lam;
+        if (lam == 0.0) *done = 2;
+        else if (fabs(lam - st[1]) <= tol * lam) *done = 1;
+        else st[1] = lam;
+    }
+}
+
+// v = w / lambda (skipped once the iteration has stopped: v is not used again)
+__global__ void k_pw_div(const double *__restrict__ w, double *__restrict__ v, int n, const double *st,
+                         const int *done) {
+    if (*done) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) v[j] = w[j] / st[0];
+}
+
+}  // namespace dev
+
+int device_power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, double *out) {
+    using namespace dev;
+    *out = 0.0;
+    const int n = A.cols, m = A.rows;
+    if (n == 0 || m == 0) return UC_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        set_error("power iteration on the device: no CUDA device");
+        return UC_ECUDA;
+    }
+    const int64_t nnz = A.nnz();
+    const int np = (n + kPwThreads - 1) / kPwThreads;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_arp = take(sizeof(int32_t) * (m + 1)), o_aci = take(sizeof(int32_t) * nnz),
+                 o_av = take(sizeof(double) * nnz), o_trp = take(sizeof(int32_t) * (n + 1)),
+                 o_tci = take(sizeof(int32_t) * nnz), o_tv = take(sizeof(double) * nnz),
+                 o_v = take(sizeof(double) * n), o_t = take(sizeof(double) * m), o_w = take(sizeof(double) * n),
+                 o_part = take(sizeof(double) * np), o_st = take(sizeof(double) * 2), o_done = take(sizeof(int));
+    cudaStream_t s = nullptr;
+    UC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    char *D = nullptr;
+    int *h_done = nullptr;
+    int rc = UC_OK;
+    auto fail = [&](cudaError_t e, const char *what) {
+        set_error("power iteration on the device: %s failed: %s", what, cudaGetErrorString(e));
+        rc = (e == cudaErrorMemoryAllocation) ? UC_ENOMEM : UC_ECUDA;
+    };
+    cudaError_t e = cudaMallocAsync((void **)&D, off, s);
+    if (e != cudaSuccess) fail(e, "cudaMallocAsync");
+    if (rc == UC_OK && (e = cudaMallocHost((void **)&h_done, sizeof(int))) != cudaSuccess) fail(e, "cudaMallocHost");
+    if (rc == UC_OK) {
+        std::vector<double> v0((size_t)n, 1.0 / std::sqrt((double)n));
+        const double st0[2] = {0.0, 0.0};
+        const int zero = 0;
+        struct Up { size_t o; const void *src; size_t bytes; } ups[] = {
+            {o_arp, A.rowptr.data(), sizeof(int32_t) * (m + 1)}, {o_aci, A.colidx.data(), sizeof(int32_t) * nnz},
+            {o_av, A.val.data(), sizeof(double) * nnz}, {o_trp, AT.rowptr.data(), sizeof(int32_t) * (n + 1)},
+            {o_tci, AT.colidx.data(), sizeof(int32_t) * nnz}, {o_tv, AT.val.data(), sizeof(double) * nnz},
+            {o_v, v0.data(), sizeof(double) * n}, {o_st, st0, sizeof(st0)}, {o_done, &zero, sizeof(int)}};
+        for (const Up &u : ups)
+            if (rc == UC_OK && (e = cudaMemcpyAsync(D + u.o, u.src, u.bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                fail(e, "cudaMemcpyAsync");
+        // the sources are stack / local vectors: finish the copies before they go
+        if (rc == UC_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) fail(e, "upload");
+    }
+    if (rc == UC_OK) {
+        const int32_t *arp = (const int32_t *)(D + o_arp), *aci = (const int32_t *)(D + o_aci);
+        const int32_t *trp = (const int32_t *)(D + o_trp), *tci = (const int32_t *)(D + o_tci);
+        const double *av = (const double *)(D + o_av), *tv = (const double *)(D + o_tv);
+        double *v = (double *)(D + o_v), *t = (double *)(D + o_t), *w = (double *)(D + o_w);
+        double *part = (double *)(D + o_part), *st = (double *)(D + o_st);
+        int *done = (int *)(D + o_done);
+        const int gm = (m + kPwThreads - 1) / kPwThreads, gn = np;
+        constexpr int kPoll = 64;   // steps queued between polls of the stop flag
+        for (int it = 0; it < max_iter && rc == UC_OK;) {
+            const int batch = std::min(kPoll, max_iter - it);
+            for (int b = 0; b < batch; b++) {
+                k_pw_spmv<<<gm, kPwThreads, 0, s>>>(arp, aci, av, m, v, t, nullptr, done);
+                k_pw_spmv<<<gn, kPwThreads, 0, s>>>(trp, tci, tv, n, t, w, part, done);
+                k_pw_norm<<<1, 1024, 0, s>>>(part, np, st, done, tol);
+                k_pw_div<<<gn, kPwThreads, 0, s>>>(w, v, n, st, done);
+            }
+            it += batch;
+            if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "kernel launch"); break; }
+            if ((e = cudaMemcpyAsync(h_done, done, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+                fail(e, "power iteration");
+                break;
+            }
+            if (*h_done) break;
+        }
+        // every pass of the loop ends with a synchronisation, so *h_done is current
+        double lam = 0.0;
+        if (rc == UC_OK && ((e = cudaMemcpyAsync(&lam, st, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                            (e = cudaStreamSynchronize(s)) != cudaSuccess))
+            fail(e, "result download");
+        if (rc == UC_OK) *out = (*h_done == 2) ? 0.0 : std::sqrt(lam);
+    }
+    if (D) cudaFreeAsync(D, s);
+    cudaStreamSynchronize(s);
+    if (h_done) cudaFreeHost(h_done);
+    cudaStreamDestroy(s);
+    return rc;
+}
+
+namespace dev {
+
 }  // namespace dev
 }  // namespace uc
 

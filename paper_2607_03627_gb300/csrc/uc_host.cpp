@@ -452,30 +452,47 @@ static void scale_lp(PsData &ps, const uc_presolve_opts &o, int threads) {
     ps.Dr.assign(m, 1.0);
     ps.Dc.assign(n, 1.0);
     std::vector<double> rf(m), cf(n);
-    for (int it = 0; it < o.ruiz_iters; it++) {           // Ruiz: sqrt of row / column max
-        std::fill(rf.begin(), rf.end(), 0.0);
-        std::fill(cf.begin(), cf.end(), 0.0);
+    // column view of A: the positions in A.val of column j's entries, rows
+    // ascending (the order in which a row-by-row sweep meets them), so the
+    // column sums below add in the same order as such a sweep
+    std::vector<int32_t> cp((size_t)n + 1, 0), pos(A.colidx.size());
+    for (int32_t j : A.colidx) cp[(size_t)j + 1]++;
+    for (int j = 0; j < n; j++) cp[j + 1] += cp[j];
+    {
+        std::vector<int32_t> next(cp.begin(), cp.end() - 1);
         for (int i = 0; i < m; i++)
-            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
-                double a = std::fabs(A.val[k]);
-                rf[i] = std::max(rf[i], a);
-                cf[A.colidx[k]] = std::max(cf[A.colidx[k]], a);
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) pos[next[A.colidx[k]]++] = k;
+    }
+    // factor = sqrt(max |a|) (Ruiz) or sqrt(sum |a|) (Pock-Chambolle, alpha = 1)
+    // of every row and column; 1 for an empty one
+    auto factors = [&](bool sum) {
+        parallel_for(m, threads, [&](int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; i++) {
+                double r = 0.0;
+                for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                    const double a = std::fabs(A.val[k]);
+                    r = sum ? r + a : std::max(r, a);
+                }
+                rf[i] = r > 0 ? std::sqrt(r) : 1.0;
             }
-        for (auto &v : rf) v = v > 0 ? std::sqrt(v) : 1.0;
-        for (auto &v : cf) v = v > 0 ? std::sqrt(v) : 1.0;
+        });
+        parallel_for(n, threads, [&](int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; j++) {
+                double r = 0.0;
+                for (int32_t p = cp[j]; p < cp[j + 1]; p++) {
+                    const double a = std::fabs(A.val[pos[p]]);
+                    r = sum ? r + a : std::max(r, a);
+                }
+                cf[j] = r > 0 ? std::sqrt(r) : 1.0;
+            }
+        });
+    };
+    for (int it = 0; it < o.ruiz_iters; it++) {           // Ruiz: sqrt of row / column max
+        factors(false);
         apply_scaling(A, rf, cf, ps.Dr, ps.Dc, threads);
     }
     if (o.pock_chambolle) {                                // Pock-Chambolle, alpha = 1
-        std::fill(rf.begin(), rf.end(), 0.0);
-        std::fill(cf.begin(), cf.end(), 0.0);
-        for (int i = 0; i < m; i++)
-            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
-                double a = std::fabs(A.val[k]);
-                rf[i] += a;
-                cf[A.colidx[k]] += a;
-            }
-        for (auto &v : rf) v = v > 0 ? std::sqrt(v) : 1.0;
-        for (auto &v : cf) v = v > 0 ? std::sqrt(v) : 1.0;
+        factors(true);
         apply_scaling(A, rf, cf, ps.Dr, ps.Dc, threads);
     }
     for (int i = 0; i < m; i++) ps.q[i] *= ps.Dr[i];
@@ -581,6 +598,7 @@ void uc_default_presolve_opts(uc_presolve_opts *o) {
     o->power_tol = 1e-10;
     o->value_bits = 64;
     o->threads = 0;
+    o->power_device = 0;
 }
 
 void uc_default_solve_opts(uc_solve_opts *o) {
@@ -641,6 +659,7 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
     if (opts) o = *opts;
     if (o.value_bits != 64 && o.value_bits != 32) { set_error("uc_presolve: value_bits must be 32 or 64"); return UC_EINVAL; }
     if (o.ruiz_iters < 0 || o.power_max_iter < 1) { set_error("uc_presolve: bad iteration counts"); return UC_EINVAL; }
+    if (o.power_device != 0 && o.power_device != 1) { set_error("uc_presolve: power_device must be 0 or 1"); return UC_EINVAL; }
     int threads = o.threads > 0 ? o.threads : (int)std::max(1u, std::thread::hardware_concurrency());
     try {
         auto ps = std::make_shared<PsData>();
@@ -655,7 +674,12 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
         ps->c_inf = ci;
         scale_lp(*ps, o, threads);
         ps->AT = transpose(ps->A);
-        ps->norm_A = power_norm(ps->A, ps->AT, o.power_max_iter, o.power_tol, threads);
+        if (o.power_device) {
+            rc = device_power_norm(ps->A, ps->AT, o.power_max_iter, o.power_tol, &ps->norm_A);
+            if (rc) return rc;
+        } else {
+            ps->norm_A = power_norm(ps->A, ps->AT, o.power_max_iter, o.power_tol, threads);
+        }
         ps->eta = ps->norm_A > 0 ? 0.998 / ps->norm_A : 1.0;
         double cn = std::sqrt(sumsq(ps->c, threads)), qn = std::sqrt(sumsq(ps->q, threads));
         ps->omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;

@@ -67,6 +67,13 @@ struct PsData {
     int m() const { return A.rows; }
 };
 
+// ||A||_2 by power iteration on A^T A on the current CUDA device: the steps of
+// the host power iteration (start 1/sqrt(n), lambda = ||A^T A v||, stop at
+// relative change <= tol or after max_iter products), with fixed-order device
+// reductions.  *out = sqrt(lambda).  UC_ECUDA when no device or a CUDA call
+// fails, UC_ENOMEM when device memory is short.
+int device_power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, double *out);
+
 // Host-side postsolve: scaled presolved (x_s, y_s) -> raw (x, y).
 void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
                std::vector<double> &y);

@@ -124,3 +124,19 @@ def test_presolve_does_not_depend_on_the_thread_count(B):
             np.testing.assert_array_equal(d[k], ref[k], err_msg=f"{k} threads={th}")
         for k in ("eta", "omega0", "norm_A"):
             assert d[k] == ref[k], (k, th)
+
+
+def test_power_device_option_is_checked(B):
+    lp = B.uc_build_lp(ucgen.tiny(0))
+    with pytest.raises(B.UCError, match="power_device"):
+        B.uc_presolve(lp, power_device=2)
+    with pytest.raises(TypeError, match="unknown presolve option"):
+        B.uc_presolve(lp, power_devcie=1)
+
+
+def test_power_device_without_a_device_fails_loudly(B):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(B.UCError, match="no CUDA device"):
+        B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)), power_device=1)
