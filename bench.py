@@ -51,12 +51,15 @@ NCU_TRAFFIC_RPT2 = {
 
 
 def _src_hash():
-    """sha256 (16 hex digits) of the row kernels and their helpers in uc_device.cu."""
+    """sha256 (16 hex digits) of the row kernels and their helpers in uc_device.cu,
+    and of the code that lays the LP out in device order."""
     with open(os.path.join(ROOT, "paper_2607_03627_gb300", "csrc", "uc_device.cu")) as f:
         src = f.read()
     a = src.index("// FP64 is scarce on this GPU")
     b = src.index("// staged iteration kernels (Halpern)")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    c = src.index("// Device view of an LP.")
+    d = src.index("// same scaled matrix (structure, values as stored, equality rows)")
+    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()[:16]
 
 
 def _peaks():

@@ -1298,23 +1298,49 @@ static void put(std::vector<char> &st, size_t off, const T *src, size_t count) {
     if (count) std::memcpy(st.data() + off, src, count * sizeof(T));
 }
 
-// Device view of an LP.  Warps work on 32 consecutive rows and issue as many
-// FMA iterations as their longest row, so rows are reordered, within windows
-// of kOrderWindow rows, by decreasing length (stable; equality rows stay
-// first).  Columns are reordered the same way by their A^T row length.  Each
-// row keeps its entries in their original order, so every dot product sums in
-// the same order as in the natural layout.
+// Device view of an LP.  Rows and columns are put in entity-major order: by
+// (kind, unit / bus / line, period) of the raw LP they come from, equality
+// rows first.  Consecutive rows are then one constraint of one unit, bus or
+// line in consecutive periods, whose entries point at one variable of one
+// entity in consecutive periods, which the device stores consecutively too:
+// a warp's gathers read a few contiguous sectors instead of one sector per
+// thread.  Warps issue as many FMA iterations as their longest row, so within
+// windows of kOrderWindow rows of that order the rows are then sorted by
+// decreasing length (stable).  Columns get the same treatment with their A^T
+// row length.  Each row keeps its entries in their original order, so every
+// dot product sums in the same order as in the natural layout.
 constexpr int kOrderWindow = 1024;
 
-static void window_order(const std::vector<int32_t> &rp, int begin, int end, std::vector<int32_t> &out) {
-    for (int w0 = begin; w0 < end; w0 += kOrderWindow) {
-        const int w1 = std::min(end, w0 + kOrderWindow);
-        const size_t base = out.size();
-        for (int r = w0; r < w1; r++) out.push_back(r);
-        std::stable_sort(out.begin() + base, out.end(), [&](int32_t a, int32_t b) {
+static void window_order(const std::vector<int32_t> &rp, const std::vector<int32_t> &base, std::vector<int32_t> &out) {
+    for (size_t w0 = 0; w0 < base.size(); w0 += kOrderWindow) {
+        const size_t w1 = std::min(base.size(), w0 + (size_t)kOrderWindow);
+        const size_t o = out.size();
+        out.insert(out.end(), base.begin() + w0, base.begin() + w1);
+        std::stable_sort(out.begin() + o, out.end(), [&](int32_t a, int32_t b) {
             return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
         });
     }
+}
+
+// [begin, end) sorted by the (kind, entity, period) of the raw row or column
+// each maps to; natural order when the raw labels are missing
+static std::vector<int32_t> entity_order(int begin, int end, const std::vector<int32_t> &map,
+                                         const std::vector<int8_t> &kind, const std::vector<int32_t> &ent,
+                                         const std::vector<int32_t> &per) {
+    std::vector<int32_t> o;
+    o.reserve(end - begin);
+    for (int r = begin; r < end; r++) o.push_back(r);
+    const size_t nraw = kind.size();
+    bool ok = ent.size() == nraw && per.size() == nraw && (int64_t)map.size() >= end;
+    for (int r = begin; ok && r < end; r++) ok = map[r] >= 0 && (size_t)map[r] < nraw;
+    if (!ok) return o;
+    std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) {
+        const int32_t ra = map[a], rb = map[b];
+        if (kind[ra] != kind[rb]) return kind[ra] < kind[rb];
+        if (ent[ra] != ent[rb]) return ent[ra] < ent[rb];
+        return per[ra] < per[rb];
+    });
+    return o;
 }
 
 static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsData> &src, bool reorder,
@@ -1329,9 +1355,11 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
         for (int j = 0; j < n; j++) pcol[j] = j;
         return src;
     }
-    window_order(p.A.rowptr, 0, p.m_eq, prow);
-    window_order(p.A.rowptr, p.m_eq, m, prow);
-    window_order(p.AT.rowptr, 0, n, pcol);
+    static const RawLp kNoLabels;
+    const RawLp &R = p.raw ? *p.raw : kNoLabels;
+    window_order(p.A.rowptr, entity_order(0, p.m_eq, p.row_map, R.row_kind, R.row_idx, R.row_t), prow);
+    window_order(p.A.rowptr, entity_order(p.m_eq, m, p.row_map, R.row_kind, R.row_idx, R.row_t), prow);
+    window_order(p.AT.rowptr, entity_order(0, n, p.col_map, R.col_kind, R.col_idx, R.col_t), pcol);
     std::vector<int32_t> irow(m), icol(n);
     for (int i = 0; i < m; i++) irow[prow[i]] = i;
     for (int j = 0; j < n; j++) icol[pcol[j]] = j;
