@@ -41,12 +41,12 @@ MAX_ITER = 100_000
 # were taken on (the hash of the row kernels' section of uc_device.cu) and the
 # launch shape (threads per CTA, rows per thread).
 NCU_TRAFFIC = {
-    ("paper", "halpern", "k_primal"): {"src": "ca26752728c2412e", "launch": (128, 1), "bytes": 65717632 + 1918592},
-    ("paper", "halpern", "k_dual"): {"src": "ca26752728c2412e", "launch": (128, 1), "bytes": 44744064 + 1339008},
+    ("paper", "halpern", "k_primal"): {"src": "7af00afb8c03e5fd", "launch": (128, 1), "bytes": 65662336 + 2434176},
+    ("paper", "halpern", "k_dual"): {"src": "7af00afb8c03e5fd", "launch": (128, 1), "bytes": 44714496 + 1490432},
 }
 NCU_TRAFFIC_RPT2 = {
-    ("paper", "halpern", "k_primal"): {"src": "ca26752728c2412e", "launch": (128, 2), "bytes": 65937920 + 1483648},
-    ("paper", "halpern", "k_dual"): {"src": "ca26752728c2412e", "launch": (128, 2), "bytes": 44863232 + 867968},
+    ("paper", "halpern", "k_primal"): {"src": "7af00afb8c03e5fd", "launch": (128, 2), "bytes": 65927808 + 1882624},
+    ("paper", "halpern", "k_dual"): {"src": "7af00afb8c03e5fd", "launch": (128, 2), "bytes": 44738816 + 1195520},
 }
 
 
@@ -549,7 +549,8 @@ def run_lanes(args):
 def run_served(args):
     """Served stream: requests on the 6,049-bus grid with loads scaled by
     {0.80..1.20} and AR(1) noise, Poisson arrivals at 2 req/s, continuous
-    batching with warm starts, against one-at-a-time cold FP64 solves."""
+    batching (2 slots in a shared-matrix session; warm starts with
+    --warm-start), against one-at-a-time cold FP64 solves."""
     import torch
     import ucgen
     torch.cuda.set_device(0)
@@ -565,7 +566,8 @@ def run_served(args):
         for r in range(n):
             reqs.append(Request(rid=45 * w + r, problem=ucgen.served_request(base, w, r), arrival=float(arr[r])))
         t = float(arr[-1])
-    srv = Server(base, slots=args.slots, hbm_budget_gb=150.0, tol=TOL, max_iter=args.max_iter)
+    srv = Server(base, slots=args.slots, hbm_budget_gb=150.0, tol=TOL, max_iter=args.max_iter,
+                 warm_start=args.warm_start)
     with ClockSampler(0) as clk:
         m = srv.serve(reqs, realtime=True)
     srv.close()
@@ -574,7 +576,8 @@ def run_served(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{len(reqs)} requests on the 6049-bus / 700-unit / 48-period grid, "
                                             "load x{0.80..1.20} + AR(1) 5%, Poisson 2 req/s",
-                                            "slots": m["slots"], "hbm_budget_gb": 150.0, "tol_rel_kkt": TOL},
+                                            "slots": m["slots"], "hbm_budget_gb": 150.0, "tol_rel_kkt": TOL,
+                                            "warm_start": args.warm_start},
             "served": m, "clocks": clk.summary(), "impl": "ours",
             "per_request": [{"rid": r.rid, "iters": r.iters, "status": r.status, "warm_from": r.warm_from,
                              "latency_s": r.latency, "omega": r.omega, "start_omega": r.start_omega}
@@ -595,7 +598,9 @@ def main():
     ap.add_argument("--lanes", type=int, default=4, help="paper-lanes: LPs in the shared-matrix session (2 or 4)")
     ap.add_argument("--batch", type=int, default=64, help="batch64: number of LPs")
     ap.add_argument("--requests", type=int, default=45, help="served: requests (45 per wave)")
-    ap.add_argument("--slots", type=int, default=4, help="served: session slots")
+    ap.add_argument("--slots", type=int, default=2, help="served: session slots")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="served: warm-start requests from the nearest solved one (duals + primal weight)")
     ap.add_argument("--no-sequential", action="store_true", help="batch64/served: skip the one-at-a-time baseline")
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict_
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
 template <typename VT, int ALGO, int BS>
-__global__ void __launch_bounds__(BS, 1280 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src,
+__global__ void __launch_bounds__(BS, 1536 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src,
                                                          Uniform u) {
     const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
