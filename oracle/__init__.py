@@ -10,7 +10,8 @@ Contents (each function cites the passage it follows; the paper defers its UC
 model to the GO Challenge 3 specification (Sec. II-A) and names PDHG without
 stating it (Sec. II-C, Sec. III-C), so the model follows the DC relaxation the
 benchmark configurations define and the PDHG follows the published PDLP method
-(Applegate et al., NeurIPS 2021) with constant steps):
+(Applegate et al., NeurIPS 2021) with constant steps, or with PDLP's adaptive
+step size as an option of the averaging variant):
 
 * ``lp``        -- O-builder: raw DC-UC LP from problem data (Sec. II-A/II-B,
                    Alg. 1 "same relaxed problem").

@@ -26,6 +26,23 @@ but does not state the method.  This follows the published PDLP scheme
           the new omega; sums and j reset; tau, sigma recomputed.
 All arithmetic is on the scaled problem except the stopping test.
 
+Adaptive step size (averaging variant, option ``adaptive=True``; PDLP,
+Applegate et al. 2021, Sec. 3.1).  Each iteration is an attempt with the trial
+step eta (initially the constant step S.eta):
+
+  attempt: (x', y') = the PDHG step above with tau = eta/omega, sigma = eta*omega
+           eta_bar = ||z' - z||^2_omega / (2 |(y' - y)^T A (x' - x)|)
+                     (+inf when the product is 0), with
+                     ||z||^2_omega = omega ||x||^2 + ||y||^2 / omega
+           accepted when eta <= eta_bar: z = z', and z' enters the running
+           sums with weight eta (the average is sum(eta z) / sum(eta));
+           otherwise z stays
+           next trial eta = min((1 - (k+1)^-0.3) eta_bar, (1 + (k+1)^-0.6) eta),
+           k = attempts so far including this one (so k + 1 >= 2)
+  Attempts count as iterations for the iteration limit, the evaluation period
+  and the restart test's j; an evaluation with no accepted step since the
+  last restart takes the current point as the average.
+
 A second variant, the default, is restarted reflected Halpern PDHG (Lu &
 Yang, "Restarted Halpern PDHG for linear programming", 2024), again with a
 constant step.  With T the PDHG map above and z = (x, y):
@@ -83,6 +100,10 @@ class State:
     j: int
     k: int
     restarts: int = 0
+    # adaptive step size
+    eta_try: float = 0.0
+    w_sum: float = 0.0
+    accepted: int = 0
 
 
 @dataclasses.dataclass
@@ -130,7 +151,7 @@ def initial_state(S, x0=None, y0=None) -> State:
     return State(x=x, y=y, x_sum=np.zeros_like(x), y_sum=np.zeros_like(y),
                  x_anchor=x.copy(), y_anchor=y.copy(), omega=omega,
                  tau=S.eta / omega, sigma=S.eta * omega, kkt_anchor=ka,
-                 kkt_prev=math.inf, j=0, k=0)
+                 kkt_prev=math.inf, j=0, k=0, eta_try=S.eta)
 
 
 def step(S, st: State, AT=None):
@@ -146,6 +167,40 @@ def step(S, st: State, AT=None):
     st.y_sum += y_new
     st.j += 1
     st.k += 1
+
+
+ADAPT_SHRINK = 0.3    # exponent of the shrink factor 1 - (k+1)^-0.3
+ADAPT_GROW = 0.6      # exponent of the growth factor 1 + (k+1)^-0.6
+
+
+def adaptive_attempt(S, st: State, AT=None):
+    """One attempt of the adaptive step (PDLP, Applegate et al. 2021, Sec. 3.1),
+    in place.  Returns (accepted, eta, eta_bar)."""
+    AT = S.A.T.tocsr() if AT is None else AT
+    eta = st.eta_try
+    tau, sigma = eta / st.omega, eta * st.omega
+    x_new = np.clip(st.x - tau * (S.c - AT @ st.y), S.l, S.u)
+    y_new = st.y + sigma * (S.q - S.A @ (2.0 * x_new - st.x))
+    y_new[S.m_eq:] = np.maximum(y_new[S.m_eq:], 0.0)
+    dx = x_new - st.x
+    dy = y_new - st.y
+    movement = st.omega * float(np.dot(dx, dx)) + float(np.dot(dy, dy)) / st.omega
+    interaction = abs(float(np.dot(dy, S.A @ dx)))
+    eta_bar = movement / (2.0 * interaction) if interaction > 0.0 else math.inf
+    k = st.k + 1
+    eta_next = min((1.0 - (k + 1) ** -ADAPT_SHRINK) * eta_bar, (1.0 + (k + 1) ** -ADAPT_GROW) * eta)
+    accepted = eta <= eta_bar
+    if accepted:
+        st.x = x_new
+        st.y = y_new
+        st.x_sum += eta * x_new
+        st.y_sum += eta * y_new
+        st.w_sum += eta
+        st.accepted += 1
+    st.eta_try = eta_next
+    st.j += 1
+    st.k += 1
+    return accepted, eta, eta_bar
 
 
 def restart_decision(kkt_cand, kkt_anchor, kkt_prev, j, k_plus_1) -> bool:
@@ -165,11 +220,18 @@ def primal_weight_update(omega, dx, dy) -> float:
     return omega
 
 
-def evaluate(S, st: State, U, tol: float):
+def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
     """Evaluation after an n_eval block; returns (done, which, point) and
     applies a restart to ``st`` when the test fires."""
-    x_avg = st.x_sum / st.j
-    y_avg = st.y_sum / st.j
+    if not adaptive:
+        x_avg = st.x_sum / st.j
+        y_avg = st.y_sum / st.j
+    elif st.w_sum > 0.0:
+        x_avg = st.x_sum / st.w_sum
+        y_avg = st.y_sum / st.w_sum
+    else:   # no step accepted since the last restart
+        x_avg = st.x
+        y_avg = st.y
     for which, (xx, yy) in (("current", (st.x, st.y)), ("average", (x_avg, y_avg))):
         rel = kkt.relative_kkt(U, S.Dc * xx, S.Dr * yy)
         if max(rel) <= tol:
@@ -192,6 +254,7 @@ def evaluate(S, st: State, U, tol: float):
         st.kkt_prev = math.inf
         st.x_sum[:] = 0.0
         st.y_sum[:] = 0.0
+        st.w_sum = 0.0
         st.j = 0
         st.tau = S.eta / st.omega
         st.sigma = S.eta * st.omega
@@ -202,17 +265,24 @@ def evaluate(S, st: State, U, tol: float):
 
 
 def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
-          x0=None, y0=None, trace=None, trace_iters=()) -> Result:
+          x0=None, y0=None, trace=None, trace_iters=(), adaptive: bool = False, attempts=None) -> Result:
     """Run O1 on a ``presolve.Scaled`` problem.  ``trace(k, state)`` is called
-    after every step k in ``trace_iters`` (k counts steps taken)."""
+    after every step k in ``trace_iters`` (k counts steps taken; with
+    ``adaptive``, attempts).  ``attempts``, a list, receives (accepted, eta,
+    eta_bar) of every adaptive attempt."""
     st = initial_state(S, x0, y0)
     AT = S.A.T.tocsr()
     U = _unscaled_lp(S)
     trace_iters = set(trace_iters)
     while st.k < max_iter:
-        step(S, st, AT)
+        if adaptive:
+            a = adaptive_attempt(S, st, AT)
+            if attempts is not None:
+                attempts.append(a)
+        else:
+            step(S, st, AT)
         if st.k % n_eval == 0:
-            done, which, pt, rel = evaluate(S, st, U, tol)
+            done, which, pt, rel = evaluate(S, st, U, tol, adaptive)
             if done:
                 return Result(x=pt[0], y=pt[1], iters=st.k, status="optimal", rel=rel,
                               restarts=st.restarts, omega=st.omega, state=st, which=which)

@@ -186,3 +186,93 @@ def test_halpern_second_step_weight():
     pdhg.halpern_step(S, st)
     # z2 = 2/3 (2 T(z1) - z1) + 1/3 z0 with T(z1) = z1 = (0, 1, 0), z0 = 0
     np.testing.assert_allclose(st.x, [0.0, 2.0 / 3.0, 0.0], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# adaptive step size (PDLP, averaging variant)
+# ---------------------------------------------------------------------------
+def _small(seed):
+    return ucgen.make_problem(seed, B=12, L=16, G=4, T=6, lo=0.4, hi=0.8, noise=0.05, zero_pmin_frac=0.25)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_adaptive_reaches_simplex_objective(seed):
+    raw, ps, S = _pipeline(_small(seed))
+    att = []
+    r = pdhg.solve(S, tol=1e-4, max_iter=100_000, adaptive=True, attempts=att)
+    assert r.status == "optimal"
+    assert any(not a[0] for a in att), "the rule never rejected a step"
+    x, y = S.Dc * r.x, S.Dr * r.y
+    assert max(kkt.relative_kkt(ps.lp, x, y)) <= 1e-4
+    ref = simplex.solve_lp(raw)
+    xr, _ = ops.postsolve(ps, x)
+    assert abs(float(raw.c @ xr) - ref.obj) / max(1.0, abs(ref.obj)) <= 1e-4
+
+
+def test_adaptive_tiny_objective_matches_golden():
+    with open(os.path.join(GOLDEN, "tiny_lp.json")) as f:
+        g = json.load(f)
+    raw, ps, S = _pipeline(ucgen.tiny(g["seed"]))
+    r = pdhg.solve(S, tol=1e-4, max_iter=100_000, adaptive=True)
+    assert r.status == "optimal"
+    xr, _ = ops.postsolve(ps, S.Dc * r.x)
+    assert abs(float(raw.c @ xr) - g["objective"]) / abs(g["objective"]) <= 1e-4
+
+
+def test_adaptive_steps_never_collapse():
+    # |dy^T A dx| <= ||A||_2 ||dx|| ||dy|| <= ||A||_2 (omega ||dx||^2 + ||dy||^2 / omega) / 2,
+    # so eta_bar >= 1 / ||A||_2 at every attempt, and the trial step stays at or
+    # above min(eta_0, (1 - 2^-0.3) / ||A||_2)
+    raw, ps, S = _pipeline(_small(1))
+    norm = float(np.linalg.norm(S.A.toarray(), 2))
+    att = []
+    pdhg.solve(S, tol=0.0, max_iter=3000, adaptive=True, attempts=att)
+    floor = min(S.eta, (1.0 - 2.0 ** -0.3) / norm)
+    for acc, eta, eta_bar in att:
+        assert eta_bar >= (1.0 - 1e-12) / norm
+        assert eta >= floor * (1.0 - 1e-12)
+
+
+def test_adaptive_acceptance_is_the_pdhg_metric_test():
+    # The rule bounds |dy^T A dx|, so a step is accepted exactly when dz^T M dz >= 0
+    # for dz = (dx, dy) and for (dx, -dy), M = [[omega/eta I, -A^T], [-A, 1/(eta omega) I]]
+    # being the PDHG preconditioner of the trial step: the quadratic forms are
+    # built here from the block matrix, not from eta_bar.
+    raw, ps, S = _pipeline(_small(2))
+    st = pdhg.initial_state(S)
+    AT = S.A.T.tocsr()
+    m, n = S.A.shape
+    seen = {True: 0, False: 0}
+    for _ in range(1500):
+        x0, y0, eta, om = st.x.copy(), st.y.copy(), st.eta_try, st.omega
+        # the trial point, recomputed independently of the attempt
+        xt = np.clip(x0 - (eta / om) * (S.c - AT @ y0), S.l, S.u)
+        yt = y0 + (eta * om) * (S.q - S.A @ (2 * xt - x0))
+        yt[S.m_eq:] = np.maximum(yt[S.m_eq:], 0.0)
+        dz = np.concatenate([xt - x0, yt - y0])
+        dzr = np.concatenate([xt - x0, y0 - yt])
+        M = sp.bmat([[sp.identity(n) * (om / eta), -AT], [-S.A, sp.identity(m) / (eta * om)]]).tocsr()
+        q = min(float(dz @ (M @ dz)), float(dzr @ (M @ dzr)))
+        scale = float(dz @ dz) / eta * max(om, 1.0 / om)
+        acc, _, _ = pdhg.adaptive_attempt(S, st, AT)
+        if abs(q) > 1e-9 * scale:
+            assert acc == (q >= 0.0), (q, acc)
+            seen[acc] += 1
+        if acc:
+            np.testing.assert_array_equal(st.x, xt)
+    assert seen[True] > 0 and seen[False] > 0
+
+
+def test_adaptive_average_is_step_weighted():
+    raw, ps, S = _pipeline(_small(0))
+    st = pdhg.initial_state(S)
+    AT = S.A.T.tocsr()
+    xs, ws = np.zeros_like(st.x), 0.0
+    for _ in range(1500):
+        acc, eta, _ = pdhg.adaptive_attempt(S, st, AT)
+        if acc:
+            xs = xs + eta * st.x
+            ws += eta
+    assert st.w_sum == pytest.approx(ws, rel=1e-13)
+    np.testing.assert_allclose(st.x_sum / st.w_sum, xs / ws, rtol=1e-12, atol=1e-15)
+    assert st.accepted < 1500 and st.k == 1500
