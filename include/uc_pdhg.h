@@ -139,6 +139,14 @@ typedef struct {
                                     and the LPs' vectors are interleaved, so every row is read once
                                     for all of them (Halpern, row kernels; UC_EINVAL otherwise).
                                     Iterates are those of separate solves, bit for bit. */
+    int adaptive_step;           /* 1: PDLP's adaptive step size (Applegate et al. 2021, Sec. 3.1) for
+                                    algorithm 1: each iteration is an attempt with a trial step eta,
+                                    accepted when eta <= ||dz||^2_omega / (2 |dy^T A dx|); next trial
+                                    min((1 - (k+1)^-0.3) that bound, (1 + (k+1)^-0.6) eta), k = attempts
+                                    so far; averages weighted by the accepted steps; attempts count as
+                                    iterations (limit, evaluation period, restarts).  One LP per
+                                    session, no lanes, row kernels; UC_EINVAL otherwise.  0: constant
+                                    step (default) */
 } uc_solve_opts;
 
 typedef struct {
@@ -161,6 +169,7 @@ typedef struct {
     int kernel_launches;         /* kernels launched by the session so far */
     int64_t h2d_bytes;           /* host -> device bytes of the session upload */
     int64_t d2h_bytes;           /* device -> host bytes of this result (+ status polls) */
+    int rejected_steps;          /* adaptive step size: attempts that were rejected (else 0) */
 } uc_stats;
 
 void uc_default_presolve_opts(uc_presolve_opts *o);

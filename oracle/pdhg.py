@@ -173,10 +173,14 @@ ADAPT_SHRINK = 0.3    # exponent of the shrink factor 1 - (k+1)^-0.3
 ADAPT_GROW = 0.6      # exponent of the growth factor 1 + (k+1)^-0.6
 
 
-def adaptive_attempt(S, st: State, AT=None):
+def adaptive_attempt(S, st: State, AT=None, exact_sums: bool = False):
     """One attempt of the adaptive step (PDLP, Applegate et al. 2021, Sec. 3.1),
-    in place.  Returns (accepted, eta, eta_bar)."""
+    in place.  Returns (accepted, eta, eta_bar).  ``exact_sums`` takes the three
+    sums of eta_bar correctly rounded (math.fsum) instead of numpy's order: the
+    step feeds back into the next one, so comparing the two measures how far
+    rounding alone moves the trajectory."""
     AT = S.A.T.tocsr() if AT is None else AT
+    dot = (lambda a, b: math.fsum(a * b)) if exact_sums else (lambda a, b: float(np.dot(a, b)))
     eta = st.eta_try
     tau, sigma = eta / st.omega, eta * st.omega
     x_new = np.clip(st.x - tau * (S.c - AT @ st.y), S.l, S.u)
@@ -184,8 +188,8 @@ def adaptive_attempt(S, st: State, AT=None):
     y_new[S.m_eq:] = np.maximum(y_new[S.m_eq:], 0.0)
     dx = x_new - st.x
     dy = y_new - st.y
-    movement = st.omega * float(np.dot(dx, dx)) + float(np.dot(dy, dy)) / st.omega
-    interaction = abs(float(np.dot(dy, S.A @ dx)))
+    movement = st.omega * dot(dx, dx) + dot(dy, dy) / st.omega
+    interaction = abs(dot(dy, S.A @ dx))
     eta_bar = movement / (2.0 * interaction) if interaction > 0.0 else math.inf
     k = st.k + 1
     eta_next = min((1.0 - (k + 1) ** -ADAPT_SHRINK) * eta_bar, (1.0 + (k + 1) ** -ADAPT_GROW) * eta)
@@ -265,7 +269,8 @@ def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
 
 
 def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
-          x0=None, y0=None, trace=None, trace_iters=(), adaptive: bool = False, attempts=None) -> Result:
+          x0=None, y0=None, trace=None, trace_iters=(), adaptive: bool = False, attempts=None,
+          exact_sums: bool = False) -> Result:
     """Run O1 on a ``presolve.Scaled`` problem.  ``trace(k, state)`` is called
     after every step k in ``trace_iters`` (k counts steps taken; with
     ``adaptive``, attempts).  ``attempts``, a list, receives (accepted, eta,
@@ -276,7 +281,7 @@ def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
     trace_iters = set(trace_iters)
     while st.k < max_iter:
         if adaptive:
-            a = adaptive_attempt(S, st, AT)
+            a = adaptive_attempt(S, st, AT, exact_sums)
             if attempts is not None:
                 attempts.append(a)
         else:

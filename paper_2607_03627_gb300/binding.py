@@ -52,7 +52,8 @@ class uc_solve_opts(C.Structure):
                 ("spmv_kernel", C.c_int), ("cta_rows", C.c_int), ("rows_per_thread", _P(C.c_int)),
                 ("no_reorder", C.c_int), ("no_pdl", C.c_int), ("algorithm", C.c_int),
                 ("restart_metric", C.c_int),
-                ("cancel", _P(C.c_int)), ("stages", C.c_int), ("lanes", C.c_int)]
+                ("cancel", _P(C.c_int)), ("stages", C.c_int), ("lanes", C.c_int),
+                ("adaptive_step", C.c_int)]
 
 
 class uc_device_lp(C.Structure):
@@ -70,7 +71,8 @@ class uc_stats(C.Structure):
                 ("dual_objective", C.c_double), ("omega", C.c_double), ("solve_ms", C.c_double),
                 ("upload_ms", C.c_double), ("primal_kernel_ms", C.c_double),
                 ("dual_kernel_ms", C.c_double), ("timed_launches", C.c_int),
-                ("kernel_launches", C.c_int), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("kernel_launches", C.c_int), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+                ("rejected_steps", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -297,7 +299,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
                restart_metric: str = "kkt", cta_rows: int = 0,
                rows_per_thread=None, pdl: bool = True, reorder: bool = True,
-               stages: int = 0, lanes: bool = False) -> tuple[uc_solve_opts, list]:
+               stages: int = 0, lanes: bool = False, adaptive_step: bool = False) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -314,6 +316,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.no_reorder = 0 if reorder else 1
     o.stages = int(stages)
     o.lanes = int(bool(lanes))
+    o.adaptive_step = int(bool(adaptive_step))
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)

@@ -29,6 +29,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <mutex>
 #include <queue>
@@ -70,6 +71,11 @@ struct Scalars {
     int restarts, evals;
     int algo;        // ALG_HALPERN or ALG_AVERAGE
     int metric;      // Halpern restart metric: METRIC_KKT or METRIC_FPR
+    // adaptive step size (averaging variant): trial step, weight of the last
+    // attempt (its step if accepted, else 0), step-weighted sum since the
+    // restart, buffer of the current iterate, accepted attempts
+    int adaptive, ad_src, ad_acc;
+    double ad_eta, ad_w, wsum;
 };
 // kkt_anchor / kkt_prev hold the restart metric's anchor and previous value
 // for the Halpern variant as well.
@@ -94,6 +100,8 @@ struct Bufs {
     const long long *lkey, *ukey;              // order keys of l and u (see okey)
     const double *W, *W1;                      // Halpern weights (j+1)/(j+2) and 1 - that, j < nW
     int nW;
+    const double *adS, *adG;                   // adaptive step: 1 - (a+2)^-0.3 and 1 + (a+2)^-0.6, attempt a
+    double *adp;                               // adaptive step: per-CTA partial sums of an attempt
     // state: x, y double-buffered
     double *x[2], *y[2];
     double *xsum, *ysum, *xa, *ya, *xret, *yret;   // Halpern: xsum holds x-bar, xret/yret the map output
@@ -877,9 +885,18 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
         // (unscaled) as maxima in RPU and RDU, all of the second record
         const bool ray = halp && (S->evals + 1) % kInfeasEvery == 0;
         const bool avg = S->algo == ALG_AVERAGE && mode == 1;
-        const double inv_j = avg ? 1.0 / (double)(S->j_base + S->n_eval) : 0.0;
         const double *x = halp ? b.xret : b.x[0];
         const double *y = halp ? b.yret : b.y[0];
+        // average = sums / steps; with adaptive steps, sums / (sum of accepted
+        // steps), or the current point when no step was accepted since the restart
+        double inv_j = 0.0;
+        const double *xav = b.xsum, *yav = b.ysum;
+        if (avg && S->adaptive) {
+            if (S->wsum > 0.0) inv_j = 1.0 / S->wsum;
+            else { inv_j = 1.0; xav = x; yav = y; }
+        } else if (avg) {
+            inv_j = 1.0 / (double)(S->j_base + S->n_eval);
+        }
         const bool rows = (sg.aux & 1) == 0;
         const int eq_end = sg.aux >> 1;   // rows: first ">=" row
         if (rows) {
@@ -890,7 +907,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     const size_t j = at(b.A_ci[k]);
                     const double a = widen(v[k]);
                     ax0 += a * x[j];
-                    if (avg) ax1 += a * (b.xsum[j] * inv_j);
+                    if (avg) ax1 += a * (xav[j] * inv_j);
                 }
                 const size_t ii = at(i);
                 const double qi = b.q[ii], idr = b.inv_Dr[ii], yh = b.ya[ii];
@@ -905,7 +922,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 if (avg) {
                     double r1 = ax1 - qi;
                     if (ineq) r1 = fmin(r1, 0.0);
-                    const double y1 = b.ysum[ii] * inv_j;
+                    const double y1 = yav[ii] * inv_j;
                     acc[kSlots + RP2] += r1 * r1;
                     acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fabs(r1) * idr);
                     acc[kSlots + QY] += qi * y1;
@@ -928,14 +945,14 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                     const size_t i = at(b.AT_ci[k]);
                     const double a = widen(v[k]);
                     t0 += a * y[i];
-                    if (avg) t1 += a * (b.ysum[i] * inv_j);
+                    if (avg) t1 += a * (yav[i] * inv_j);
                     if (ray) tr += a * (y[i] - b.y[1][i]);
                 }
                 const size_t jj = at(j);
                 const double cj = b.c[jj], lj = b.l[jj], uj = b.u[jj], idc = b.inv_Dc[jj], xh = b.xa[jj];
                 const bool lf = isfinite(lj), uf = isfinite(uj);
                 const double lam[2] = {cj - t0, cj - t1};
-                const double xs[2] = {x[jj], avg ? b.xsum[jj] * inv_j : 0.0};
+                const double xs[2] = {x[jj], avg ? xav[jj] * inv_j : 0.0};
 #pragma unroll
                 for (int cnd = 0; cnd < 2; cnd++) {
                     if (cnd == 1 && !avg) break;
@@ -1045,7 +1062,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
     const int k = S->k_base + n_eval;
     const int j = S->j_base + n_eval;
     S->evals += 1;
-    S->inv_j = 1.0 / (double)j;
+    S->inv_j = S->adaptive ? (S->wsum > 0.0 ? 1.0 / S->wsum : 0.0) : 1.0 / (double)j;
     S->k_base = k;
     if (S->algo == ALG_HALPERN) {
         // candidate 0 = last map output; fixed-point residual terms in the second record
@@ -1136,6 +1153,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
         S->tau = S->eta / wn;
         S->sigma = S->eta * wn;
         S->cand = cand;
+        S->wsum = 0.0;
         S->action = ACT_RESTART;
     } else {
         S->kkt_prev = kc;
@@ -1186,6 +1204,161 @@ __global__ void __launch_bounds__(BS) k_apply(const Seg *__restrict__ segs, int 
 }
 
 // ---------------------------------------------------------------------------
+// adaptive step size (PDLP, averaging variant; sessions of one LP)
+// ---------------------------------------------------------------------------
+// Every iteration is an attempt with the trial step eta = S->ad_eta:
+//   k_ad_primal   x' = clip(x - (eta/omega)(c - A^T y), l, u) into the other
+//                 buffer; per CTA: sum (x' - x)^2
+//   k_ad_dual     y' = y + eta omega (q - A (2x' - x)), y'_I >= 0, into the
+//                 other buffer; A (x' - x) from the same gathers; per CTA:
+//                 sum (y' - y)^2 and sum (y' - y) (A (x' - x))_i
+//   k_ad_decide   eta_bar = (omega |dx|^2 + |dy|^2 / omega) / (2 |dy^T A dx|);
+//                 accepted when eta <= eta_bar (the current buffer flips and
+//                 the step enters the weight sum); next trial
+//                 min((1 - (a+2)^-0.3) eta_bar, (1 + (a+2)^-0.6) eta)
+//   k_ad_sum      running sums += eta * accepted point
+// Before each evaluation, k_ad_norm moves the current iterate to buffer 0, so
+// the evaluation, control and restart kernels of the averaging variant apply
+// unchanged.  The kernels are plain one-thread-per-row loops: the option is
+// for parity with the published method, not tuned.
+constexpr int kAdThreads = 256;
+
+__device__ __forceinline__ bool ad_live(const Scalars *S, int it) {
+    return S->status == RUNNING && S->k_base + it < S->max_iter;
+}
+
+// fixed-order CTA sum of NV values per thread into out[0..NV)
+template <int NV>
+__device__ __forceinline__ void ad_block_sum(double (&v)[NV], double *out) {
+    __shared__ double sh[kAdThreads / 32][NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double t = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = sh[0][threadIdx.x];
+        for (int w = 1; w < kAdThreads / 32; w++) t += sh[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kAdThreads) k_ad_primal(Bufs b, int n, int it) {
+    const Scalars *S = b.S;
+    if (!ad_live(S, it)) return;
+    const int src = S->ad_src;
+    const double tau = S->ad_eta / S->omega;
+    const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+    const double *__restrict__ y = b.y[src];
+    const int j = blockIdx.x * kAdThreads + threadIdx.x;
+    double d2[1] = {0.0};
+    if (j < n) {
+        double acc = -b.c[j];   // ends at A^T y - c
+        for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) acc = fma(widen(v[k]), y[b.AT_ci[k]], acc);
+        const double xin = b.x[src][j];
+        const double xv = fmin(fmax(fma(tau, acc, xin), b.l[j]), b.u[j]);
+        b.x[src ^ 1][j] = xv;
+        const double d = xv - xin;
+        d2[0] = d * d;
+    }
+    ad_block_sum<1>(d2, b.adp + blockIdx.x);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kAdThreads) k_ad_dual(Bufs b, int m, int m_eq, int it, int nbp) {
+    const Scalars *S = b.S;
+    if (!ad_live(S, it)) return;
+    const int src = S->ad_src;
+    const double sigma = S->ad_eta * S->omega;
+    const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    const double *__restrict__ xn = b.x[src ^ 1];
+    const double *__restrict__ xo = b.x[src];
+    const int i = blockIdx.x * kAdThreads + threadIdx.x;
+    double r[2] = {0.0, 0.0};
+    if (i < m) {
+        double acc = -b.q[i];   // ends at A x-bar - q
+        double adx = 0.0;       // (A (x' - x))_i
+        for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
+            const int j = b.A_ci[k];
+            const double a = widen(v[k]);
+            acc = fma(a, fma(2.0, xn[j], -xo[j]), acc);
+            adx = fma(a, xn[j] - xo[j], adx);
+        }
+        const double yin = b.y[src][i];
+        double yv = fma(-sigma, acc, yin);
+        if (i >= m_eq) yv = fmax(yv, 0.0);
+        b.y[src ^ 1][i] = yv;
+        const double dy = yv - yin;
+        r[0] = dy * dy;
+        r[1] = dy * adx;
+    }
+    ad_block_sum<2>(r, b.adp + nbp + 2 * (size_t)blockIdx.x);
+}
+
+// one CTA: the attempt's sums in a fixed order, then the acceptance test
+__global__ void __launch_bounds__(1024) k_ad_decide(Bufs b, int nbp, int nbd, int it) {
+    Scalars *S = b.S;
+    if (!ad_live(S, it)) return;
+    __shared__ double sh[3][1024];
+    double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
+    for (int p = threadIdx.x; p < nbp; p += 1024) dx2 += b.adp[p];
+    for (int p = threadIdx.x; p < nbd; p += 1024) {
+        dy2 += b.adp[nbp + 2 * p];
+        inter += b.adp[nbp + 2 * p + 1];
+    }
+    sh[0][threadIdx.x] = dx2; sh[1][threadIdx.x] = dy2; sh[2][threadIdx.x] = inter;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int q = 0; q < 3; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double om = S->omega, eta = S->ad_eta;
+    const double movement = om * sh[0][0] + sh[1][0] / om;
+    const double interaction = fabs(sh[2][0]);
+    const double eta_bar = interaction > 0.0 ? movement / (2.0 * interaction) : INFINITY;
+    const int a = S->k_base + it;   // attempt number (0-based)
+    const double eta_next = fmin(b.adS[a] * eta_bar, b.adG[a] * eta);
+    if (eta <= eta_bar) {
+        S->ad_src ^= 1;
+        S->ad_w = eta;
+        S->wsum += eta;
+        S->ad_acc += 1;
+    } else {
+        S->ad_w = 0.0;
+    }
+    S->ad_eta = eta_next;
+}
+
+// running sums += step * accepted point (columns, then rows)
+__global__ void k_ad_sum(Bufs b, int n, int m, int it) {
+    const Scalars *S = b.S;
+    if (!ad_live(S, it)) return;
+    const double w = S->ad_w;
+    if (w == 0.0) return;
+    const int cur = S->ad_src;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b.xsum[e] = fma(w, b.x[cur][e], b.xsum[e]);
+    else if (e < n + m) b.ysum[e - n] = fma(w, b.y[cur][e - n], b.ysum[e - n]);
+}
+
+// before an evaluation: the current iterate to buffer 0 ...
+__global__ void k_ad_norm(Bufs b, int n, int m) {
+    const Scalars *S = b.S;
+    if (S->ad_src != 1) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b.x[0][e] = b.x[1][e];
+    else if (e < n + m) b.y[0][e - n] = b.y[1][e - n];
+}
+// ... and then the buffer index to 0
+__global__ void k_ad_src0(Bufs b) { b.S->ad_src = 0; }
+
+// ---------------------------------------------------------------------------
 // host orchestration: a device-resident session of k LPs
 // ---------------------------------------------------------------------------
 #define UC_CUDA(call)                                                                  \
@@ -1203,11 +1376,11 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Layout {
     // uploaded once
     size_t A_rp, A_ci, A_v, AT_rp, AT_ci, AT_v, segs_p, segs_d, segs_e, segs_a, ranges;
-    size_t W, W1;
+    size_t W, W1, adS, adG;
     // per-LP data (replaced by update_lp)
     size_t c, l, u, Dc, q, Dr, inv_Dc, inv_Dr, lkey, ukey, x_init, y_init, S_init;
     // working state
-    size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status;
+    size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status, adp;
     // staged kernels: chunk lists and per-CTA ranges
     size_t chunks_p, chunks_d, ctas_p, ctas_d;
     // lanes sessions: contiguous staging for one LP's vectors (4 (n + m) doubles:
@@ -1225,6 +1398,7 @@ struct uc_session {
     bool pdl = true;              // programmatic dependent launch between iteration kernels
     cudaError_t launch_err = cudaSuccess;
     int algo = 0;                 // ALG_HALPERN / ALG_AVERAGE (all LPs of a session)
+    bool adaptive = false;        // adaptive step size (averaging variant, one LP)
     size_t vs = 8;
     uc_solve_opts o{};
     cudaStream_t s = nullptr;
@@ -1430,6 +1604,8 @@ static Scalars make_scalars(const uc_session &X, const PsData &p, double omega =
     s.status = NEEDS_INIT;
     s.algo = X.algo;
     s.metric = X.o.restart_metric;
+    s.adaptive = X.adaptive ? 1 : 0;
+    s.ad_eta = p.eta;
     return s;
 }
 
@@ -1618,6 +1794,33 @@ static void launch_apply(uc_session &X, cudaStream_t s) {
     }
 }
 
+// n_eval attempts of the adaptive step, then the move of the current iterate
+// to buffer 0 (before the evaluation)
+static void launch_adaptive(uc_session &X, cudaStream_t s, int it, const std::function<void(int)> &rec) {
+    const int n = (int)X.Nr, m = (int)X.Mr;
+    const int nbp = (n + kAdThreads - 1) / kAdThreads, nbd = (m + kAdThreads - 1) / kAdThreads;
+    const int ne = (n + m + 255) / 256;
+    rec(0);
+    if (nbp) {
+        if (X.vb == 32) k_ad_primal<float><<<nbp, kAdThreads, 0, s>>>(X.b, n, it);
+        else k_ad_primal<double><<<nbp, kAdThreads, 0, s>>>(X.b, n, it);
+    }
+    rec(1);
+    if (nbd) {
+        if (X.vb == 32) k_ad_dual<float><<<nbd, kAdThreads, 0, s>>>(X.b, m, X.m_eq[0], it, nbp);
+        else k_ad_dual<double><<<nbd, kAdThreads, 0, s>>>(X.b, m, X.m_eq[0], it, nbp);
+    }
+    rec(2);
+    k_ad_decide<<<1, 1024, 0, s>>>(X.b, nbp, nbd, it);
+    if (ne) k_ad_sum<<<ne, 256, 0, s>>>(X.b, n, m, it);
+}
+static void launch_adaptive_norm(uc_session &X, cudaStream_t s) {
+    const int n = (int)X.Nr, m = (int)X.Mr;
+    const int ne = (n + m + 255) / 256;
+    if (ne) k_ad_norm<<<ne, 256, 0, s>>>(X.b, n, m);
+    k_ad_src0<<<1, 1, 0, s>>>(X.b);
+}
+
 static int capture(uc_session &X, int gi) {
     cudaStream_t s = X.s;
     const bool timing = X.o.kernel_timing != 0;
@@ -1631,6 +1834,10 @@ static int capture(uc_session &X, int gi) {
     // only the event nodes around it break the programmatic overlap
     const int timed_it = X.o.n_eval / 2;
     for (int it = 0; it < X.o.n_eval; it++) {
+        if (X.adaptive) {
+            launch_adaptive(X, s, it, [&](int e) { if (it == timed_it) rec(e); });
+            continue;
+        }
         const int src = it & 1;
         if (it == timed_it) rec(0);
         if (X.n_sp) launch_primal(X, s, it, src);
@@ -1638,6 +1845,7 @@ static int capture(uc_session &X, int gi) {
         if (X.n_sd) launch_dual(X, s, it, src);
         if (it == timed_it) rec(2);
     }
+    if (X.adaptive) launch_adaptive_norm(X, s);
     launch_eval(X, s, 1);
     launch_apply(X, s);
     if (err == cudaSuccess) err = cudaGetLastError();
@@ -1662,10 +1870,15 @@ static int launch_direct(uc_session &X) {
     cudaStream_t s = X.s;
     const Bufs &b = X.b;
     for (int it = 0; it < X.o.n_eval; it++) {
+        if (X.adaptive) {
+            launch_adaptive(X, s, it, [](int) {});
+            continue;
+        }
         const int src = it & 1;
         if (X.n_sp) launch_primal(X, s, it, src);
         if (X.n_sd) launch_dual(X, s, it, src);
     }
+    if (X.adaptive) launch_adaptive_norm(X, s);
     launch_eval(X, s, 1);
     launch_apply(X, s);
     UC_CUDA(cudaGetLastError());
@@ -1863,6 +2076,12 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         return UC_EINVAL;
     }
     X->algo = o.algorithm;
+    if (o.adaptive_step != 0 && o.adaptive_step != 1) { set_error("adaptive_step must be 0 or 1"); return UC_EINVAL; }
+    X->adaptive = o.adaptive_step == 1;
+    if (X->adaptive && (X->algo != ALG_AVERAGE || k != 1 || o.lanes || o.spmv_kernel == 2)) {
+        set_error("adaptive_step needs algorithm 1 (iterate averaging), one LP, no lanes, row kernels");
+        return UC_EINVAL;
+    }
     if (o.cta_rows != 0 && o.cta_rows != 128 && o.cta_rows != 256 && o.cta_rows != 512) {
         set_error("cta_rows must be 0, 128, 256 or 512");
         return UC_EINVAL;
@@ -1973,6 +2192,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     L.ctas_p = take(sizeof(int) * (X->gmax_p + 1)); L.ctas_d = take(sizeof(int) * (X->gmax_d + 1));
     const int nW = (int)std::min<long long>((long long)o.max_iter + 1, 1LL << 22);
     L.W = take(sizeof(double) * nW); L.W1 = take(sizeof(double) * nW);
+    const int64_t nAd = X->adaptive ? (int64_t)o.max_iter : 0;
+    L.adS = take(sizeof(double) * nAd); L.adG = take(sizeof(double) * nAd);
     L.c = take(N * 8); L.l = take(N * 8); L.u = take(N * 8); L.Dc = take(N * 8);
     L.inv_Dc = take(N * 8); L.lkey = take(N * 8); L.ukey = take(N * 8);
     L.q = take(M * 8); L.Dr = take(M * 8); L.inv_Dr = take(M * 8);
@@ -1982,6 +2203,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     L.xsum = take(N * 8); L.ysum = take(M * 8); L.xa = take(N * 8); L.ya = take(M * 8);
     L.xret = take(N * 8); L.yret = take(M * 8);
     L.part = take(sizeof(double) * kPart * X->n_se * X->K);
+    L.adp = take(X->adaptive ? sizeof(double) * (size_t)((Nr + kAdThreads - 1) / kAdThreads + 2 * ((Mr + kAdThreads - 1) / kAdThreads)) : 0);
     L.lane_stage = take(X->K > 1 ? (size_t)4 * (Nr + Mr) * 8 : 0);
     L.red = take(sizeof(double) * kPart * k);
     L.S = take(sizeof(Scalars) * k);
@@ -2032,6 +2254,13 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
             W[jj] = ((double)jj + 1.0) / ((double)jj + 2.0);
             W1[jj] = 1.0 - W[jj];
         }
+        // adaptive step factors of attempt a (k = a + 1 attempts, base k + 1 = a + 2),
+        // with the host's pow as the oracle computes them
+        double *adS = (double *)(st.data() + L.adS), *adG = (double *)(st.data() + L.adG);
+        for (int64_t a = 0; a < nAd; a++) {
+            adS[a] = 1.0 - std::pow((double)(a + 2), -0.3);
+            adG[a] = 1.0 + std::pow((double)(a + 2), -0.6);
+        }
     }
 
     if (user_stream) X->s = user_stream;
@@ -2064,6 +2293,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     b.inv_Dr = (const double *)(D + L.inv_Dr); b.inv_Dc = (const double *)(D + L.inv_Dc);
     b.lkey = (const long long *)(D + L.lkey); b.ukey = (const long long *)(D + L.ukey);
     b.W = (const double *)(D + L.W); b.W1 = (const double *)(D + L.W1); b.nW = nW;
+    b.adS = (const double *)(D + L.adS); b.adG = (const double *)(D + L.adG);
+    b.adp = (double *)(D + L.adp);
     b.red = (double *)(D + L.red);
     b.x[0] = (double *)(D + L.x0); b.x[1] = (double *)(D + L.x1);
     b.y[0] = (double *)(D + L.y0); b.y[1] = (double *)(D + L.y1);
@@ -2196,7 +2427,7 @@ static int session_run(uc_session &X, int max_replays) {
             UC_CUDA(cudaEventRecord(X.ev[launched & 3], s));
             launched++;
             X.polls++;
-            X.launches += 2LL * X.o.n_eval + 4;
+            X.launches += X.adaptive ? 4LL * X.o.n_eval + 6 : 2LL * X.o.n_eval + 4;
         }
         if (checked >= launched) break;
         UC_CUDA(cudaEventSynchronize(X.ev[checked & 3]));
@@ -2259,7 +2490,8 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     const int part = X.o.max_iter % n_eval;
     // current iterate: buffer 0 after a full block; after a limit reached
     // inside a block, buffer (max_iter mod n_eval) & 1
-    const int cur = (S.status == ITER_LIMIT) ? (part & 1) : 0;
+    // (adaptive step: buffer 0 always, moved there before every evaluation)
+    const int cur = (S.status == ITER_LIMIT && !X.adaptive) ? (part & 1) : 0;
     int j_now = S.j_base;
     if (S.status == ITER_LIMIT && part) j_now = S.j_base + part;
     res->x_cur.resize(n); res->y_cur.resize(m); res->x_avg.resize(n); res->y_avg.resize(m);
@@ -2301,7 +2533,11 @@ static int session_result(uc_session &X, int i, uc_result **out) {
         for (int r = 0; r < m; r++) res->y_ray[r] = res->y_ret[r] - y_in[r];
         if (X.reorder) to_natural(res->y_ray, X.prow[i]);
     }
-    if (!halp) {
+    if (!halp && X.adaptive) {   // step-weighted average (the current point before any accepted step)
+        for (int c = 0; c < n; c++) res->x_avg[c] = S.wsum > 0.0 ? res->x_avg[c] / S.wsum : res->x_cur[c];
+        for (int r = 0; r < m; r++) res->y_avg[r] = S.wsum > 0.0 ? res->y_avg[r] / S.wsum : res->y_cur[r];
+        if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
+    } else if (!halp) {
         for (int c = 0; c < n; c++) res->x_avg[c] = j_now ? res->x_avg[c] / j_now : res->x_cur[c];
         for (int r = 0; r < m; r++) res->y_avg[r] = j_now ? res->y_avg[r] / j_now : res->y_cur[r];
         if (S.status != OPTIMAL) { res->x_ret = res->x_cur; res->y_ret = res->y_cur; }
@@ -2336,6 +2572,7 @@ static int session_result(uc_session &X, int i, uc_result **out) {
     o.dual_kernel_ms = X.timed ? X.td_sum / X.timed : 0.0;
     o.timed_launches = X.timed;
     o.kernel_launches = (int)std::min<long long>(X.launches, INT32_MAX);
+    o.rejected_steps = X.adaptive ? std::max(0, o.iters - S.ad_acc) : 0;
     o.h2d_bytes = X.h2d;
     o.d2h_bytes = (long long)(n + m) * 8 * ((S.status == OPTIMAL || halp) ? 3 : 2) + (long long)sizeof(Scalars) +
                   X.polls * 4LL * X.k;

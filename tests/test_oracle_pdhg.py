@@ -276,3 +276,13 @@ def test_adaptive_average_is_step_weighted():
     assert st.w_sum == pytest.approx(ws, rel=1e-13)
     np.testing.assert_allclose(st.x_sum / st.w_sum, xs / ws, rtol=1e-12, atol=1e-15)
     assert st.accepted < 1500 and st.k == 1500
+
+
+def test_adaptive_exact_sums_move_only_rounding():
+    # correctly rounded sums in the step bound change the first attempts' iterates
+    # only at rounding level (the sensitivity the device parity tests measure)
+    raw, ps, S = _pipeline(_small(0))
+    a = pdhg.solve(S, tol=0.0, max_iter=64, adaptive=True)
+    b = pdhg.solve(S, tol=0.0, max_iter=64, adaptive=True, exact_sums=True)
+    assert np.max(np.abs(a.x - b.x)) <= 1e-11 * np.max(np.abs(a.x))
+    assert np.max(np.abs(a.y - b.y)) <= 1e-11 * np.max(np.abs(a.y))
