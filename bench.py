@@ -160,6 +160,8 @@ def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
     mat = nnz * (vs + 4)
     if algorithm == "halpern":
         return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 8 * n + 32 * m
+    if algorithm == "average-adaptive":   # attempt kernels: no sums (a separate kernel adds them)
+        return mat + 4 * (n + 1) + 8 * m + 40 * n, mat + 4 * (m + 1) + 16 * n + 24 * m
     return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 16 * n + 40 * m
 
 
@@ -171,6 +173,8 @@ def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
 def fp64_inst_per_iter(n, m, nnz, algorithm="halpern"):
     if algorithm == "halpern":
         return nnz + 4 * n, nnz + 4 * m
+    if algorithm == "average-adaptive":   # + the squared step (primal), dy and its two products (dual)
+        return nnz + 3 * n, 3 * nnz + 4 * m
     return nnz + 2 * n, 2 * nnz + 2 * m
 
 
@@ -224,6 +228,7 @@ def run_ours(args):
                      stages=args.stages,
                      rows_per_thread=[rpt], cta_rows=cta,
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
+                     adaptive_step=args.adaptive_step,
                      reorder=not args.no_reorder)
 
     def solve_once():
@@ -262,14 +267,16 @@ def run_ours(args):
     n_timed = st["timed_launches"] - nt0
     tp = (st["primal_kernel_ms"] * st["timed_launches"] - tp0) / max(n_timed, 1)
     td = (st["dual_kernel_ms"] * st["timed_launches"] - td0) / max(n_timed, 1)
-    bp, bd = bytes_per_iter(n, m, nnz, vs, args.algorithm)
-    fp, fd = fp64_inst_per_iter(n, m, nnz, args.algorithm)
+    alg_key = "average-adaptive" if args.adaptive_step else args.algorithm
+    bp, bd = bytes_per_iter(n, m, nnz, vs, alg_key)
+    fp, fd = fp64_inst_per_iter(n, m, nnz, alg_key)
+    pname, dname = ("k_ad_primal", "k_ad_dual") if args.adaptive_step else ("k_primal", "k_dual")
     peak, peak_kind = _peaks()
     clk_sum = clk.summary()
     sm_mhz = clk_sum.get("sm_mhz") or 2070.0
     fp64_peak = FP64_INST_PER_CLK * sm_mhz * 1e6 / 1e9      # G FP64 instructions / s
     kern = {}
-    for name, b_, f_, t_ in (("k_primal", bp, fp, tp), ("k_dual", bd, fd, td)):
+    for name, b_, f_, t_ in ((pname, bp, fp, tp), (dname, bd, fd, td)):
         if t_ <= 0:
             continue
         gbs = b_ / (t_ / 1e3) / 1e9
@@ -279,7 +286,7 @@ def run_ours(args):
                       "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
                       "alu_fp64": {"achieved": gis, "peak": fp64_peak, "unit": "G FP64 inst/s",
                                    "frac": gis / fp64_peak}}
-    dom = max(kern, key=lambda k: kern[k]["mean_launch_us"]) if kern else "k_primal"
+    dom = max(kern, key=lambda k: kern[k]["mean_launch_us"]) if kern else pname
     dk = kern.get(dom, {"hbm": {"frac": 0, "achieved": 0, "peak": peak, "unit": "GB/s"},
                         "alu_fp64": {"frac": 0, "achieved": 0, "peak": fp64_peak, "unit": ""},
                         "mean_launch_us": 0, "algorithmic_bytes_per_launch": 0})
@@ -312,6 +319,7 @@ def run_ours(args):
             lp2 = B.uc_build_lp(P)
             ps2 = B.uc_presolve(lp2, value_bits=vbits, power_device=pw_dev)
             r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter, algorithm=args.algorithm,
+                                 adaptive_step=args.adaptive_step,
                                  restart_metric=args.restart_metric)
             sol = B.uc_get_solution(r2, P.T, P.B, P.L, P.G)
             tot_it += sol["stats"]["iters"]
@@ -339,11 +347,12 @@ def run_ours(args):
             "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
                            tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
                            algorithm=args.algorithm, restart_metric=args.restart_metric,
+                           adaptive_step=bool(args.adaptive_step),
                            rows_per_thread=rpt, cta_rows=cta or 128,
                            l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
                            parallelism=f"replicas x{world}"),
             "time_to_1e-4_ms": ms_max / args.steps,
-            "iters_per_solve": st["iters"], "status": st["status_name"],
+            "iters_per_solve": st["iters"], "status": st["status_name"], "rejected_steps": st["rejected_steps"],
             "rel_kkt": max(st["rel_primal"], st["rel_dual"], st["rel_gap"]),
             "objective": st["objective"], "restarts": st["restarts"],
             "pdhg_iters_per_s_per_gpu": total_iters / world / (ms_max / 1e3),
@@ -612,6 +621,8 @@ def main():
                     help="0 default (thread per row), 1 thread per row, 2 staged")
     ap.add_argument("--stages", type=int, default=0, help="staged kernels: chunks in flight per CTA (0: 2)")
     ap.add_argument("--algorithm", default="halpern", choices=["halpern", "average"])
+    ap.add_argument("--adaptive-step", action="store_true",
+                    help="PDLP adaptive step size (needs --algorithm average)")
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--no-reorder", action="store_true", help="keep the natural row/column order on the device")
     ap.add_argument("--cta-rows", type=int, default=0, help="threads per CTA of the iteration kernels (0: 128)")

@@ -1216,10 +1216,12 @@ __global__ void __launch_bounds__(BS) k_apply(const Seg *__restrict__ segs, int 
 //                 accepted when eta <= eta_bar (the current buffer flips and
 //                 the step enters the weight sum); next trial
 //                 min((1 - (a+2)^-0.3) eta_bar, (1 + (a+2)^-0.6) eta)
-//   k_ad_sum      running sums += eta * accepted point
-// Before each evaluation, k_ad_norm moves the current iterate to buffer 0, so
-// the evaluation, control and restart kernels of the averaging variant apply
-// unchanged.  The kernels are plain one-thread-per-row loops: the option is
+// An accepted step enters the running sums (+= eta * the accepted point) one
+// kernel later: the next attempt's primal and dual kernels read that point as
+// their input anyway, so they add it (S->ad_w holds the pending weight, 0 after
+// a rejection).  Before each evaluation, k_ad_norm adds the last pending
+// weight and moves the current iterate to buffer 0, so the evaluation, control
+// and restart kernels of the averaging variant apply unchanged.  The kernels are plain one-thread-per-row loops: the option is
 // for parity with the published method, not tuned.
 constexpr int kAdThreads = 256;
 
@@ -1251,16 +1253,18 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_primal(Bufs b, int n, int it)
     const Scalars *S = b.S;
     if (!ad_live(S, it)) return;
     const int src = S->ad_src;
-    const double tau = S->ad_eta / S->omega;
+    const double tau = S->ad_eta / S->omega, w = S->ad_w;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
     const int j = blockIdx.x * kAdThreads + threadIdx.x;
     double d2[1] = {0.0};
     if (j < n) {
-        double acc = -b.c[j];   // ends at A^T y - c
-        for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) acc = fma(widen(v[k]), y[b.AT_ci[k]], acc);
+        const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
         const double xin = b.x[src][j];
-        const double xv = fmin(fmax(fma(tau, acc, xin), b.l[j]), b.u[j]);
+        double acc = -ld_stream(b.c + j);   // ends at A^T y - c
+        for (int k = k0; k < k1; k++) acc = fma(widen(ld_stream(v + k)), y[ld_stream(b.AT_ci + k)], acc);
+        if (w != 0.0) b.xsum[j] = fma(w, xin, b.xsum[j]);   // the last accepted step
+        const double xv = fmin(fmax(fma(tau, acc, xin), ld_stream(b.l + j)), ld_stream(b.u + j));
         b.x[src ^ 1][j] = xv;
         const double d = xv - xin;
         d2[0] = d * d;
@@ -1273,22 +1277,24 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_dual(Bufs b, int m, int m_eq,
     const Scalars *S = b.S;
     if (!ad_live(S, it)) return;
     const int src = S->ad_src;
-    const double sigma = S->ad_eta * S->omega;
+    const double sigma = S->ad_eta * S->omega, w = S->ad_w;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
     const double *__restrict__ xn = b.x[src ^ 1];
     const double *__restrict__ xo = b.x[src];
     const int i = blockIdx.x * kAdThreads + threadIdx.x;
     double r[2] = {0.0, 0.0};
     if (i < m) {
-        double acc = -b.q[i];   // ends at A x-bar - q
-        double adx = 0.0;       // (A (x' - x))_i
-        for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
-            const int j = b.A_ci[k];
-            const double a = widen(v[k]);
+        const int k0 = __ldg(b.A_rp + i), k1 = __ldg(b.A_rp + i + 1);
+        const double yin = b.y[src][i];
+        double acc = -ld_stream(b.q + i);   // ends at A x-bar - q
+        double adx = 0.0;                   // (A (x' - x))_i
+        for (int k = k0; k < k1; k++) {
+            const int j = ld_stream(b.A_ci + k);
+            const double a = widen(ld_stream(v + k));
             acc = fma(a, fma(2.0, xn[j], -xo[j]), acc);
             adx = fma(a, xn[j] - xo[j], adx);
         }
-        const double yin = b.y[src][i];
+        if (w != 0.0) b.ysum[i] = fma(w, yin, b.ysum[i]);   // the last accepted step
         double yv = fma(-sigma, acc, yin);
         if (i >= m_eq) yv = fmax(yv, 0.0);
         b.y[src ^ 1][i] = yv;
@@ -1299,28 +1305,37 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_dual(Bufs b, int m, int m_eq,
     ad_block_sum<2>(r, b.adp + nbp + 2 * (size_t)blockIdx.x);
 }
 
-// one CTA: the attempt's sums in a fixed order, then the acceptance test
+// one CTA: the attempt's sums in a fixed order (strided partials per thread,
+// then warp shuffles, then the 32 warp sums), then the acceptance test
 __global__ void __launch_bounds__(1024) k_ad_decide(Bufs b, int nbp, int nbd, int it) {
     Scalars *S = b.S;
     if (!ad_live(S, it)) return;
-    __shared__ double sh[3][1024];
-    double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
-    for (int p = threadIdx.x; p < nbp; p += 1024) dx2 += b.adp[p];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int p = threadIdx.x; p < nbp; p += 1024) v[0] += b.adp[p];
     for (int p = threadIdx.x; p < nbd; p += 1024) {
-        dy2 += b.adp[nbp + 2 * p];
-        inter += b.adp[nbp + 2 * p + 1];
+        v[1] += b.adp[nbp + 2 * p];
+        v[2] += b.adp[nbp + 2 * p + 1];
     }
-    sh[0][threadIdx.x] = dx2; sh[1][threadIdx.x] = dy2; sh[2][threadIdx.x] = inter;
+    __shared__ double sh[32][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        if (lane == 0) sh[warp][q] = v[q];
+    }
     __syncthreads();
-    for (int h = 512; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-            for (int q = 0; q < 3; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + h];
-        __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        v[q] = sh[lane][q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     }
-    if (threadIdx.x != 0) return;
+    if (lane != 0) return;
     const double om = S->omega, eta = S->ad_eta;
-    const double movement = om * sh[0][0] + sh[1][0] / om;
-    const double interaction = fabs(sh[2][0]);
+    const double movement = om * v[0] + v[1] / om;
+    const double interaction = fabs(v[2]);
     const double eta_bar = interaction > 0.0 ? movement / (2.0 * interaction) : INFINITY;
     const int a = S->k_base + it;   // attempt number (0-based)
     const double eta_next = fmin(b.adS[a] * eta_bar, b.adG[a] * eta);
@@ -1335,28 +1350,28 @@ __global__ void __launch_bounds__(1024) k_ad_decide(Bufs b, int nbp, int nbd, in
     S->ad_eta = eta_next;
 }
 
-// running sums += step * accepted point (columns, then rows)
-__global__ void k_ad_sum(Bufs b, int n, int m, int it) {
-    const Scalars *S = b.S;
-    if (!ad_live(S, it)) return;
-    const double w = S->ad_w;
-    if (w == 0.0) return;
-    const int cur = S->ad_src;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) b.xsum[e] = fma(w, b.x[cur][e], b.xsum[e]);
-    else if (e < n + m) b.ysum[e - n] = fma(w, b.y[cur][e - n], b.ysum[e - n]);
-}
-
-// before an evaluation: the current iterate to buffer 0 ...
+// before an evaluation: the pending accepted step into the sums, and the
+// current iterate to buffer 0 ...
 __global__ void k_ad_norm(Bufs b, int n, int m) {
     const Scalars *S = b.S;
-    if (S->ad_src != 1) return;
+    const double w = S->ad_w;
+    const int cur = S->ad_src;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) b.x[0][e] = b.x[1][e];
-    else if (e < n + m) b.y[0][e - n] = b.y[1][e - n];
+    if (e < n) {
+        const double v = b.x[cur][e];
+        if (w != 0.0) b.xsum[e] = fma(w, v, b.xsum[e]);
+        if (cur == 1) b.x[0][e] = v;
+    } else if (e < n + m) {
+        const double v = b.y[cur][e - n];
+        if (w != 0.0) b.ysum[e - n] = fma(w, v, b.ysum[e - n]);
+        if (cur == 1) b.y[0][e - n] = v;
+    }
 }
-// ... and then the buffer index to 0
-__global__ void k_ad_src0(Bufs b) { b.S->ad_src = 0; }
+// ... and then the buffer index and the pending weight to 0
+__global__ void k_ad_src0(Bufs b) {
+    b.S->ad_src = 0;
+    b.S->ad_w = 0.0;
+}
 
 // ---------------------------------------------------------------------------
 // host orchestration: a device-resident session of k LPs
@@ -1799,7 +1814,6 @@ static void launch_apply(uc_session &X, cudaStream_t s) {
 static void launch_adaptive(uc_session &X, cudaStream_t s, int it, const std::function<void(int)> &rec) {
     const int n = (int)X.Nr, m = (int)X.Mr;
     const int nbp = (n + kAdThreads - 1) / kAdThreads, nbd = (m + kAdThreads - 1) / kAdThreads;
-    const int ne = (n + m + 255) / 256;
     rec(0);
     if (nbp) {
         if (X.vb == 32) k_ad_primal<float><<<nbp, kAdThreads, 0, s>>>(X.b, n, it);
@@ -1812,7 +1826,6 @@ static void launch_adaptive(uc_session &X, cudaStream_t s, int it, const std::fu
     }
     rec(2);
     k_ad_decide<<<1, 1024, 0, s>>>(X.b, nbp, nbd, it);
-    if (ne) k_ad_sum<<<ne, 256, 0, s>>>(X.b, n, m, it);
 }
 static void launch_adaptive_norm(uc_session &X, cudaStream_t s) {
     const int n = (int)X.Nr, m = (int)X.Mr;
@@ -2427,7 +2440,7 @@ static int session_run(uc_session &X, int max_replays) {
             UC_CUDA(cudaEventRecord(X.ev[launched & 3], s));
             launched++;
             X.polls++;
-            X.launches += X.adaptive ? 4LL * X.o.n_eval + 6 : 2LL * X.o.n_eval + 4;
+            X.launches += X.adaptive ? 3LL * X.o.n_eval + 6 : 2LL * X.o.n_eval + 4;
         }
         if (checked >= launched) break;
         UC_CUDA(cudaEventSynchronize(X.ev[checked & 3]));
