@@ -211,6 +211,17 @@ int uc_presolved_export(const uc_presolved *ps, int32_t *rowptr, int32_t *colidx
                         double *q, double *c, double *l, double *u, double *Dr, double *Dc,
                         int32_t *col_map, int32_t *row_map, double *scalars);
 
+/* The layout a device session gives the presolved LP (host only, no device
+ * needed): prow [m] and pcol [n] receive, for each device position in order, the
+ * presolved row / column stored there.  With reorder != 0 (the solver's
+ * default) rows and columns are sorted by the (kind, unit / bus / line, period)
+ * label of the raw row or column they come from, equality rows first, so that
+ * consecutive rows are one constraint of one entity in consecutive periods and
+ * a warp's gathers read consecutive entries; then, within windows of 1024
+ * positions, by decreasing number of entries (stable).  reorder = 0 gives the
+ * identity.  UC_EINVAL on null pointers; the caller owns both arrays. */
+int uc_presolved_device_order(const uc_presolved *ps, int reorder, int32_t *prow, int32_t *pcol);
+
 /* Restarted, diagonally scaled PDHG on the device (Sec. II-C "PDHG (GPU)"),
  * stopping at relative KKT <= tol_rel_kkt (infinity norm, unscaled presolved
  * LP) or at max_iter.  `stream` is a cudaStream_t (NULL: legacy default).

@@ -95,6 +95,7 @@ _SIGS = {
     "uc_get_solution": (C.c_int, [C.c_void_p, _d, _d, _d, _d, _d, _d, _d, _P(uc_stats)]),
     "uc_get_raw_solution": (C.c_int, [C.c_void_p, _d, _d]),
     "uc_get_iterate": (C.c_int, [C.c_void_p, C.c_int, _d, _d]),
+    "uc_presolved_device_order": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32)]),
     "uc_session_create": (C.c_int, [_P(C.c_void_p), C.c_int, _P(uc_solve_opts), C.c_void_p, _P(C.c_void_p)]),
     "uc_session_reset": (C.c_int, [C.c_void_p, C.c_int]),
     "uc_session_run": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int)]),
@@ -255,6 +256,16 @@ def uc_presolved_export(ps) -> dict:
     d.update(n=n, m=m, m_eq=m_eq, eta=s[0], omega0=s[1], norm_A=s[2], obj_const=s[3],
              q_inf=s[4], c_inf=s[5])
     return d
+
+
+def uc_presolved_device_order(ps, reorder: bool = True):
+    """(prow, pcol): the presolved row / column at each device position."""
+    n, m, _, _ = uc_presolved_dims(ps)
+    prow = np.zeros(m, np.int32)
+    pcol = np.zeros(n, np.int32)
+    _check(lib.uc_presolved_device_order(ps.ptr, int(bool(reorder)), _ptr(prow, C.c_int32), _ptr(pcol, C.c_int32)),
+           "uc_presolved_device_order")
+    return prow, pcol
 
 
 class _TorchAllocator:

@@ -2965,6 +2965,20 @@ using namespace uc;
 
 extern "C" {
 
+int uc_presolved_device_order(const uc_presolved *ps, int reorder, int32_t *prow, int32_t *pcol) {
+    if (!ps || !ps->d || !prow || !pcol) { set_error("uc_presolved_device_order: null argument"); return UC_EINVAL; }
+    try {
+        std::vector<int32_t> r, c;
+        dev::device_view(ps->d, reorder != 0, r, c);
+        std::memcpy(prow, r.data(), r.size() * sizeof(int32_t));
+        std::memcpy(pcol, c.data(), c.size() * sizeof(int32_t));
+    } catch (const std::bad_alloc &) {
+        set_error("uc_presolved_device_order: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
 int uc_session_create(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
                       uc_session **out) {
     if (!ps || !out || k < 1) { set_error("uc_session_create: bad arguments"); return UC_EINVAL; }

@@ -140,3 +140,52 @@ def test_power_device_without_a_device_fails_loudly(B):
         pytest.skip("a CUDA device is present")
     with pytest.raises(B.UCError, match="no CUDA device"):
         B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)), power_device=1)
+
+
+def _warp_sectors(rp, ci, order, inv_cols):
+    """Distinct 32-byte sectors a warp's gathers touch per gathered FP64 value,
+    for rows visited in `order` (device order) gathering at inv_cols[col]."""
+    L = np.diff(rp)[order]
+    secs = gathers = 0
+    for q in range(int(L.max())):
+        has = L > q
+        rows = order[has]
+        warp = np.nonzero(has)[0] // 32
+        sector = (inv_cols[ci[rp[rows] + q]] * 8) // 32
+        secs += len(np.unique(warp.astype(np.int64) * (1 << 32) + sector))
+        gathers += len(rows)
+    return secs / gathers
+
+
+@pytest.mark.parametrize("which", ["tiny", "paper"])
+def test_device_order_is_entity_major_and_length_windowed(B, which):
+    P = ucgen.tiny(0) if which == "tiny" else ucgen.paper_scale(0)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    d = B.uc_presolved_export(ps)
+    n, m, m_eq = d["n"], d["m"], d["m_eq"]
+    prow, pcol = B.uc_presolved_device_order(ps)
+    np.testing.assert_array_equal(np.sort(prow), np.arange(m))
+    np.testing.assert_array_equal(np.sort(pcol), np.arange(n))
+    assert (prow[:m_eq] < m_eq).all()                    # equality rows keep the first positions
+    rp, ci = d["rowptr"].astype(np.int64), d["colidx"].astype(np.int64)
+    lr = np.diff(rp)
+    lc = np.bincount(ci, minlength=n)
+    for order, lens, blocks in ((prow, lr, [(0, m_eq), (m_eq, m)]), (pcol, lc, [(0, n)])):
+        for b0, b1 in blocks:
+            for w0 in range(b0, b1, 1024):
+                w = lens[order[w0:min(b1, w0 + 1024)]]
+                assert (np.diff(w) <= 0).all()           # decreasing length inside a window
+    nat_r, nat_c = B.uc_presolved_device_order(ps, reorder=False)
+    np.testing.assert_array_equal(nat_r, np.arange(m))
+    np.testing.assert_array_equal(nat_c, np.arange(n))
+    if which == "paper":
+        # what the layout is for: a warp's gathers hit few sectors (natural order: ~0.69)
+        ATc = np.argsort(ci, kind="stable")
+        icol = np.empty(n, np.int64); icol[pcol] = np.arange(n)
+        irow = np.empty(m, np.int64); irow[prow] = np.arange(m)
+        rows_of = np.repeat(np.arange(m), lr)
+        rpT = np.concatenate([[0], np.cumsum(lc)])
+        ciT = rows_of[ATc]
+        assert _warp_sectors(rp, ci, prow.astype(np.int64), icol) <= 0.3
+        assert _warp_sectors(rpT, ciT, pcol.astype(np.int64), irow) <= 0.3
+        assert _warp_sectors(rp, ci, np.arange(m), np.arange(n)) >= 0.6
