@@ -160,8 +160,8 @@ def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
     mat = nnz * (vs + 4)
     if algorithm == "halpern":
         return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 8 * n + 32 * m
-    if algorithm == "average-adaptive":   # attempt kernels: no sums (a separate kernel adds them)
-        return mat + 4 * (n + 1) + 8 * m + 40 * n, mat + 4 * (m + 1) + 16 * n + 24 * m
+    # averaging, constant or adaptive step (the adaptive kernels add the previous
+    # attempt's accepted point to the sums, so they touch the same vectors)
     return mat + 4 * (n + 1) + 8 * m + 56 * n, mat + 4 * (m + 1) + 16 * n + 40 * m
 
 
@@ -173,8 +173,11 @@ def bytes_per_iter(n, m, nnz, vs, algorithm="halpern"):
 def fp64_inst_per_iter(n, m, nnz, algorithm="halpern"):
     if algorithm == "halpern":
         return nnz + 4 * n, nnz + 4 * m
-    if algorithm == "average-adaptive":   # + the squared step (primal), dy and its two products (dual)
-        return nnz + 3 * n, 3 * nnz + 4 * m
+    if algorithm == "average-adaptive":
+        # primal per column: the step, clip bounds, dx, dx^2 and the sum (FP64 min / max
+        # counted); dual per entry: x-bar, its FMA, dx and the A dx FMA; per row: the
+        # step, projection, dy, dy^2, dy (A dx) and the sum
+        return nnz + 6 * n, 4 * nnz + 6 * m
     return nnz + 2 * n, 2 * nnz + 2 * m
 
 
