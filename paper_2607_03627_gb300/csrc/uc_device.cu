@@ -76,6 +76,10 @@ struct Scalars {
     // restart, buffer of the current iterate, accepted attempts
     int adaptive, ad_src, ad_acc;
     double ad_eta, ad_w, wsum;
+    // quotients the kernels would otherwise divide out per thread (an FP64
+    // division is a long FP64 sequence): the trial step's tau and sigma, 1 / wsum,
+    // and 1 / (steps averaged) at the next evaluation of the constant-step variant
+    double ad_tau, ad_sigma, inv_wsum, inv_next;
 };
 // kkt_anchor / kkt_prev hold the restart metric's anchor and previous value
 // for the Halpern variant as well.
@@ -892,10 +896,10 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
         double inv_j = 0.0;
         const double *xav = b.xsum, *yav = b.ysum;
         if (avg && S->adaptive) {
-            if (S->wsum > 0.0) inv_j = 1.0 / S->wsum;
+            if (S->wsum > 0.0) inv_j = S->inv_wsum;
             else { inv_j = 1.0; xav = x; yav = y; }
         } else if (avg) {
-            inv_j = 1.0 / (double)(S->j_base + S->n_eval);
+            inv_j = S->inv_next;   // 1 / (j_base + n_eval)
         }
         const bool rows = (sg.aux & 1) == 0;
         const int eq_end = sg.aux >> 1;   // rows: first ">=" row
@@ -1062,7 +1066,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
     const int k = S->k_base + n_eval;
     const int j = S->j_base + n_eval;
     S->evals += 1;
-    S->inv_j = S->adaptive ? (S->wsum > 0.0 ? 1.0 / S->wsum : 0.0) : 1.0 / (double)j;
+    S->inv_j = S->adaptive ? (S->wsum > 0.0 ? S->inv_wsum : 0.0) : S->inv_next;
     S->k_base = k;
     if (S->algo == ALG_HALPERN) {
         // candidate 0 = last map output; fixed-point residual terms in the second record
@@ -1154,11 +1158,15 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
         S->sigma = S->eta * wn;
         S->cand = cand;
         S->wsum = 0.0;
+        S->inv_wsum = 0.0;
+        S->ad_tau = S->ad_eta / wn;
+        S->ad_sigma = S->ad_eta * wn;
         S->action = ACT_RESTART;
     } else {
         S->kkt_prev = kc;
         S->j_base = j;
     }
+    S->inv_next = 1.0 / (double)(S->j_base + n_eval);
     if (k >= S->max_iter) {
         S->status = ITER_LIMIT;
         b.status[inst] = S->status;
@@ -1253,7 +1261,7 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_primal(Bufs b, int n, int it)
     const Scalars *S = b.S;
     if (!ad_live(S, it)) return;
     const int src = S->ad_src;
-    const double tau = S->ad_eta / S->omega, w = S->ad_w;
+    const double tau = S->ad_tau, w = S->ad_w;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const double *__restrict__ y = b.y[src];
     const int j = blockIdx.x * kAdThreads + threadIdx.x;
@@ -1277,7 +1285,7 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_dual(Bufs b, int m, int m_eq,
     const Scalars *S = b.S;
     if (!ad_live(S, it)) return;
     const int src = S->ad_src;
-    const double sigma = S->ad_eta * S->omega, w = S->ad_w;
+    const double sigma = S->ad_sigma, w = S->ad_w;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
     const double *__restrict__ xn = b.x[src ^ 1];
     const double *__restrict__ xo = b.x[src];
@@ -1343,11 +1351,14 @@ __global__ void __launch_bounds__(1024) k_ad_decide(Bufs b, int nbp, int nbd, in
         S->ad_src ^= 1;
         S->ad_w = eta;
         S->wsum += eta;
+        S->inv_wsum = 1.0 / S->wsum;
         S->ad_acc += 1;
     } else {
         S->ad_w = 0.0;
     }
     S->ad_eta = eta_next;
+    S->ad_tau = eta_next / om;
+    S->ad_sigma = eta_next * om;
 }
 
 // before an evaluation: the pending accepted step into the sums, and the
@@ -1621,6 +1632,9 @@ static Scalars make_scalars(const uc_session &X, const PsData &p, double omega =
     s.metric = X.o.restart_metric;
     s.adaptive = X.adaptive ? 1 : 0;
     s.ad_eta = p.eta;
+    s.ad_tau = p.eta / w;
+    s.ad_sigma = p.eta * w;
+    s.inv_next = 1.0 / (double)X.o.n_eval;
     return s;
 }
 
