@@ -26,6 +26,7 @@ step size as an option of the averaging variant):
 * ``closed``    -- O4: one-bus merit order, two-bus congestion, PTDF flows.
 
 Parity status: every function is pinned by tests under ``tests/`` against
-brute force, closed forms or invariants, except the absolute feasibility
-figure (``kkt.abs_primal_inf``) which is reported only ("parity unpinned").
+brute force, closed forms or invariants (the absolute feasibility figure
+``kkt.abs_primal_inf``, reported only, against element-by-element loops and
+the simplex optimum).
 """

@@ -116,7 +116,9 @@ def is_infeasibility_certificate(lp, y, eps: float = INFEASIBLE_EPS) -> bool:
 
 
 def abs_primal_inf(lp, x) -> float:
-    """max_i |violation_i| plus bound violation (reported only: parity unpinned)."""
+    """Largest absolute violation of a row (|r| for equality rows, max(-r, 0)
+    for ">=" rows) or of a bound (Sec. II-D absolute feasibility, reported, not
+    gated)."""
     r = lp.A @ x - lp.q
     r[lp.m_eq:] = np.minimum(r[lp.m_eq:], 0.0)
     bv = np.maximum(lp.l - x, 0.0) + np.maximum(x - lp.u, 0.0)

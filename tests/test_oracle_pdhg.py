@@ -286,3 +286,43 @@ def test_adaptive_exact_sums_move_only_rounding():
     b = pdhg.solve(S, tol=0.0, max_iter=64, adaptive=True, exact_sums=True)
     assert np.max(np.abs(a.x - b.x)) <= 1e-11 * np.max(np.abs(a.x))
     assert np.max(np.abs(a.y - b.y)) <= 1e-11 * np.max(np.abs(a.y))
+
+
+# ---------------------------------------------------------------------------
+# absolute primal infeasibility (the reported 1e-5 figure)
+# ---------------------------------------------------------------------------
+def _abs_violation_by_loops(lp, x):
+    """max over rows and bounds of the violation, one element at a time."""
+    A = lp.A.tocsr()
+    worst = 0.0
+    for i in range(A.shape[0]):
+        act = 0.0
+        for k in range(A.indptr[i], A.indptr[i + 1]):
+            act += A.data[k] * x[A.indices[k]]
+        r = act - lp.q[i]
+        v = abs(r) if i < lp.m_eq else max(-r, 0.0)
+        worst = max(worst, v)
+    for j in range(A.shape[1]):
+        worst = max(worst, lp.l[j] - x[j], x[j] - lp.u[j])
+    return worst
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_abs_primal_inf_matches_loops_and_vanishes_at_the_optimum(seed):
+    P = ucgen.micro(seed, B=6, L=8, G=3, T=4)
+    raw = olp.build_lp(P)
+    ref = simplex.solve_lp(raw)
+    scale = 1.0 + float(np.max(np.abs(raw.q)))
+    # a basic optimal point is feasible to the simplex's tolerance
+    assert kkt.abs_primal_inf(raw, ref.x) <= 1e-8 * scale
+    assert _abs_violation_by_loops(raw, ref.x) <= 1e-8 * scale
+    # random points, inside and outside the bounds
+    rng = np.random.default_rng(seed)
+    lo = np.where(np.isfinite(raw.l), raw.l, -50.0)
+    hi = np.where(np.isfinite(raw.u), raw.u, 50.0)
+    for _ in range(5):
+        x = rng.uniform(lo - 10.0, hi + 10.0)
+        got = kkt.abs_primal_inf(raw, x)
+        want = _abs_violation_by_loops(raw, x)
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-12)
+        assert got > 0.0
