@@ -863,6 +863,18 @@ __device__ __forceinline__ void block_reduce_record(const double (&acc)[kPart], 
     }
 }
 
+// Selections of the evaluation on the integer pipe (the kernel is FP64-bound):
+// sign and finiteness from the bit pattern, max(v, 0) / min(v, 0) as a choice
+// between v and 0.  Where they differ from fmax / fmin (a zero's sign) the
+// value is only squared, taken absolutely or added to a sum, so the records
+// are unchanged.
+__device__ __forceinline__ bool is_neg(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool is_fin(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ double pos_part(double v) { return is_neg(v) ? 0.0 : v; }
+__device__ __forceinline__ double neg_part(double v) { return is_neg(v) ? v : 0.0; }
+
 // mode 0: the start point (candidate 0 only); mode 1: regular evaluation.
 // Average variant: candidate 0 = current point, candidate 1 = average since the
 // last restart.  Halpern variant: candidate 0 = the last map output
@@ -917,7 +929,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 const double qi = b.q[ii], idr = b.inv_Dr[ii], yh = b.ya[ii];
                 const bool ineq = i >= eq_end;
                 double r0 = ax0 - qi;
-                if (ineq) r0 = fmin(r0, 0.0);
+                if (ineq && !is_neg(r0)) r0 = 0.0;
                 const double y0 = y[ii];
                 acc[RP2] += r0 * r0;
                 acc[RPU] = nnmax(acc[RPU], fabs(r0) * idr);
@@ -925,7 +937,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 acc[DY2] += (y0 - yh) * (y0 - yh);
                 if (avg) {
                     double r1 = ax1 - qi;
-                    if (ineq) r1 = fmin(r1, 0.0);
+                    if (ineq && !is_neg(r1)) r1 = 0.0;
                     const double y1 = yav[ii] * inv_j;
                     acc[kSlots + RP2] += r1 * r1;
                     acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fabs(r1) * idr);
@@ -938,7 +950,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 if (ray) {
                     const double dy = y0 - b.y[1][ii];
                     acc[kSlots + QY] += qi * dy;
-                    if (ineq) acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], fmax(-dy, 0.0) * b.Dr[ii]);
+                    if (ineq) acc[kSlots + RPU] = nnmax(acc[kSlots + RPU], (is_neg(dy) ? -dy : 0.0) * b.Dr[ii]);
                 }
             }
         } else {
@@ -954,18 +966,18 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 }
                 const size_t jj = at(j);
                 const double cj = b.c[jj], lj = b.l[jj], uj = b.u[jj], idc = b.inv_Dc[jj], xh = b.xa[jj];
-                const bool lf = isfinite(lj), uf = isfinite(uj);
+                const bool lf = is_fin(lj), uf = is_fin(uj);
                 const double lam[2] = {cj - t0, cj - t1};
                 const double xs[2] = {x[jj], avg ? xav[jj] * inv_j : 0.0};
 #pragma unroll
                 for (int cnd = 0; cnd < 2; cnd++) {
                     if (cnd == 1 && !avg) break;
                     const double lm = lam[cnd];
-                    const double lp = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
+                    const double lp = (lf && uf) ? lm : lf ? pos_part(lm) : uf ? neg_part(lm) : 0.0;
                     const double rd = lm - lp;
                     double bnd = 0.0;
-                    if (lf) bnd += lj * fmax(lp, 0.0);
-                    if (uf) bnd += uj * fmin(lp, 0.0);
+                    if (lf) bnd += lj * pos_part(lp);
+                    if (uf) bnd += uj * neg_part(lp);
                     double *a = acc + cnd * kSlots;
                     a[RD2] += rd * rd;
                     a[RDU] = nnmax(a[RDU], fabs(rd) * idc);
@@ -979,10 +991,10 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 }
                 if (ray) {   // reduced cost of the direction: lam = -A^T dy
                     const double lm = -tr;
-                    const double lp = (lf && uf) ? lm : lf ? fmax(lm, 0.0) : uf ? fmin(lm, 0.0) : 0.0;
+                    const double lp = (lf && uf) ? lm : lf ? pos_part(lm) : uf ? neg_part(lm) : 0.0;
                     double bnd = 0.0;
-                    if (lf) bnd += lj * fmax(lp, 0.0);
-                    if (uf) bnd += uj * fmin(lp, 0.0);
+                    if (lf) bnd += lj * pos_part(lp);
+                    if (uf) bnd += uj * neg_part(lp);
                     acc[kSlots + BND] += bnd;
                     acc[kSlots + RDU] = nnmax(acc[kSlots + RDU], fabs(lm - lp) * idc);
                 }
