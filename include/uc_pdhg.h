@@ -120,9 +120,11 @@ typedef struct {
     const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or
                                     4 (default 1); results do not depend on it (autotuned per size
                                     bucket, so LPs of one launch may differ) */
-    int no_reorder;              /* 1: keep the LP's row/column order on the device (default: rows
-                                    and columns sorted by length within 1024-row windows so warps
-                                    see similar lengths; results come back in the LP's order) */
+    int no_reorder;              /* 1: keep the LP's row/column order on the device.  Default: the
+                                    layout of uc_presolved_device_order (entity-major, so a warp's
+                                    gathers are contiguous, then sorted by length within 1024-row
+                                    windows so warps see similar lengths); iterates are identical
+                                    either way and results come back in the LP's order */
     int no_pdl;                  /* 1: launch iteration kernels without programmatic dependent
                                     launch (no overlap of consecutive kernels); default 0 */
     int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
