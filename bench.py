@@ -10,8 +10,17 @@ is PDHG iterations per second summed over ranks (weak scaling: every rank
 solves its own copy; no collective on the data path).  Time-to-1e-4 per LP,
 the algorithmic HBM bandwidth and the kernel roofline are reported beside it.
 `e2e` repeats the step through the public C ABI from host arrays (LP build,
-presolve, upload, solve, download, postsolve).  `--impl reference` times the
-CPU oracle (the same algorithm, plain numpy) on a bounded sample.
+presolve with its power iteration on the device, upload, solve, download,
+postsolve).  `--impl reference` times the CPU oracle (the same algorithm,
+plain numpy) on a bounded sample.
+
+Other configurations (`--config`): paper-fp32 (FP32 matrix values), tiny
+(30 buses, with the dense simplex timed too), batch64 (64 uneven LPs in one
+block-diagonal session against one-at-a-time solves), served (a Poisson
+request stream through the continuous-batching server, 2 shared-matrix slots,
+cold starts unless --warm-start), paper-lanes (load variants sharing one
+stored matrix).  `--algorithm average [--adaptive-step]` selects PDLP
+averaging, optionally with its adaptive step size.
 """
 import os
 
