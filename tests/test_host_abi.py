@@ -189,3 +189,56 @@ def test_device_order_is_entity_major_and_length_windowed(B, which):
         assert _warp_sectors(rp, ci, prow.astype(np.int64), icol) <= 0.3
         assert _warp_sectors(rpT, ciT, pcol.astype(np.int64), irow) <= 0.3
         assert _warp_sectors(rp, ci, np.arange(m), np.arange(n)) >= 0.6
+
+
+def _c_solve(B, pss, **kw):
+    """The C entry point called directly (the Python binding refuses to solve
+    without a CUDA device): (status, last error)."""
+    import ctypes
+    o, keep = B.solve_opts(**kw)
+    arr = (ctypes.c_void_p * len(pss))(*[p.ptr for p in pss])
+    outs = (ctypes.c_void_p * len(pss))()
+    if len(pss) == 1:
+        rc = B.lib.uc_solve(pss[0].ptr, ctypes.byref(o), None, outs)
+    else:
+        rc = B.lib.uc_solve_batch(arr, len(pss), ctypes.byref(o), None, outs)
+    return rc, B.lib.uc_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(n_eval=3), "n_eval must be even"),
+    (dict(max_iter=-1), "max_iter must be"),
+    (dict(spmv_kernel=3), "spmv_kernel must be"),
+    (dict(stages=1), "stages must be"),
+    (dict(cta_rows=100), "cta_rows must be"),
+    (dict(rows_per_thread=[3]), "rows_per_thread must be"),
+    (dict(adaptive_step=True), "adaptive_step needs"),                  # Halpern
+    (dict(algorithm="average", spmv_kernel=2), "staged kernels need"),
+])
+def test_solve_rejects_bad_options_before_touching_the_device(B, kw, msg):
+    ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)))
+    rc, err = _c_solve(B, [ps], **kw)
+    assert rc == B.UC_EINVAL and msg in err, (rc, err)
+
+
+def test_sessions_reject_bad_shapes_before_touching_the_device(B):
+    import ctypes
+    ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)))
+    for pss, kw, msg in (([ps] * 3, dict(lanes=True), "lanes sessions hold 2 or 4"),
+                         ([ps] * 2, dict(lanes=True, algorithm="average"), "lanes sessions run the Halpern"),
+                         ([ps] * 2, dict(algorithm="average", adaptive_step=True), "adaptive_step needs")):
+        rc, err = _c_solve(B, pss, **kw)
+        assert rc == B.UC_EINVAL and msg in err, (rc, err)
+    out = ctypes.c_void_p()
+    assert B.lib.uc_solve(None, None, None, ctypes.byref(out)) == B.UC_EINVAL
+    assert b"null argument" in B.lib.uc_last_error()
+    assert B.lib.uc_session_create(None, 1, None, None, ctypes.byref(out)) == B.UC_EINVAL
+
+
+def test_python_solve_fails_loudly_without_a_device(B):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)))
+    with pytest.raises(RuntimeError, match="needs a CUDA device"):
+        B.uc_solve(ps)
