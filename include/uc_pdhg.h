@@ -223,6 +223,16 @@ int uc_presolved_export(const uc_presolved *ps, int32_t *rowptr, int32_t *colidx
  * positions, by decreasing number of entries (stable).  reorder = 0 gives the
  * identity.  UC_EINVAL on null pointers; the caller owns both arrays. */
 int uc_presolved_device_order(const uc_presolved *ps, int reorder, int32_t *prow, int32_t *pcol);
+/* Period-strided groups of the device layout of A (transpose = 0) or A^T (1),
+ * host only.  Rows are taken in groups of 16 consecutive device rows; a group is
+ * strided when its rows have one entry count k and, for each entry q, row s of
+ * the group has device column col_q + s and value val_q.  counts [5] receives
+ * groups, strided groups, entries, entries in strided groups and slots.  When
+ * k, off, col and val are non-NULL they receive, per group, k (or -1) [groups],
+ * the first slot [groups + 1], and per slot the first row's device column and
+ * the shared value [slots]; call once with NULL arrays to size them. */
+int uc_presolved_strided_groups(const uc_presolved *ps, int transpose, int64_t *counts, int32_t *k,
+                                int32_t *off, int32_t *col, double *val);
 
 /* Restarted, diagonally scaled PDHG on the device (Sec. II-C "PDHG (GPU)"),
  * stopping at relative KKT <= tol_rel_kkt (infinity norm, unscaled presolved

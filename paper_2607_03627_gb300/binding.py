@@ -96,6 +96,8 @@ _SIGS = {
     "uc_get_raw_solution": (C.c_int, [C.c_void_p, _d, _d]),
     "uc_get_iterate": (C.c_int, [C.c_void_p, C.c_int, _d, _d]),
     "uc_presolved_device_order": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32)]),
+    "uc_presolved_strided_groups": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int64), _P(C.c_int32),
+                                              _P(C.c_int32), _P(C.c_int32), _d]),
     "uc_session_create": (C.c_int, [_P(C.c_void_p), C.c_int, _P(uc_solve_opts), C.c_void_p, _P(C.c_void_p)]),
     "uc_session_reset": (C.c_int, [C.c_void_p, C.c_int]),
     "uc_session_run": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int)]),
@@ -266,6 +268,24 @@ def uc_presolved_device_order(ps, reorder: bool = True):
     _check(lib.uc_presolved_device_order(ps.ptr, int(bool(reorder)), _ptr(prow, C.c_int32), _ptr(pcol, C.c_int32)),
            "uc_presolved_device_order")
     return prow, pcol
+
+
+def uc_presolved_strided_groups(ps, transpose: bool = False) -> dict:
+    """Period-strided 16-row groups of the device layout of A (or A^T): counts
+    and the descriptors (k per group, slot offsets, slot columns and values)."""
+    counts = np.zeros(5, np.int64)
+    _check(lib.uc_presolved_strided_groups(ps.ptr, int(bool(transpose)), _ptr(counts, C.c_int64),
+                                           None, None, None, None), "uc_presolved_strided_groups")
+    ng, slots = int(counts[0]), int(counts[4])
+    d = dict(k=np.zeros(ng, np.int32), off=np.zeros(ng + 1, np.int32), col=np.zeros(slots, np.int32),
+             val=np.zeros(slots))
+    _check(lib.uc_presolved_strided_groups(ps.ptr, int(bool(transpose)), _ptr(counts, C.c_int64),
+                                           _ptr(d["k"], C.c_int32), _ptr(d["off"], C.c_int32),
+                                           _ptr(d["col"], C.c_int32), _ptr(d["val"], C.c_double)),
+           "uc_presolved_strided_groups")
+    d.update(groups=ng, strided_groups=int(counts[1]), entries=int(counts[2]),
+             strided_entries=int(counts[3]), slots=slots)
+    return d
 
 
 class _TorchAllocator:

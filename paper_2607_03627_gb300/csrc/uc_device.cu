@@ -1608,6 +1608,55 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     return d;
 }
 
+// Period-strided groups of a device-order matrix.  In the entity-major layout
+// consecutive rows are one constraint of one entity in consecutive periods,
+// and the variables they use sit in consecutive device columns.  A group of
+// kStrideRows consecutive rows is "strided" when all its rows have the same
+// number of entries k and, for every entry q, row s of the group has column
+// col_q + s and value val_q: the group is then described by k (column, value)
+// slots instead of kStrideRows * k entries.  Other groups have k = -1.  Entry
+// order within a row is kept, so a kernel summing the slots in order does the
+// row's arithmetic in the same order as the CSR row.
+constexpr int kStrideRows = 16;
+
+struct StridedGroups {
+    std::vector<int32_t> k;     // per group: entries per row, or -1
+    std::vector<int32_t> off;   // per group: first slot (groups + 1 offsets)
+    std::vector<int32_t> col;   // per slot: device column of the group's first row
+    std::vector<double> val;    // per slot: the value all rows of the group share
+};
+
+static StridedGroups strided_groups(const Csr &M) {
+    StridedGroups g;
+    const int rows = M.rows;
+    const int ng = (rows + kStrideRows - 1) / kStrideRows;
+    g.k.assign(ng, -1);
+    g.off.assign((size_t)ng + 1, 0);
+    for (int gi = 0; gi < ng; gi++) {
+        g.off[gi] = (int32_t)g.col.size();
+        const int r0 = gi * kStrideRows;
+        if (r0 + kStrideRows > rows) continue;   // a ragged last group stays on the CSR path
+        const int k = M.rowptr[r0 + 1] - M.rowptr[r0];
+        bool ok = k > 0;
+        for (int s = 1; ok && s < kStrideRows; s++) {
+            const int r = r0 + s;
+            if (M.rowptr[r + 1] - M.rowptr[r] != k) { ok = false; break; }
+            for (int q = 0; q < k; q++) {
+                const int32_t e0 = M.rowptr[r0] + q, e = M.rowptr[r] + q;
+                if (M.colidx[e] != M.colidx[e0] + s || M.val[e] != M.val[e0]) { ok = false; break; }
+            }
+        }
+        if (!ok) continue;
+        g.k[gi] = k;
+        for (int q = 0; q < k; q++) {
+            g.col.push_back(M.colidx[M.rowptr[r0] + q]);
+            g.val.push_back(M.val[M.rowptr[r0] + q]);
+        }
+    }
+    g.off[ng] = (int32_t)g.col.size();
+    return g;
+}
+
 // same scaled matrix (structure, values as stored, equality rows)
 static bool same_matrix(const PsData &a, const PsData &b) {
     return a.n() == b.n() && a.m() == b.m() && a.m_eq == b.m_eq && a.value_bits == b.value_bits &&
@@ -3000,6 +3049,35 @@ int uc_presolved_device_order(const uc_presolved *ps, int reorder, int32_t *prow
         std::memcpy(pcol, c.data(), c.size() * sizeof(int32_t));
     } catch (const std::bad_alloc &) {
         set_error("uc_presolved_device_order: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
+int uc_presolved_strided_groups(const uc_presolved *ps, int transpose, int64_t *counts, int32_t *k,
+                                int32_t *off, int32_t *col, double *val) {
+    if (!ps || !ps->d || !counts) { set_error("uc_presolved_strided_groups: null argument"); return UC_EINVAL; }
+    try {
+        std::vector<int32_t> r, c;
+        const auto view = dev::device_view(ps->d, true, r, c);
+        const Csr &M = transpose ? view->AT : view->A;
+        const dev::StridedGroups g = dev::strided_groups(M);
+        int64_t sg = 0, se = 0;
+        for (size_t i = 0; i < g.k.size(); i++)
+            if (g.k[i] >= 0) { sg++; se += (int64_t)g.k[i] * dev::kStrideRows; }
+        counts[0] = (int64_t)g.k.size();
+        counts[1] = sg;
+        counts[2] = M.nnz();
+        counts[3] = se;
+        counts[4] = (int64_t)g.col.size();
+        if (k && off && col && val) {
+            std::memcpy(k, g.k.data(), g.k.size() * sizeof(int32_t));
+            std::memcpy(off, g.off.data(), g.off.size() * sizeof(int32_t));
+            std::memcpy(col, g.col.data(), g.col.size() * sizeof(int32_t));
+            std::memcpy(val, g.val.data(), g.val.size() * sizeof(double));
+        }
+    } catch (const std::bad_alloc &) {
+        set_error("uc_presolved_strided_groups: out of host memory");
         return UC_ENOMEM;
     }
     return UC_OK;

@@ -242,3 +242,55 @@ def test_python_solve_fails_loudly_without_a_device(B):
     ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)))
     with pytest.raises(RuntimeError, match="needs a CUDA device"):
         B.uc_solve(ps)
+
+
+def _device_csr(d, prow, pcol, transpose):
+    """The device-order matrix (rows in device order, columns relabelled to device
+    positions, each row's entries in their original order), built here."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((d["val"], d["colidx"], d["rowptr"]), shape=(d["m"], d["n"]))
+    M = A.T.tocsr() if transpose else A
+    rorder = (pcol if transpose else prow).astype(np.int64)
+    cperm = (prow if transpose else pcol).astype(np.int64)
+    cinv = np.empty(len(cperm), np.int64)
+    cinv[cperm] = np.arange(len(cperm))
+    lens = np.diff(M.indptr)[rorder]
+    indptr = np.concatenate([[0], np.cumsum(lens)])
+    take = np.concatenate([np.arange(M.indptr[r], M.indptr[r + 1]) for r in rorder]) if len(rorder) else []
+    return indptr, cinv[M.indices[take]], M.data[take]
+
+
+@pytest.mark.parametrize("which", ["tiny", "paper"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_strided_groups_describe_the_device_matrix_exactly(B, which, transpose):
+    P = ucgen.tiny(0) if which == "tiny" else ucgen.paper_scale(0)
+    ps = B.uc_presolve(B.uc_build_lp(P))
+    d = B.uc_presolved_export(ps)
+    prow, pcol = B.uc_presolved_device_order(ps)
+    rp, ci, va = _device_csr(d, prow, pcol, transpose)
+    g = B.uc_presolved_strided_groups(ps, transpose)
+    G = 16
+    rows = len(rp) - 1
+    assert g["groups"] == (rows + G - 1) // G and g["entries"] == len(ci)
+    rng = np.random.default_rng(0)
+    groups = np.arange(g["groups"]) if which == "tiny" else rng.choice(g["groups"], 3000, replace=False)
+    for gi in groups:
+        r0 = gi * G
+        k = int(g["k"][gi])
+        o = int(g["off"][gi])
+        if k >= 0:
+            cols, vals = g["col"][o:o + k], g["val"][o:o + k]
+            for s in range(G):
+                e0, e1 = rp[r0 + s], rp[r0 + s + 1]
+                np.testing.assert_array_equal(ci[e0:e1], cols + s)
+                np.testing.assert_array_equal(va[e0:e1], vals)
+        elif r0 + G <= rows:    # a full group left on the CSR path really breaks the pattern
+            lens = np.diff(rp[r0:r0 + G + 1])
+            if lens.min() == lens.max() and lens[0] > 0:
+                C = np.stack([ci[rp[r0 + s]:rp[r0 + s + 1]] for s in range(G)])
+                V = np.stack([va[rp[r0 + s]:rp[r0 + s + 1]] for s in range(G)])
+                assert not ((C - C[0] == np.arange(G)[:, None]).all() and (V == V[0]).all())
+    assert int(g["k"][g["k"] >= 0].astype(np.int64).sum()) == g["slots"]
+    assert g["strided_entries"] == int((g["k"][g["k"] >= 0].astype(np.int64) * G).sum())
+    if which == "paper":   # the time-expanded structure the layout exposes
+        assert g["strided_entries"] / g["entries"] >= (0.9 if transpose else 0.85)
