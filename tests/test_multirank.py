@@ -4,8 +4,6 @@ rank and its work the sum over ranks."""
 import os
 import sys
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
