@@ -1608,6 +1608,12 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     return d;
 }
 
+// same scaled matrix (structure, values as stored, equality rows)
+static bool same_matrix(const PsData &a, const PsData &b) {
+    return a.n() == b.n() && a.m() == b.m() && a.m_eq == b.m_eq && a.value_bits == b.value_bits &&
+           a.A.rowptr == b.A.rowptr && a.A.colidx == b.A.colidx && a.A.val == b.A.val && a.A_val32 == b.A_val32;
+}
+
 // Period-strided groups of a device-order matrix.  In the entity-major layout
 // consecutive rows are one constraint of one entity in consecutive periods,
 // and the variables they use sit in consecutive device columns.  A group of
@@ -1655,12 +1661,6 @@ static StridedGroups strided_groups(const Csr &M) {
     }
     g.off[ng] = (int32_t)g.col.size();
     return g;
-}
-
-// same scaled matrix (structure, values as stored, equality rows)
-static bool same_matrix(const PsData &a, const PsData &b) {
-    return a.n() == b.n() && a.m() == b.m() && a.m_eq == b.m_eq && a.value_bits == b.value_bits &&
-           a.A.rowptr == b.A.rowptr && a.A.colidx == b.A.colidx && a.A.val == b.A.val && a.A_val32 == b.A_val32;
 }
 
 // natural-order vector -> device order (and back)
