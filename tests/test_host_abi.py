@@ -294,3 +294,18 @@ def test_strided_groups_describe_the_device_matrix_exactly(B, which, transpose):
     assert g["strided_entries"] == int((g["k"][g["k"] >= 0].astype(np.int64) * G).sum())
     if which == "paper":   # the time-expanded structure the layout exposes
         assert g["strided_entries"] / g["entries"] >= (0.9 if transpose else 0.85)
+
+
+@pytest.mark.parametrize("which", ["tiny", "paper"])
+def test_presolve_reuse_equals_a_full_presolve_on_the_host(B, which):
+    base = ucgen.tiny(3) if which == "tiny" else ucgen.paper_scale(0)
+    ps0 = B.uc_presolve(B.uc_build_lp(base))
+    Q = ucgen.served_request(base, 1, 7)
+    full = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(Q)))
+    re = B.uc_presolved_export(B.uc_presolve_reuse(ps0, B.uc_build_lp(Q)))
+    for k in ("rowptr", "colidx", "val", "q", "c", "l", "u", "Dr", "Dc", "col_map", "row_map"):
+        np.testing.assert_array_equal(re[k], full[k], err_msg=k)
+    for k in ("eta", "omega0", "q_inf", "c_inf", "obj_const"):
+        assert re[k] == full[k], k
+    with pytest.raises(B.UCError, match="matrix differs"):
+        B.uc_presolve_reuse(ps0, B.uc_build_lp(ucgen.tiny(4) if which == "tiny" else ucgen.tiny(0)))
