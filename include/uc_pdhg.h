@@ -206,9 +206,13 @@ int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **
 int uc_presolved_dims(const uc_presolved *ps, int *n, int *m, int *m_eq, int64_t *nnz);
 /* Copy out the scaled reduced LP and its scaling: rowptr [m+1], colidx [nnz],
  * val [nnz] (FP64 scaled values), q, Dr [m], c, l, u, Dc [n], col_map [n] and
- * row_map [m] (raw indices), scalars [6] = {eta, omega0, ||A_s||_2, objective
- * constant, ||q||_inf, ||c||_inf} (the last two unscaled).  Any pointer may be
- * NULL to skip that array. */
+ * row_map [m] (raw indices), scalars [7] = {eta, omega0, power estimate of
+ * ||A_s||_2, objective constant, ||q||_inf, ||c||_inf (both unscaled), the
+ * bound eta is taken from}.  eta = 0.998 / bound, bound = max(estimate, U) with U
+ * a certified upper bound on ||A_s||_2: 1 after the Pock-Chambolle pass (Schur
+ * test), else sqrt(max row * max column absolute sum); the estimate alone is a
+ * lower bound and could break PDHG's step condition tau sigma ||A||^2 < 1.  Any
+ * pointer may be NULL to skip that array. */
 int uc_presolved_export(const uc_presolved *ps, int32_t *rowptr, int32_t *colidx, double *val,
                         double *q, double *c, double *l, double *u, double *Dr, double *Dc,
                         int32_t *col_map, int32_t *row_map, double *scalars);

@@ -25,9 +25,16 @@ with alpha = 1 (divide by sqrt of row / column absolute sums).  With the
 accumulated factors D_r, D_c:  A_s = D_r A D_c,  c_s = D_c c,  q_s = D_r q,
 l_s = l / D_c,  u_s = u / D_c.
 
-Step size: eta = 0.998 / ||A_s||_2 with ||A_s||_2^2 from power iteration on
-A_s^T A_s started at 1/sqrt(n), stopped when the estimate changes by at most
-1e-10 relative or after 500 products.  Initial primal weight
+||A_s||_2 estimate: power iteration on A_s^T A_s started at 1/sqrt(n), stopped
+when the estimate changes by at most 1e-10 relative or after 500 products.
+
+Step size: eta = 0.998 / max(U, estimate), U a certified upper bound on
+||A_s||_2.  PDHG converges for tau sigma ||A||^2 < 1, and a power estimate
+approaches ||A_s||_2 from below, so the estimate alone can overshoot the step.
+After the Pock-Chambolle pass (alpha = 1) the Schur test, with weights the
+square roots of the row and column absolute sums the pass divided by, gives
+||A_s||_2 <= 1, so U = 1; without that pass U = sqrt(||A_s||_1 ||A_s||_inf)
+(the Schur test with unit weights).  Initial primal weight
 omega0 = ||c_s|| / ||q_s|| when both exceed 1e-10, else 1.
 """
 from __future__ import annotations
@@ -212,7 +219,8 @@ class Scaled:
     Dc: np.ndarray
     eta: float
     omega0: float
-    norm_A: float
+    norm_A: float             # power-iteration estimate of ||A_s||_2
+    norm_bound: float         # max(U, norm_A): the step is ETA_FACTOR / norm_bound
     q_inf_unscaled: float
     c_inf_unscaled: float
 
@@ -272,6 +280,18 @@ def power_norm(A: sp.csr_matrix, tol: float = POWER_TOL, max_iter: int = POWER_M
     return float(np.sqrt(lam))
 
 
+def norm_upper_bound(A: sp.csr_matrix, pock_chambolle: bool) -> float:
+    """Certified upper bound U on ||A||_2 of the scaled matrix (see the module
+    docstring): 1 after a Pock-Chambolle pass with alpha = 1, else
+    sqrt(max column absolute sum * max row absolute sum)."""
+    if pock_chambolle:
+        return 1.0
+    absA = abs(A)
+    r = float(np.max(np.asarray(absA.sum(axis=1)).ravel(), initial=0.0))
+    c = float(np.max(np.asarray(absA.sum(axis=0)).ravel(), initial=0.0))
+    return float(np.sqrt(r * c))
+
+
 def scale(lp: LP, ruiz_iters: int = RUIZ_ITERS, pock_chambolle: bool = True) -> Scaled:
     A = lp.A.tocsr().astype(np.float64)
     Dr = np.ones(lp.m)
@@ -290,11 +310,12 @@ def scale(lp: LP, ruiz_iters: int = RUIZ_ITERS, pock_chambolle: bool = True) -> 
         l = lp.l / Dc
         u = lp.u / Dc
     nrm = power_norm(A)
-    eta = ETA_FACTOR / nrm if nrm > 0 else 1.0
+    bound = max(norm_upper_bound(A, pock_chambolle), nrm)
+    eta = ETA_FACTOR / bound if bound > 0 else 1.0
     cn = float(np.linalg.norm(c))
     qn = float(np.linalg.norm(q))
     omega0 = cn / qn if (cn > 1e-10 and qn > 1e-10) else 1.0
     return Scaled(A=A, q=q, c=c, l=l, u=u, m_eq=lp.m_eq, Dr=Dr, Dc=Dc, eta=eta,
-                  omega0=omega0, norm_A=nrm,
+                  omega0=omega0, norm_A=nrm, norm_bound=bound,
                   q_inf_unscaled=float(np.max(np.abs(lp.q), initial=0.0)),
                   c_inf_unscaled=float(np.max(np.abs(lp.c), initial=0.0)))

@@ -247,7 +247,7 @@ def uc_presolved_export(ps) -> dict:
     d = dict(rowptr=np.zeros(m + 1, np.int32), colidx=np.zeros(nnz, np.int32), val=np.zeros(nnz),
              q=np.zeros(m), c=np.zeros(n), l=np.zeros(n), u=np.zeros(n), Dr=np.zeros(m),
              Dc=np.zeros(n), col_map=np.zeros(n, np.int32), row_map=np.zeros(m, np.int32),
-             scalars=np.zeros(6))
+             scalars=np.zeros(7))
     _check(lib.uc_presolved_export(
         ps.ptr, _ptr(d["rowptr"], C.c_int32), _ptr(d["colidx"], C.c_int32), _ptr(d["val"], C.c_double),
         _ptr(d["q"], C.c_double), _ptr(d["c"], C.c_double), _ptr(d["l"], C.c_double),
@@ -256,7 +256,7 @@ def uc_presolved_export(ps) -> dict:
         "uc_presolved_export")
     s = d.pop("scalars")
     d.update(n=n, m=m, m_eq=m_eq, eta=s[0], omega0=s[1], norm_A=s[2], obj_const=s[3],
-             q_inf=s[4], c_inf=s[5])
+             q_inf=s[4], c_inf=s[5], norm_bound=s[6])
     return d
 
 

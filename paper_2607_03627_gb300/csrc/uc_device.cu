@@ -4,7 +4,7 @@
 // The paper's GPU arm solves the LP relaxation with PDHG (Sec. II-C, Alg. 1
 // "Solver 1"; Sec. III-C), with an iteration limit of 100,000 and a
 // convergence tolerance of 1e-4 (Sec. II-D).  The method is the PDLP scheme
-// with a constant step (eta = 0.998 / ||A_s||_2, tau = eta / omega,
+// with a constant step (eta = 0.998 / U, U >= ||A_s||_2 a certified bound, tau = eta / omega,
 // sigma = eta * omega):
 //
 //   x+ = clip(x - tau (c - A^T y), l, u)            k_primal  (A^T row = column of A)
@@ -1579,7 +1579,7 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     d->raw = p.raw;
     d->m_eq = p.m_eq;
     d->value_bits = p.value_bits;
-    d->eta = p.eta; d->omega0 = p.omega0; d->norm_A = p.norm_A; d->obj_const = p.obj_const;
+    d->eta = p.eta; d->omega0 = p.omega0; d->norm_A = p.norm_A; d->norm_bound = p.norm_bound; d->obj_const = p.obj_const;
     d->q_inf = p.q_inf; d->c_inf = p.c_inf;
     auto permute_csr = [](const Csr &A, const std::vector<float> &v32, const std::vector<int32_t> &order,
                           const std::vector<int32_t> &inv_cols, Csr &out, std::vector<float> &o32) {

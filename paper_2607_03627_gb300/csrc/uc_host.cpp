@@ -503,6 +503,28 @@ static void scale_lp(PsData &ps, const uc_presolve_opts &o, int threads) {
     }
 }
 
+// Certified upper bound on ||A_s||_2.  After a Pock-Chambolle pass with
+// alpha = 1 (row i divided by sqrt(r_i), column j by sqrt(c_j), the absolute
+// row and column sums before the pass), the Schur test with weights sqrt(r_i)
+// and sqrt(c_j) gives ||A_s||_2 <= 1.  Without that pass: the Schur test with
+// unit weights, sqrt(max row absolute sum * max column absolute sum).
+static double norm_upper_bound(const Csr &A, bool pock_chambolle) {
+    if (pock_chambolle) return 1.0;
+    std::vector<double> cs((size_t)A.cols, 0.0);
+    double rmax = 0.0;
+    for (int i = 0; i < A.rows; i++) {
+        double r = 0.0;
+        for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+            r += std::fabs(A.val[k]);
+            cs[A.colidx[k]] += std::fabs(A.val[k]);
+        }
+        rmax = std::max(rmax, r);
+    }
+    double cmax = 0.0;
+    for (double v : cs) cmax = std::max(cmax, v);
+    return std::sqrt(rmax * cmax);
+}
+
 // ||A||_2 by power iteration on A^T A from the unit vector 1/sqrt(n).  Every
 // step runs on one pool of workers; the sum of squares adds fixed 16384-element
 // chunk partials in order, so the result does not depend on the thread count.
@@ -680,7 +702,10 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
         } else {
             ps->norm_A = power_norm(ps->A, ps->AT, o.power_max_iter, o.power_tol, threads);
         }
-        ps->eta = ps->norm_A > 0 ? 0.998 / ps->norm_A : 1.0;
+        // the step needs tau sigma ||A_s||^2 < 1 and the power estimate is a lower
+        // bound, so the step takes the larger of it and a certified upper bound
+        ps->norm_bound = std::max(norm_upper_bound(ps->A, o.pock_chambolle != 0), ps->norm_A);
+        ps->eta = ps->norm_bound > 0 ? 0.998 / ps->norm_bound : 1.0;
         double cn = std::sqrt(sumsq(ps->c, threads)), qn = std::sqrt(sumsq(ps->q, threads));
         ps->omega0 = (cn > 1e-10 && qn > 1e-10) ? cn / qn : 1.0;
         ps->value_bits = o.value_bits;
@@ -735,6 +760,7 @@ int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **
             ps->u[j] /= ps->Dc[j];
         }
         ps->norm_A = b.norm_A;
+        ps->norm_bound = b.norm_bound;
         ps->eta = b.eta;
         // same fixed-chunk sums as uc_presolve, so omega0 is bit-identical to a full presolve
         const double cn = std::sqrt(sumsq(ps->c, 1)), qn = std::sqrt(sumsq(ps->q, 1));
@@ -775,7 +801,7 @@ int uc_presolved_export(const uc_presolved *h, int32_t *rowptr, int32_t *colidx,
     if (row_map) std::memcpy(row_map, p.row_map.data(), p.row_map.size() * 4);
     if (scalars) {
         scalars[0] = p.eta; scalars[1] = p.omega0; scalars[2] = p.norm_A;
-        scalars[3] = p.obj_const; scalars[4] = p.q_inf; scalars[5] = p.c_inf;
+        scalars[3] = p.obj_const; scalars[4] = p.q_inf; scalars[5] = p.c_inf; scalars[6] = p.norm_bound;
     }
     return UC_OK;
 }

@@ -61,6 +61,7 @@ struct PsData {
     std::vector<RemovedRow> removed;
     std::vector<double> raw_reduced_val;   // reduced matrix values before scaling
     double eta = 1.0, omega0 = 1.0, norm_A = 0.0, obj_const = 0.0;
+    double norm_bound = 0.0;               // max(certified upper bound, norm_A); eta = 0.998 / it
     double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
     int value_bits = 64;
     int n() const { return A.cols; }

@@ -80,6 +80,25 @@ def test_presolve_and_scaling_match_oracle(B, P):
     assert d["q_inf"] == S.q_inf_unscaled and d["c_inf"] == S.c_inf_unscaled
 
 
+@pytest.mark.parametrize("pc", [1, 0], ids=["pock_chambolle", "ruiz_only"])
+def test_step_comes_from_a_certified_bound(B, pc):
+    # eta = 0.998 / max(U, power estimate), U an upper bound on ||A_s||_2, so that
+    # eta ||A_s||_2 < 1 (checked with a dense SVD); the oracle takes the same bound
+    P = ucgen.make_problem(7, B=37, L=53, G=11, T=5, lo=0.5, hi=0.9, noise=0.05, zero_pmin_frac=0.2)
+    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P), pock_chambolle=pc))
+    S = ops.scale(ops.presolve(olp.build_lp(P)).lp, pock_chambolle=bool(pc))
+    A = np.zeros((d["m"], d["n"]))
+    for i in range(d["m"]):
+        A[i, d["colidx"][d["rowptr"][i]:d["rowptr"][i + 1]]] = d["val"][d["rowptr"][i]:d["rowptr"][i + 1]]
+    smax = float(np.linalg.svd(A, compute_uv=False)[0])
+    assert d["norm_A"] <= smax * (1 + 1e-12) <= d["norm_bound"] * (1 + 1e-12)
+    assert d["eta"] == 0.998 / d["norm_bound"] and d["eta"] * smax < 1.0
+    assert d["norm_bound"] == pytest.approx(S.norm_bound, rel=1e-13)
+    assert d["eta"] == pytest.approx(S.eta, rel=1e-13)
+    if pc:
+        assert d["norm_bound"] == 1.0
+
+
 def test_builder_rejects_bad_data(B):
     P = ucgen.micro(0, B=3, L=3, G=2, T=2)
     bad = P.copy(); bad.line_to = bad.line_from.copy()

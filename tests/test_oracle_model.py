@@ -166,6 +166,30 @@ def test_power_norm():
     assert true <= 1.0 + 1e-12                 # Pock-Chambolle alpha=1 bounds ||A_s|| by 1
 
 
+STEP_CASES = [
+    ("tiny", lambda: ucgen.tiny(0)),
+    ("ragged37", lambda: ucgen.make_problem(7, B=37, L=53, G=11, T=5, lo=0.5, hi=0.9, noise=0.05,
+                                            zero_pmin_frac=0.2)),
+    ("micro", lambda: ucgen.micro(2, B=5, L=6, G=3, T=3)),
+]
+
+
+@pytest.mark.parametrize("pc", [True, False], ids=["pock_chambolle", "ruiz_only"])
+@pytest.mark.parametrize("name,make", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_step_meets_the_pdhg_step_condition(name, make, pc):
+    # PDHG converges for tau sigma ||A||^2 = eta^2 ||A_s||^2 < 1: checked with the
+    # largest singular value of the dense scaled matrix (LAPACK SVD), which the
+    # power estimate approaches from below and the certified bound from above
+    S = ops.scale(ops.presolve(olp.build_lp(make())).lp, pock_chambolle=pc)
+    smax = float(np.linalg.svd(S.A.toarray(), compute_uv=False)[0])
+    assert S.norm_A <= smax * (1 + 1e-12)
+    assert S.norm_bound >= smax * (1 - 1e-14)
+    assert S.eta * smax < 1.0
+    assert S.eta * smax >= 0.998 * (smax / S.norm_bound)
+    if pc:
+        assert S.norm_bound == 1.0 and smax <= 1.0 + 1e-13
+
+
 def test_commitment_enumeration_bounds_lp():
     P = ucgen.micro(2, B=2, L=1, G=3, T=3)     # 2^9 commitments
     raw = olp.build_lp(P)
