@@ -327,11 +327,13 @@ typedef struct {
 } uc_device_lp;
 
 /* Relative KKT of a scaled presolved point (x [n], y [m], device memory) --
- * the same quantities the solver's own evaluation reports -- computed
- * WITHOUT ANY DEVICE ALLOCATION.  The paper has no counterpart: this entry
- * exists for callers that cannot allocate device memory, e.g. code being
- * recorded into a CUDA graph under global stream capture, or a process whose
- * device memory is all reserved ahead of time by its own pool allocator.
+ * the same quantities the solver's own evaluation reports, NaN included --
+ * computed WITHOUT ANY DEVICE ALLOCATION.  The paper has no counterpart: this
+ * entry exists for callers that cannot allocate device memory, e.g. a process
+ * whose device memory is all reserved ahead of time by its own pool allocator
+ * (a fresh driver allocation would fail or fragment that pool), or a
+ * latency-bound loop that must not enter the allocator (cudaMalloc and
+ * cudaFree may synchronise the device).
  * Results go to `out`, 8 doubles of caller-owned device memory:
  * {rel_primal, rel_dual, rel_gap, KKT_omega (with the given omega > 0),
  *  primal objective, dual objective (both of the scaled presolved LP, no
@@ -344,10 +346,12 @@ typedef struct {
  * are rejected with UC_EINVAL.  All calls share that array, so calls whose
  * device work overlaps (several streams or host threads at once) race and
  * must be serialised by the caller; no part of it needs to start at zero.
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and loads the entry's two kernels
- * (cudaFuncGetAttributes; under CUDA's lazy module loading the driver may take
- * device memory for their code then) with that device current; make that
+ * Set-up: every call looks up the array's device address for the current
+ * device (cudaGetSymbolAddress, which allocates nothing), so a context that was
+ * reset and re-created never gets a stale address, and makes sure the entry's
+ * two kernels are loaded (cudaFuncGetAttributes).  Under CUDA's lazy module
+ * loading the driver may take device memory for their code on the first call
+ * on each device (and on the first call after a cudaDeviceReset); make that
  * first call before starting any stream capture.  No cudaMalloc, cudaFree or
  * other allocating call is made. */
 int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, double omega, double *out,

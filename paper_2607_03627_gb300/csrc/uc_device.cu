@@ -31,7 +31,6 @@
 #include <cstring>
 #include <functional>
 #include <limits>
-#include <mutex>
 #include <queue>
 #include <vector>
 
@@ -2744,12 +2743,12 @@ static int max_replays(const uc_session &X) { return X.o.max_iter / X.o.n_eval +
 // ---------------------------------------------------------------------------
 // KKT evaluation that allocates nothing (uc_kkt_noalloc)
 //
-// Some callers may not allocate device memory at all: code recorded into a
-// CUDA graph under global stream capture (where cudaMalloc is illegal), and
-// processes whose device memory is fully reserved up front by another pool
-// allocator, where a fresh driver allocation would fail or fragment the pool.
-// For them this variant of the evaluation keeps its per-CTA partial sums in
-// the file-scope array below instead of session memory.  Every GPU that loads
+// Some callers may not allocate device memory at all: processes whose device
+// memory is reserved up front by their own pool allocator (a fresh driver
+// allocation would then fail or fragment the pool), and latency-bound loops
+// that must not enter the allocator, since cudaMalloc and cudaFree may
+// synchronise the device.  For them this variant of the evaluation keeps its
+// per-CTA partial sums in the file-scope array below instead of session memory.  Every GPU that loads
 // this library holds the array (kNoAllocMaxBlocks * kNoAllocSlots doubles,
 // 512 KiB) until the process exits.
 // ---------------------------------------------------------------------------
@@ -2774,9 +2773,9 @@ __global__ void __launch_bounds__(kThreads) k_kkt_partials_noalloc(uc_device_lp 
             for (int k = lp.A_rowptr[i]; k < lp.A_rowptr[i + 1]; k++) ax += lp.A_val[k] * x[lp.A_colidx[k]];
             const double qi = lp.q[i];
             double r = ax - qi;
-            if (i >= lp.m_eq) r = fmin(r, 0.0);
+            if (i >= lp.m_eq && r > 0.0) r = 0.0;   // min(r, 0) that keeps a NaN
             acc[RP2] += r * r;
-            acc[RPU] = fmax(acc[RPU], fabs(r) / lp.Dr[i]);
+            acc[RPU] = nnmax(acc[RPU], fabs(r) / lp.Dr[i]);   // a NaN wins, as in k_eval
             acc[QY] += qi * y[i];
         }
     } else {
@@ -2793,7 +2792,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_partials_noalloc(uc_device_lp 
             if (lf) bnd += lj * fmax(lpj, 0.0);
             if (uf) bnd += uj * fmin(lpj, 0.0);
             acc[RD2] += rd * rd;
-            acc[RDU] = fmax(acc[RDU], fabs(rd) / lp.Dc[j]);
+            acc[RDU] = nnmax(acc[RDU], fabs(rd) / lp.Dc[j]);
             acc[CX] += cj * x[j];
             acc[BND] += bnd;
         }
@@ -2817,7 +2816,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_finish_noalloc(int nblocks, co
 #pragma unroll
         for (int s = 0; s < kNoAllocSlots; s++) {
             const double v = scratch[(size_t)blk * kNoAllocSlots + s];
-            acc[s] = (s == RPU || s == RDU) ? fmax(acc[s], v) : acc[s] + v;
+            acc[s] = (s == RPU || s == RDU) ? nnmax(acc[s], v) : acc[s] + v;
         }
     }
 #pragma unroll
@@ -2827,7 +2826,7 @@ __global__ void __launch_bounds__(kThreads) k_kkt_finish_noalloc(int nblocks, co
         if (threadIdx.x < h)
             for (int s = 0; s < kNoAllocSlots; s++) {
                 const double a = red[threadIdx.x][s], c = red[threadIdx.x + h][s];
-                red[threadIdx.x][s] = (s == RPU || s == RDU) ? fmax(a, c) : a + c;
+                red[threadIdx.x][s] = (s == RPU || s == RDU) ? nnmax(a, c) : a + c;
             }
         __syncthreads();
     }
@@ -2844,34 +2843,29 @@ __global__ void __launch_bounds__(kThreads) k_kkt_finish_noalloc(int nblocks, co
     out[7] = 0.0;
 }
 
-// per-device address of g_kkt_scratch, looked up once per device
-static std::mutex g_kkt_scratch_mu;
-static void *g_kkt_scratch_ptr[128];
-
+// Device address of g_kkt_scratch for the current device.  Looked up on every
+// call (cudaGetSymbolAddress allocates nothing), so a context that was reset
+// and re-created, where the array may sit elsewhere, never gets a stale
+// address.  The entry's kernels are loaded here too: under lazy module loading
+// the driver may take device memory for their code on first use, and this
+// moves that to the first call on a device.
 static int kkt_scratch_address(double **out) {
     int dev = 0;
     UC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) { set_error("device ordinal %d unsupported", dev); return UC_EINVAL; }
-    std::lock_guard<std::mutex> lock(g_kkt_scratch_mu);
-    if (!g_kkt_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(scratch) failed on device %d: %s", dev, cudaGetErrorString(e));
-            return UC_ECUDA;
-        }
-        // load the entry's kernels now: under lazy module loading the driver
-        // may take device memory for their code on first use
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, k_kkt_partials_noalloc);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_kkt_finish_noalloc);
-        if (e != cudaSuccess) {
-            set_error("loading the KKT kernels failed on device %d: %s", dev, cudaGetErrorString(e));
-            return UC_ECUDA;
-        }
-        g_kkt_scratch_ptr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_kkt_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(scratch) failed on device %d: %s", dev, cudaGetErrorString(e));
+        return UC_ECUDA;
     }
-    *out = (double *)g_kkt_scratch_ptr[dev];
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_kkt_partials_noalloc);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_kkt_finish_noalloc);
+    if (e != cudaSuccess) {
+        set_error("loading the KKT kernels failed on device %d: %s", dev, cudaGetErrorString(e));
+        return UC_ECUDA;
+    }
+    *out = (double *)p;
     return UC_OK;
 }
 
@@ -3155,14 +3149,15 @@ int uc_kkt_noalloc(const uc_device_lp *lp, const double *x, const double *y, dou
         set_error("uc_kkt_noalloc: need n, m >= 0, 0 <= m_eq <= m and omega > 0");
         return UC_EINVAL;
     }
-    const int nbr = (lp->m + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
-    const int nbc = (lp->n + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
-    const int nblocks = nbr + nbc;
-    if (nblocks > dev::kNoAllocMaxBlocks) {
-        set_error("uc_kkt_noalloc: LP too large for the fixed scratch: ceil(m/1024) + ceil(n/1024) = %d > %d "
-                  "(n + m up to about 8.4 million)", nblocks, dev::kNoAllocMaxBlocks);
+    // block counts in 64 bits: n and m near INT_MAX must be refused, not wrap
+    const int64_t nbr64 = ((int64_t)lp->m + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
+    const int64_t nbc64 = ((int64_t)lp->n + dev::kNoAllocRows - 1) / dev::kNoAllocRows;
+    if (nbr64 + nbc64 > dev::kNoAllocMaxBlocks) {
+        set_error("uc_kkt_noalloc: LP too large for the fixed scratch: ceil(m/1024) + ceil(n/1024) = %lld > %d "
+                  "(n + m up to about 8.4 million)", (long long)(nbr64 + nbc64), dev::kNoAllocMaxBlocks);
         return UC_EINVAL;
     }
+    const int nbr = (int)nbr64, nblocks = (int)(nbr64 + nbc64);
     double *scratch = nullptr;
     int rc = dev::kkt_scratch_address(&scratch);
     if (rc) return rc;
