@@ -473,9 +473,10 @@ def run_batch(args):
     ps32 = presolve_all(probs, value_bits=32)
     presolve_s = time.perf_counter() - t0
     tuner = Tuner()
-    solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32)      # warm-up + tuning
+    kw = dict(restart_metric=args.restart_metric)
+    solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)      # warm-up + tuning
     with ClockSampler(0) as clk:
-        res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32)
+        res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)
     st32 = [B.uc_get_stats(r) for r, _ in res32]
     line = {"metric": METRIC, "value": args.batch / (info["solve_ms"] / 1e3), "unit": "UC LP/s",
             "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": info["solve_ms"], "higher_is_better": True,
@@ -494,7 +495,7 @@ def run_batch(args):
         errs = []
         seq_iters = []
         for p, (r32, _), s32 in zip(ps64, res32, st32):
-            sess = B.Session([p], tol=TOL, max_iter=args.max_iter)
+            sess = B.Session([p], tol=TOL, max_iter=args.max_iter, **kw)
             sess.reset(-1); sess.run()                      # warm-up
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(); sess.reset(-1); sess.run(); e1.record(); torch.cuda.synchronize()

@@ -110,11 +110,17 @@ typedef struct {
     uc_alloc_fn alloc;           /* nullable device allocator */
     uc_free_fn free;
     void *alloc_ctx;
-    int spmv_kernel;             /* iteration kernels: 0 (default) or 1, one thread per row; 2 staged:
-                                    persistent CTAs that copy each 128-row chunk's matrix rows and
-                                    vectors into shared memory ahead of use (Halpern only, rows of at
-                                    most 640 entries, else UC_EINVAL).  All variants give identical
-                                    iterates. */
+    int spmv_kernel;             /* iteration kernels, one thread per row: 0 (default) rows in
+                                    period-strided 16-row groups (in the device layout, 16 consecutive
+                                    rows whose entry q is (col_q + s, val_q) in row s of the group, as
+                                    for one constraint of one entity in consecutive periods) read the
+                                    group's k <= 16 (column, value) slots instead of row pointers and
+                                    CSR entries, the other rows their CSR row; 1: every row from CSR;
+                                    2 staged: persistent CTAs that copy each 128-row chunk's matrix
+                                    rows and vectors into shared memory ahead of use (Halpern only,
+                                    rows of at most 640 entries, else UC_EINVAL).  The strided slots
+                                    are not used by shared-matrix (lanes) sessions.  All variants give
+                                    identical iterates. */
     int cta_rows;                /* threads per CTA of the iteration kernels: 0 (default 128), 128,
                                     256 or 512; results do not depend on it (tuning knob) */
     const int *rows_per_thread;  /* nullable [k]: rows each thread of LP i's CTAs handles, 1, 2 or

@@ -97,6 +97,10 @@ struct Bufs {
     // matrices (block-diagonal when batched, global indices)
     const int *A_rp, *A_ci, *AT_rp, *AT_ci;
     const void *A_v, *AT_v;
+    // period-strided 16-row groups: entries per row of group g (or -1) and the
+    // group's slot records at 16 g + q (see k_primal)
+    const signed char *A_sk, *AT_sk;
+    const void *A_sl, *AT_sl;
     // constant vectors
     const double *c, *l, *u, *q, *Dr, *Dc;
     const double *inv_Dr, *inv_Dc;             // 1 / D_r, 1 / D_c (evaluation only)
@@ -154,6 +158,15 @@ __device__ __forceinline__ double widen(float f) {
     return __longlong_as_double((long long)bits);
 }
 
+// -v by flipping the sign bit on the integer pipe (exact).  The accumulators of
+// the iteration kernels start at -c / -q; written as a plain negation the
+// compiler spends an FP64 add on it, one FP64 instruction per row.
+__device__ __forceinline__ double neg_bits(double v) {
+    int hi = __double2hiint(v);
+    asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
+    return __hiloint2double(hi, __double2loint(v));
+}
+
 // max of two non-negative doubles through their bit patterns
 __device__ __forceinline__ double nnmax(double a, double b) {
     return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
@@ -195,6 +208,55 @@ __device__ __forceinline__ Seg row_slice(const Seg *__restrict__ segs, const Uni
     return Seg{0, begin, min(begin + BS * u.rpt, u.n), u.aux, u.rpt};
 }
 
+// Period-strided 16-row groups (SD = true).  In the entity-major device layout
+// consecutive rows are one constraint (or variable) of one entity in
+// consecutive periods.  A group of 16 consecutive rows, g = row / 16, is
+// strided when all its rows have k entries and entry q of row s is
+// (col_q + s, val_q) for one list of k (col_q, val_q) pairs.  Such a group is
+// stored as k slot records at the fixed positions 16 g + q (k <= 16) and
+// sk[g] = k; other groups have sk[g] = -1 and keep the CSR path.  A strided
+// row thus needs no row pointers and its k slots are read once for 16 rows
+// (broadcast to the half-warp, 16x less matrix traffic): its loads are the
+// slots and sk[g], all independent of one another, then the gathers of 16
+// consecutive elements.  Entry q of a strided row is entry q of its CSR row,
+// so the dot product adds the same terms in the same order: iterates are
+// identical to the CSR path's, bit for bit.
+template <typename VT> struct SlotT;
+template <> struct __align__(16) SlotT<double> { int col, pad; double val; };
+template <> struct __align__(8) SlotT<float> { int col; float val; };
+
+__device__ __forceinline__ void ld_slot(const SlotT<double> *p, int &col, double &v) {
+    const int4 r = __ldg(reinterpret_cast<const int4 *>(p));
+    col = r.x;
+    v = __hiloint2double(r.w, r.z);
+}
+__device__ __forceinline__ void ld_slot(const SlotT<float> *p, int &col, double &v) {
+    const int2 r = __ldg(reinterpret_cast<const int2 *>(p));
+    col = r.x;
+    v = widen(__int_as_float(r.y));
+}
+
+// The first kPre entries of row r (CSR entries k0 .. k1 - 1, or the group's
+// slots): column, value and the row's entry count.  st: the row is in a strided
+// group (its slots and sk were loaded before, see the kernels).
+template <typename VT, bool SD>
+__device__ __forceinline__ int row_head(const int *__restrict__ ci_arr, const VT *__restrict__ v, int k0, int k1,
+                                        bool st, int kk, int r, const int (&scol)[kPre], const double (&sval)[kPre],
+                                        int (&ci)[kPre], double (&av)[kPre]) {
+    if (SD && st) {
+#pragma unroll
+        for (int q = 0; q < kPre; q++) { ci[q] = scol[q] + (r & 15); av[q] = sval[q]; }
+        return kk;
+    }
+#pragma unroll
+    for (int q = 0; q < kPre; q++) {
+        ci[q] = 0;
+        av[q] = 0.0;
+        if (k0 + q < k1) { ci[q] = ld_stream(ci_arr + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
+    }
+    return k1 - k0;
+}
+
 // ALGO = ALG_AVERAGE: x+ = clip(x - tau (c - A^T y), l, u), running sum of x+.
 // ALGO = ALG_HALPERN: x_hat = that map, x-bar = 2 x_hat - x (gathered by the
 // dual kernel), x <- w x-bar + (1 - w) x0 with w = (j+1)/(j+2); x_hat kept at
@@ -205,13 +267,14 @@ __device__ __forceinline__ Seg row_slice(const Seg *__restrict__ segs, const Uni
 // memory latency, so more resident rows outweigh the primal kernel's spills.
 // The loads of a row are issued before the LP's state is read (the addresses
 // are valid either way), so that read overlaps them instead of heading the
-// chain of dependent loads.
-template <typename VT, int ALGO, int BS>
+// chain of dependent loads.  SD: strided groups read their slots (see above).
+template <typename VT, int ALGO, int BS, bool SD>
 __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src,
                                                            Uniform u) {
     const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+    const SlotT<VT> *__restrict__ slots = static_cast<const SlotT<VT> *>(b.AT_sl);
     const double *__restrict__ y = b.y[src];
     bool waited = false, keep = false;
     for (int t = 0; t < sg.rpt; t++) {
@@ -219,19 +282,22 @@ __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict_
         if (j >= sg.end) break;
         // independent of the dual kernel that precedes this one
         const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
+        int kk = -1, scol[kPre];
+        double sval[kPre];
+        if (SD) {   // the group's k and first slots, whatever path the row takes
+            kk = __ldg(b.AT_sk + (j >> 4));
+#pragma unroll
+            for (int q = 0; q < kPre; q++) ld_slot(slots + (j & ~15) + q, scol[q], sval[q]);
+        }
         const double xin = ld_stream(b.x[src] + j);
         const long long lk = ld_stream(b.lkey + j), uk = ld_stream(b.ukey + j);
         const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : ld_stream(b.xa + j);
+        const bool st = SD && kk >= 0;
         int ci[kPre];
         double av[kPre];
-#pragma unroll
-        for (int q = 0; q < kPre; q++) {
-            ci[q] = 0;
-            av[q] = 0.0;
-            if (k0 + q < k1) { ci[q] = ld_stream(b.AT_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
-        }
+        const int cnt = row_head<VT, SD>(b.AT_ci, v, k0, k1, st, kk, j, scol, sval, ci, av);
         // the accumulator starts at -c, so it ends at A^T y - c
-        double acc = -ld_stream(b.c + j);
+        double acc = neg_bits(ld_stream(b.c + j));
         if (t == 0) {   // the LP's state, read while the row's loads are in flight
             const int k = S->k_base + it;
             if (S->status != RUNNING || k >= S->max_iter) return;
@@ -242,10 +308,19 @@ __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict_
         const unsigned lanes = __activemask();
 #pragma unroll
         for (int q = 0; q < kPre; q++) {
-            if (!__any_sync(lanes, k0 + q < k1)) break;
-            if (k0 + q < k1) acc = fma(av[q], y[ci[q]], acc);
+            if (!__any_sync(lanes, q < cnt)) break;
+            if (q < cnt) acc = fma(av[q], y[ci[q]], acc);
         }
-        for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), y[ld_stream(b.AT_ci + kk)], acc);
+        if (SD && st) {
+            for (int q = kPre; q < cnt; q++) {
+                int c;
+                double a;
+                ld_slot(slots + (j & ~15) + q, c, a);
+                acc = fma(a, y[c + (j & 15)], acc);
+            }
+        } else {
+            for (int e = k0 + kPre; e < k1; e++) acc = fma(widen(ld_stream(v + e)), y[ld_stream(b.AT_ci + e)], acc);
+        }
         const double xv = clip_keys(fma(S->tau, acc, xin), lk, uk);
         if (ALGO == ALG_AVERAGE) {
             b.x[src ^ 1][j] = xv;
@@ -265,57 +340,79 @@ __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict_
 // ALGO = ALG_AVERAGE: y+ = proj(y + sigma (q - A (2 x+ - x))), running sum.
 // ALGO = ALG_HALPERN: y_hat = proj(y + sigma (q - A x-bar)),
 // y <- w (2 y_hat - y) + (1 - w) y0; y_hat kept like x_hat.
-template <typename VT, int ALGO, int BS>
+template <typename VT, int ALGO, int BS, bool SD>
 __global__ void __launch_bounds__(BS, 1536 / BS) k_dual(const Seg *__restrict__ segs, Bufs b, int it, int src,
                                                          Uniform u) {
     const Seg sg = row_slice<BS>(segs, u);
     const Scalars *S = b.S + sg.inst;
     const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
+    const SlotT<VT> *__restrict__ slots = static_cast<const SlotT<VT> *>(b.A_sl);
     bool waited = false, keep = false;
     for (int t = 0; t < sg.rpt; t++) {
         const int i = sg.begin + t * BS + threadIdx.x;
         if (i >= sg.end) break;
         const int k0 = __ldg(b.A_rp + i), k1 = __ldg(b.A_rp + i + 1);
+        int kk = -1, scol[kPre];
+        double sval[kPre];
+        if (SD) {
+            kk = __ldg(b.A_sk + (i >> 4));
+#pragma unroll
+            for (int q = 0; q < kPre; q++) ld_slot(slots + (i & ~15) + q, scol[q], sval[q]);
+        }
         const double yin = ld_stream(b.y[src] + i);
         const double aux = (ALGO == ALG_AVERAGE) ? b.ysum[i] : ld_stream(b.ya + i);
+        const bool st = SD && kk >= 0;
         int ci[kPre];
         double av[kPre];
-#pragma unroll
-        for (int q = 0; q < kPre; q++) {
-            ci[q] = 0;
-            av[q] = 0.0;
-            if (k0 + q < k1) { ci[q] = ld_stream(b.A_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
-        }
+        const int cnt = row_head<VT, SD>(b.A_ci, v, k0, k1, st, kk, i, scol, sval, ci, av);
         // the accumulator starts at -q, so it ends at A x - q
-        double acc = -ld_stream(b.q + i);
+        double acc = neg_bits(ld_stream(b.q + i));
         if (t == 0) {   // the LP's state, read while the row's loads are in flight
             const int k = S->k_base + it;
             if (S->status != RUNNING || k >= S->max_iter) return;
             keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
         }
         if (!waited) { pdl_wait(); pdl_trigger(); waited = true; }
+        const unsigned lanes = __activemask();
         if (ALGO == ALG_AVERAGE) {
             const double *__restrict__ xn = b.x[src ^ 1];
             const double *__restrict__ xo = b.x[src];
-            const unsigned lanes = __activemask();
 #pragma unroll
             for (int q = 0; q < kPre; q++) {
-                if (!__any_sync(lanes, k0 + q < k1)) break;
-                if (k0 + q < k1) acc = fma(av[q], fma(2.0, xn[ci[q]], -xo[ci[q]]), acc);
+                if (!__any_sync(lanes, q < cnt)) break;
+                if (q < cnt) acc = fma(av[q], fma(2.0, xn[ci[q]], -xo[ci[q]]), acc);
             }
-            for (int kk = k0 + kPre; kk < k1; kk++) {
-                const int j = b.A_ci[kk];
-                acc = fma(widen(v[kk]), fma(2.0, xn[j], -xo[j]), acc);
+            if (SD && st) {
+                for (int q = kPre; q < cnt; q++) {
+                    int c;
+                    double a;
+                    ld_slot(slots + (i & ~15) + q, c, a);
+                    c += i & 15;
+                    acc = fma(a, fma(2.0, xn[c], -xo[c]), acc);
+                }
+            } else {
+                for (int e = k0 + kPre; e < k1; e++) {
+                    const int j = b.A_ci[e];
+                    acc = fma(widen(v[e]), fma(2.0, xn[j], -xo[j]), acc);
+                }
             }
         } else {
             const double *__restrict__ xb = b.xsum;
-            const unsigned lanes = __activemask();
 #pragma unroll
             for (int q = 0; q < kPre; q++) {
-                if (!__any_sync(lanes, k0 + q < k1)) break;
-                if (k0 + q < k1) acc = fma(av[q], xb[ci[q]], acc);
+                if (!__any_sync(lanes, q < cnt)) break;
+                if (q < cnt) acc = fma(av[q], xb[ci[q]], acc);
             }
-            for (int kk = k0 + kPre; kk < k1; kk++) acc = fma(widen(ld_stream(v + kk)), xb[ld_stream(b.A_ci + kk)], acc);
+            if (SD && st) {
+                for (int q = kPre; q < cnt; q++) {
+                    int c;
+                    double a;
+                    ld_slot(slots + (i & ~15) + q, c, a);
+                    acc = fma(a, xb[c + (i & 15)], acc);
+                }
+            } else {
+                for (int e = k0 + kPre; e < k1; e++) acc = fma(widen(ld_stream(v + e)), xb[ld_stream(b.A_ci + e)], acc);
+            }
         }
         double yv = fma(-S->sigma, acc, yin);
         if (i >= sg.aux) yv = nonneg(yv);
@@ -555,7 +652,7 @@ __global__ void __launch_bounds__(kStRows, 8) k_iter_staged(const Chunk *__restr
         const double *vec = reinterpret_cast<const double *>(sb + Ly::kVec0);
         const int k0 = srp[r - w.rpa], k1 = srp[r + 1 - w.rpa];
         // the accumulator starts at -c (-q) and sums the row in entry order
-        double acc = -vec[1 * VS + lr];
+        double acc = neg_bits(vec[1 * VS + lr]);
         const unsigned lanes = __activemask();
         for (int e = k0; __any_sync(lanes, e < k1); e += 4) {
             double gv[4];
@@ -652,7 +749,7 @@ __global__ void __launch_bounds__(BS) k_primal_lanes(const Seg *__restrict__ seg
         if (k0 + q < k1) { ci[q] = ld_stream(b.AT_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
     }
     const double2 cc = ld_stream(reinterpret_cast<const double2 *>(b.c + e));
-    double acc0 = -cc.x, acc1 = -cc.y;   // the accumulators end at A^T y - c
+    double acc0 = neg_bits(cc.x), acc1 = neg_bits(cc.y);   // the accumulators end at A^T y - c
     pdl_wait();
     pdl_trigger();
     const double *__restrict__ y = b.y[src] + 2 * p;
@@ -714,7 +811,7 @@ __global__ void __launch_bounds__(BS) k_dual_lanes(const Seg *__restrict__ segs,
         if (k0 + q < k1) { ci[q] = ld_stream(b.A_ci + k0 + q); av[q] = widen(ld_stream(v + k0 + q)); }
     }
     const double2 qq = ld_stream(reinterpret_cast<const double2 *>(b.q + e));
-    double acc0 = -qq.x, acc1 = -qq.y;   // the accumulators end at A x-bar - q
+    double acc0 = neg_bits(qq.x), acc1 = neg_bits(qq.y);   // the accumulators end at A x-bar - q
     pdl_wait();
     pdl_trigger();
     const double *__restrict__ xb = b.xsum + 2 * p;
@@ -1280,7 +1377,7 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_primal(Bufs b, int n, int it)
     if (j < n) {
         const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
         const double xin = b.x[src][j];
-        double acc = -ld_stream(b.c + j);   // ends at A^T y - c
+        double acc = neg_bits(ld_stream(b.c + j));   // ends at A^T y - c
         for (int k = k0; k < k1; k++) acc = fma(widen(ld_stream(v + k)), y[ld_stream(b.AT_ci + k)], acc);
         if (w != 0.0) b.xsum[j] = fma(w, xin, b.xsum[j]);   // the last accepted step
         const double xv = fmin(fmax(fma(tau, acc, xin), ld_stream(b.l + j)), ld_stream(b.u + j));
@@ -1305,7 +1402,7 @@ __global__ void __launch_bounds__(kAdThreads) k_ad_dual(Bufs b, int m, int m_eq,
     if (i < m) {
         const int k0 = __ldg(b.A_rp + i), k1 = __ldg(b.A_rp + i + 1);
         const double yin = b.y[src][i];
-        double acc = -ld_stream(b.q + i);   // ends at A x-bar - q
+        double acc = neg_bits(ld_stream(b.q + i));   // ends at A x-bar - q
         double adx = 0.0;                   // (A (x' - x))_i
         for (int k = k0; k < k1; k++) {
             const int j = ld_stream(b.A_ci + k);
@@ -1420,6 +1517,8 @@ struct Layout {
     size_t x0, x1, y0, y1, xsum, ysum, xa, ya, xret, yret, part, red, S, status, adp;
     // staged kernels: chunk lists and per-CTA ranges
     size_t chunks_p, chunks_d, ctas_p, ctas_d;
+    // period-strided groups: k per group and slot records (row kernels)
+    size_t A_sk, AT_sk, A_sl, AT_sl;
     // lanes sessions: contiguous staging for one LP's vectors (4 (n + m) doubles:
     // the seven vectors a result may download)
     size_t lane_stage;
@@ -1468,6 +1567,9 @@ struct uc_session {
     // once, vectors interleaved (element j of LP r at j*K + r); K = 1 otherwise
     int K = 1;
     int64_t Mr = 0, Nr = 0;       // rows of A and of A^T as stored
+    // period-strided 16-row groups read from slot records (row kernels, K = 1)
+    bool strided = false;
+    int64_t strided_rows_A = 0, strided_rows_AT = 0;
     // staged iteration kernels
     bool staged = false;
     int stages = 4;
@@ -1662,6 +1764,45 @@ static StridedGroups strided_groups(const Csr &M) {
     return g;
 }
 
+// Slot records of the period-strided groups of a stored CSR matrix (global
+// indices, values as stored): sk[g] = k and the records of group g at
+// 16 g + q when the group is strided with k <= 16 entries per row, else
+// sk[g] = -1.  Values are compared bit for bit.  Record layout as SlotT:
+// int32 column at byte 0, the value at byte 8 (FP64) or 4 (FP32).  The slot
+// area must be zeroed.  Returns the rows in strided groups.
+template <typename VT>
+static int64_t build_slots(const int32_t *rp, const int32_t *ci, const VT *v, int64_t rows, signed char *sk,
+                           char *sl) {
+    const size_t rec = sizeof(VT) == 8 ? 16 : 8, voff = sizeof(VT) == 8 ? 8 : 4;
+    const int64_t ng = (rows + kStrideRows - 1) / kStrideRows;
+    int64_t covered = 0;
+    for (int64_t g = 0; g < ng; g++) {
+        sk[g] = -1;
+        const int64_t r0 = g * kStrideRows;
+        if (r0 + kStrideRows > rows) continue;
+        const int k = rp[r0 + 1] - rp[r0];
+        if (k <= 0 || k > kStrideRows) continue;
+        bool ok = true;
+        for (int s = 1; ok && s < kStrideRows; s++) {
+            const int64_t r = r0 + s;
+            if (rp[r + 1] - rp[r] != k) { ok = false; break; }
+            for (int q = 0; q < k; q++) {
+                const int64_t e0 = rp[r0] + q, e = rp[r] + q;
+                if (ci[e] != ci[e0] + s || std::memcmp(v + e, v + e0, sizeof(VT)) != 0) { ok = false; break; }
+            }
+        }
+        if (!ok) continue;
+        sk[g] = (signed char)k;
+        for (int q = 0; q < k; q++) {
+            char *p = sl + (size_t)(r0 + q) * rec;
+            std::memcpy(p, ci + rp[r0] + q, 4);
+            std::memcpy(p + voff, v + rp[r0] + q, sizeof(VT));
+        }
+        covered += kStrideRows;
+    }
+    return covered;
+}
+
 // natural-order vector -> device order (and back)
 static std::vector<double> to_device(const double *v, const std::vector<int32_t> &order) {
     std::vector<double> o(order.size());
@@ -1817,6 +1958,16 @@ static cudaError_t launch_staged(const uc_session &X, cudaStream_t s, bool pdl, 
                               X.b, it, src, X.stages);
 }
 
+template <typename VT, int ALGO, int BS, bool SD>
+static cudaError_t launch_rows(const uc_session &X, cudaStream_t s, bool pdl, int it, int src, bool primal) {
+    if (primal) {
+        const Uniform u = X.k == 1 ? Uniform{(int)X.Nr, 0, X.rpt[0]} : Uniform{0, 0, 0};
+        return launch_k(k_primal<VT, ALGO, BS, SD>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
+    }
+    const Uniform u = X.k == 1 ? Uniform{(int)X.Mr, X.m_eq[0], X.rpt[0]} : Uniform{0, 0, 0};
+    return launch_k(k_dual<VT, ALGO, BS, SD>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
+}
+
 template <int ALGO, int BS>
 static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool primal) {
     // the first primal kernel of a block follows the evaluation kernels: no overlap there
@@ -1841,15 +1992,10 @@ static void launch_iter(uc_session &X, cudaStream_t s, int it, int src, bool pri
         if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
         return;
     }
-    if (primal) {
-        const Uniform u = X.k == 1 ? Uniform{(int)X.Nr, 0, X.rpt[0]} : Uniform{0, 0, 0};
-        if (X.vb == 32) e = launch_k(k_primal<float, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
-        else e = launch_k(k_primal<double, ALGO, BS>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
-    } else {
-        const Uniform u = X.k == 1 ? Uniform{(int)X.Mr, X.m_eq[0], X.rpt[0]} : Uniform{0, 0, 0};
-        if (X.vb == 32) e = launch_k(k_dual<float, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
-        else e = launch_k(k_dual<double, ALGO, BS>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
-    }
+    if (X.vb == 32) e = X.strided ? launch_rows<float, ALGO, BS, true>(X, s, pdl, it, src, primal)
+                                  : launch_rows<float, ALGO, BS, false>(X, s, pdl, it, src, primal);
+    else e = X.strided ? launch_rows<double, ALGO, BS, true>(X, s, pdl, it, src, primal)
+                       : launch_rows<double, ALGO, BS, false>(X, s, pdl, it, src, primal);
     if (e != cudaSuccess && X.launch_err == cudaSuccess) X.launch_err = e;
 }
 template <int ALGO>
@@ -2272,6 +2418,12 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     const int64_t Mr = X->Mr, Nr = X->Nr;   // rows of A and A^T as stored
     L.A_rp = take((Mr + 1) * 4); L.A_ci = take((Z + 4) * 4); L.A_v = take((Z + 4) * vs);
     L.AT_rp = take((Nr + 1) * 4); L.AT_ci = take((Z + 4) * 4); L.AT_v = take((Z + 4) * vs);
+    X->strided = o.spmv_kernel == 0 && X->K == 1 && !X->staged;
+    const int64_t gA = X->strided ? (Mr + kStrideRows - 1) / kStrideRows : 0;
+    const int64_t gAT = X->strided ? (Nr + kStrideRows - 1) / kStrideRows : 0;
+    const size_t slot_bytes = X->vb == 32 ? sizeof(SlotT<float>) : sizeof(SlotT<double>);
+    L.A_sk = take(gA); L.AT_sk = take(gAT);
+    L.A_sl = take(gA * kStrideRows * slot_bytes); L.AT_sl = take(gAT * kStrideRows * slot_bytes);
     L.segs_p = take(sizeof(Seg) * X->n_sp); L.segs_d = take(sizeof(Seg) * X->n_sd);
     L.segs_e = take(sizeof(Seg) * X->n_se); L.segs_a = take(sizeof(Seg) * X->n_sa);
     L.ranges = take(sizeof(InstRange) * k);
@@ -2328,6 +2480,17 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         }
         arp[Mr] = (int32_t)Z;
         atrp[Nr] = (int32_t)Z;
+        if (X->strided) {
+            auto slots = [&](const int32_t *rp, const int32_t *ci, size_t v_off, int64_t rows, size_t sk_off,
+                             size_t sl_off) {
+                signed char *sk = (signed char *)(st.data() + sk_off);
+                char *sl = st.data() + sl_off;
+                return X->vb == 32 ? build_slots(rp, ci, (const float *)(st.data() + v_off), rows, sk, sl)
+                                   : build_slots(rp, ci, (const double *)(st.data() + v_off), rows, sk, sl);
+            };
+            X->strided_rows_A = slots(arp, aci, L.A_v, Mr, L.A_sk, L.A_sl);
+            X->strided_rows_AT = slots(atrp, atci, L.AT_v, Nr, L.AT_sk, L.AT_sl);
+        }
         put(st, L.segs_p, sp.data(), X->n_sp);
         put(st, L.segs_d, sd.data(), X->n_sd);
         put(st, L.segs_e, se.data(), X->n_se);
@@ -2374,6 +2537,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     X->h2d = (long long)L.upload_end;
     Bufs &b = X->b;
     b.A_rp = (const int *)(D + L.A_rp); b.A_ci = (const int *)(D + L.A_ci); b.A_v = D + L.A_v;
+    b.A_sk = (const signed char *)(D + L.A_sk); b.AT_sk = (const signed char *)(D + L.AT_sk);
+    b.A_sl = D + L.A_sl; b.AT_sl = D + L.AT_sl;
     b.AT_rp = (const int *)(D + L.AT_rp); b.AT_ci = (const int *)(D + L.AT_ci); b.AT_v = D + L.AT_v;
     b.c = (const double *)(D + L.c); b.l = (const double *)(D + L.l); b.u = (const double *)(D + L.u);
     b.q = (const double *)(D + L.q); b.Dr = (const double *)(D + L.Dr); b.Dc = (const double *)(D + L.Dc);
