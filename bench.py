@@ -210,6 +210,10 @@ def make_workload(name, rank):
     return P, desc, (32 if name == "paper-fp32" else 64)
 
 
+def _gains(args):
+    return None if not args.pw_gains else tuple(float(v) for v in args.pw_gains.split(","))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -240,7 +244,7 @@ def run_ours(args):
                      stages=args.stages,
                      rows_per_thread=[rpt], cta_rows=cta,
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
-                     adaptive_step=args.adaptive_step,
+                     adaptive_step=args.adaptive_step, pw_gains=_gains(args),
                      reorder=not args.no_reorder)
 
     def solve_once():
@@ -346,6 +350,20 @@ def run_ours(args):
                "includes": "uc_build_lp + uc_presolve (power iteration for ||A|| on the %s) + uc_solve "
                            "(upload, solve, download) + uc_get_solution" % ("host" if args.power_host else "device")}
 
+    # primal feasibility polishing (outside the timed region): the paper's
+    # absolute feasibility tolerance of 1e-5 (Sec. II-D) on the same solve
+    polish = None
+    if not args.no_polish and not args.adaptive_step and args.algorithm == "halpern":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp_, rcp = B.uc_solve(ps, tol=TOL, max_iter=args.max_iter, rows_per_thread=[rpt], cta_rows=cta,
+                              pw_gains=_gains(args), polish=True, tol_abs_feas=1e-5)
+        sp = B.uc_get_stats(rp_)
+        polish = {"status": sp["status_name"], "main_iters": sp["iters"], "polish_iters": sp["polish_iters"],
+                  "abs_primal_before": sp["abs_primal_unpolished"], "abs_primal_after": sp["abs_primal"],
+                  "rel_kkt_after": max(sp["rel_primal"], sp["rel_dual"], sp["rel_gap"]),
+                  "wall_s": time.perf_counter() - t0, "tol_abs_feas": 1e-5}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(P, args.cpu_iters, desc["workload"], simplex=args.config == "tiny")
@@ -374,6 +392,7 @@ def run_ours(args):
             "clocks": clk_sum,
             "gpu_launches": st["kernel_launches"] - launches0,
             "e2e": e2e,
+            "polish": polish,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -473,7 +492,7 @@ def run_batch(args):
     ps32 = presolve_all(probs, value_bits=32)
     presolve_s = time.perf_counter() - t0
     tuner = Tuner()
-    kw = dict(restart_metric=args.restart_metric)
+    kw = dict(restart_metric=args.restart_metric, pw_gains=_gains(args))
     solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)      # warm-up + tuning
     with ClockSampler(0) as clk:
         res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)
@@ -585,10 +604,12 @@ def run_served(args):
     for w in range((args.requests + 44) // 45):
         n = min(45, args.requests - 45 * w)
         arr = ucgen.poisson_arrivals(100 + w, n, 2.0) + t
+        if args.burst:               # the whole wave arrives at once, when its first request would
+            arr[:] = arr[0]
         for r in range(n):
             reqs.append(Request(rid=45 * w + r, problem=ucgen.served_request(base, w, r), arrival=float(arr[r])))
-        t = float(arr[-1])
-    srv = Server(base, slots=args.slots, hbm_budget_gb=150.0, tol=TOL, max_iter=args.max_iter,
+        t = float(arr[-1]) if not args.burst else float(ucgen.poisson_arrivals(100 + w, n, 2.0)[-1] + t)
+    srv = Server(base, slots=args.slots, hbm_budget_gb=args.hbm_budget_gb, tol=TOL, max_iter=args.max_iter,
                  warm_start=args.warm_start)
     with ClockSampler(0) as clk:
         m = srv.serve(reqs, realtime=True)
@@ -597,15 +618,70 @@ def run_served(args):
             "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": m["makespan_s"] / len(reqs) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{len(reqs)} requests on the 6049-bus / 700-unit / 48-period grid, "
-                                            "load x{0.80..1.20} + AR(1) 5%, Poisson 2 req/s",
-                                            "slots": m["slots"], "hbm_budget_gb": 150.0, "tol_rel_kkt": TOL,
-                                            "warm_start": args.warm_start},
+                                            "load x{0.80..1.20} + AR(1) 5%, Poisson 2 req/s" +
+                                            (", each wave in one burst" if args.burst else ""),
+                                            "slots": m["slots"], "hbm_budget_gb": args.hbm_budget_gb,
+                                            "tol_rel_kkt": TOL, "warm_start": args.warm_start},
             "served": m, "clocks": clk.summary(), "impl": "ours",
             "per_request": [{"rid": r.rid, "iters": r.iters, "status": r.status, "warm_from": r.warm_from,
                              "latency_s": r.latency, "omega": r.omega, "start_omega": r.start_omega}
                             for r in sorted(reqs, key=lambda r: r.rid)]}
     if not args.no_sequential:
         line["sequential_fp64_cold"] = sequential_baseline(reqs, base, tol=TOL, max_iter=args.max_iter)
+    print(json.dumps(line), flush=True)
+
+
+def run_served_mixed(args):
+    """Served stream of requests on grids of different sizes (the batch
+    members' grids: 300 to 6,049 buses, T 24/48), Poisson arrivals at
+    `--rate` req/s, continuous batching with one session per admitted request
+    on its own stream (MixedServer, `--slots` at most, HBM budget
+    `--hbm-budget-gb`), against one-at-a-time cold FP64 solves of the same
+    requests replayed on a simulated clock."""
+    import numpy as np
+    import torch
+    import ucgen
+    torch.cuda.set_device(0)
+    import paper_2607_03627_gb300 as pkg
+    pkg.build()
+    from paper_2607_03627_gb300 import binding as B
+    from paper_2607_03627_gb300.serve import MixedServer, Request
+    arr = ucgen.poisson_arrivals(200, args.requests, args.rate)
+    probs = [ucgen.batch_member(1 + (r % 64)) for r in range(args.requests)]
+    reqs = [Request(rid=r, problem=probs[r], arrival=float(arr[r])) for r in range(args.requests)]
+    srv = MixedServer(max_active=args.slots, hbm_budget_gb=args.hbm_budget_gb, tol=TOL, max_iter=args.max_iter)
+    with ClockSampler(0) as clk:
+        m = srv.serve(reqs)
+    srv.close()
+    line = {"metric": METRIC, "value": m["p50_latency_s"], "unit": "s (p50 served latency)",
+            "n_gpus": 1, "steps": len(reqs), "warmup": 0, "ms_per_step": m["makespan_s"] / len(reqs) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} requests on grids of 300-6049 buses (batch members 1-64, cycled), "
+                                   f"Poisson {args.rate} req/s", "max_active": args.slots,
+                       "hbm_budget_gb": args.hbm_budget_gb, "tol_rel_kkt": TOL},
+            "served": m, "clocks": clk.summary(), "impl": "ours",
+            "per_request": [{"rid": r.rid, "buses": r.problem.B, "iters": r.iters, "status": r.status,
+                             "latency_s": r.latency} for r in reqs]}
+    if not args.no_sequential:
+        t = 0.0
+        lat = []
+        for r in reqs:
+            ps = B.uc_presolve(B.uc_build_lp(r.problem))
+            sess = B.Session([ps], tol=TOL, max_iter=args.max_iter)
+            g0 = time.perf_counter()
+            sess.reset(-1)
+            sess.run()
+            sess.result(0)
+            g = time.perf_counter() - g0
+            sess.close()
+            t = max(t, r.arrival) + g
+            lat.append(t - r.arrival)
+        lat = np.array(lat)
+        line["sequential_fp64_cold"] = {
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "throughput_req_per_s": len(reqs) / (t - reqs[0].arrival),
+            "note": "device-resident cold solves one at a time, replayed on a simulated clock; presolve and "
+                    "upload not counted"}
     print(json.dumps(line), flush=True)
 
 
@@ -616,11 +692,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="paper",
-                    choices=["paper", "paper-fp32", "tiny", "batch64", "served", "paper-lanes"])
+                    choices=["paper", "paper-fp32", "tiny", "batch64", "served", "served-mixed", "paper-lanes"])
     ap.add_argument("--lanes", type=int, default=4, help="paper-lanes: LPs in the shared-matrix session (2 or 4)")
     ap.add_argument("--batch", type=int, default=64, help="batch64: number of LPs")
     ap.add_argument("--requests", type=int, default=45, help="served: requests (45 per wave)")
-    ap.add_argument("--slots", type=int, default=2, help="served: session slots")
+    ap.add_argument("--slots", type=int, default=2, help="served: session slots (served-mixed: sessions at once)")
+    ap.add_argument("--hbm-budget-gb", type=float, default=150.0, help="served: HBM budget for admission")
+    ap.add_argument("--burst", action="store_true", help="served: every wave arrives at once")
+    ap.add_argument("--rate", type=float, default=2.0, help="served-mixed: Poisson arrival rate (req/s)")
     ap.add_argument("--warm-start", action="store_true",
                     help="served: warm-start requests from the nearest solved one (duals + primal weight)")
     ap.add_argument("--no-sequential", action="store_true", help="batch64/served: skip the one-at-a-time baseline")
@@ -642,6 +721,10 @@ def main():
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
+    ap.add_argument("--no-polish", action="store_true",
+                    help="skip the untimed feasibility-polishing solve reported beside the line")
+    ap.add_argument("--pw-gains", default=None,
+                    help="primal-weight controller gains kp,ki,kd (default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -653,6 +736,8 @@ def main():
         run_lanes(args)
     elif args.config == "served":
         run_served(args)
+    elif args.config == "served-mixed":
+        run_served_mixed(args)
     else:
         run_ours(args)
 

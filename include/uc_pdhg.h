@@ -155,6 +155,22 @@ typedef struct {
                                     iterations (limit, evaluation period, restarts).  One LP per
                                     session, no lanes, row kernels; UC_EINVAL otherwise.  0: constant
                                     step (default) */
+    double pw_kp, pw_ki, pw_kd;  /* primal-weight update at restarts, a PID controller on ln omega with
+                                    error e = ln(omega dx / dy), dx and dy the primal and dual movement
+                                    of the epoch: ln omega -= kp e + ki sum(e) + kd (e - e_prev).
+                                    kp = 0.5, ki = kd = 0 is PDLP's rule.  Defaults: see
+                                    uc_default_solve_opts */
+    int polish;                  /* 1: primal feasibility polishing (uc_solve / uc_solve_batch, Halpern,
+                                    no lanes): an LP whose result meets tol_rel_kkt but violates a row
+                                    by more than tol_abs_feas (absolute, unscaled presolved LP; the
+                                    paper's absolute feasibility tolerance, Sec. II-D) is iterated on
+                                    with its objective cleared (c = 0), from the result's primal point,
+                                    a zero dual and the final primal weight, until its largest row
+                                    violation is at most tol_abs_feas.  The polished primal replaces
+                                    the result's, the dual is kept, and the stats are those of the
+                                    combined point.  0: off (default) */
+    int polish_max_iter;         /* iteration limit of the polishing phase (0: 10000); if it is
+                                    reached the result keeps its unpolished primal */
 } uc_solve_opts;
 
 typedef struct {
@@ -178,6 +194,8 @@ typedef struct {
     int64_t h2d_bytes;           /* host -> device bytes of the session upload */
     int64_t d2h_bytes;           /* device -> host bytes of this result (+ status polls) */
     int rejected_steps;          /* adaptive step size: attempts that were rejected (else 0) */
+    int polish_iters;            /* iterations of the polishing phase (0: not run) */
+    double abs_primal_unpolished; /* abs_primal of the point before polishing */
 } uc_stats;
 
 void uc_default_presolve_opts(uc_presolve_opts *o);

@@ -59,6 +59,19 @@ constant step.  With T the PDHG map above and z = (x, y):
           z = z0 = z_hat, j = 0, r_anchor = r re-weighted with the new omega.
 The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr".
 
+Primal feasibility polishing (after a solve that met the relative KKT
+tolerance).  The paper's PDHG runs with an absolute feasibility tolerance of
+1e-5 beside the 1e-4 convergence tolerance (Sec. II-D).  A point that meets
+the relative test can still violate rows by more than that in absolute terms,
+and on the UC LP such a violation (unserved load priced at VOLL) moves the
+objective.  Polishing (PDLP's feasibility polishing, Applegate et al. 2025,
+primal half) runs the Halpern variant on the feasibility problem -- the same
+rows and bounds, objective c = 0 -- from the solve's primal point, a zero dual
+and the solve's final primal weight, and stops when the map output's largest
+absolute violation on the unscaled presolved LP (kkt.abs_primal_inf) is at
+most the tolerance.  The polished primal replaces the solve's primal; the
+solve's dual is kept.
+
 Infeasibility detection (Halpern variant).  When the LP has no feasible point,
 the map has no fixed point and the step residual T(z) - z tends to a nonzero
 direction (the infimal displacement vector of the nonexpansive PDHG map).  At
@@ -84,6 +97,21 @@ BETA_ARTIFICIAL = 0.36
 N_EVAL = 64
 
 
+PDLP_GAINS = (0.5, 0.0, 0.0)
+DEFAULT_PW_GAINS = PDLP_GAINS     # the gains the solves use unless told otherwise
+
+
+@dataclasses.dataclass
+class PrimalWeightControl:
+    """PID controller on ln omega at restarts (see primal_weight_update)."""
+    kp: float = 0.5
+    ki: float = 0.0
+    kd: float = 0.0
+    isum: float = 0.0        # sum of the errors so far
+    eprev: float = 0.0       # the last error
+    has: bool = False        # an error was seen
+
+
 @dataclasses.dataclass
 class State:
     x: np.ndarray
@@ -104,6 +132,7 @@ class State:
     eta_try: float = 0.0
     w_sum: float = 0.0
     accepted: int = 0
+    pw: PrimalWeightControl = dataclasses.field(default_factory=PrimalWeightControl)
 
 
 @dataclasses.dataclass
@@ -218,10 +247,24 @@ def restart_decision(kkt_cand, kkt_anchor, kkt_prev, j, k_plus_1) -> bool:
     return False
 
 
-def primal_weight_update(omega, dx, dy) -> float:
-    if dx > 1e-10 and dy > 1e-10:
+def primal_weight_update(omega, dx, dy, ctl: PrimalWeightControl | None = None) -> float:
+    """The primal weight after a restart whose epoch moved the primal by dx and
+    the dual by dy.  The error e = ln(omega dx / dy) vanishes when the weighted
+    movements omega dx^2 and dy^2 / omega balance; the update is
+    ln omega <- ln omega - (kp e + ki sum(e) + kd (e - e_prev)) (the derivative
+    term is 0 at the first update).  PDLP's rule (Applegate et al. 2021),
+    omega <- exp(0.5 ln(dy/dx) + 0.5 ln omega), is kp = 0.5, ki = kd = 0, and is
+    computed in that form.  omega is kept when dx or dy is at most 1e-10."""
+    if not (dx > 1e-10 and dy > 1e-10):
+        return omega
+    if ctl is None or (ctl.kp, ctl.ki, ctl.kd) == PDLP_GAINS:
         return math.exp(0.5 * math.log(dy / dx) + 0.5 * math.log(omega))
-    return omega
+    e = math.log(omega * dx / dy)
+    ctl.isum += e
+    de = e - ctl.eprev if ctl.has else 0.0
+    ctl.eprev = e
+    ctl.has = True
+    return math.exp(math.log(omega) - (ctl.kp * e + ctl.ki * ctl.isum + ctl.kd * de))
 
 
 def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
@@ -249,7 +292,7 @@ def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
     if restart_decision(kc, st.kkt_anchor, st.kkt_prev, st.j, st.k):
         dx = float(np.linalg.norm(xc - st.x_anchor))
         dy = float(np.linalg.norm(yc - st.y_anchor))
-        st.omega = primal_weight_update(st.omega, dx, dy)
+        st.omega = primal_weight_update(st.omega, dx, dy, st.pw)
         st.x = xc.copy()
         st.y = yc.copy()
         st.x_anchor = st.x.copy()
@@ -270,12 +313,13 @@ def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
 
 def solve(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
           x0=None, y0=None, trace=None, trace_iters=(), adaptive: bool = False, attempts=None,
-          exact_sums: bool = False) -> Result:
+          exact_sums: bool = False, pw_gains=None) -> Result:
     """Run O1 on a ``presolve.Scaled`` problem.  ``trace(k, state)`` is called
     after every step k in ``trace_iters`` (k counts steps taken; with
     ``adaptive``, attempts).  ``attempts``, a list, receives (accepted, eta,
     eta_bar) of every adaptive attempt."""
     st = initial_state(S, x0, y0)
+    st.pw = PrimalWeightControl(*(DEFAULT_PW_GAINS if pw_gains is None else pw_gains))
     AT = S.A.T.tocsr()
     U = _unscaled_lp(S)
     trace_iters = set(trace_iters)
@@ -321,6 +365,7 @@ class HState:
     metric: str
     restarts: int = 0
     evals: int = 0
+    pw: PrimalWeightControl = dataclasses.field(default_factory=PrimalWeightControl)
 
 
 INFEAS_EVERY = 4      # evaluations between infeasibility tests
@@ -359,13 +404,16 @@ def halpern_step(S, st: HState, AT=None):
     st.k += 1
 
 
-def halpern_evaluate(S, st: HState, U, tol: float):
+def halpern_evaluate(S, st: HState, U, tol: float, stop_abs=None):
     """Evaluation after an n_eval block: (status, point, rel) with status None
     (continue), "optimal" or "infeasible" (point = the Farkas direction, scaled
-    dual space); applies a restart."""
+    dual space); applies a restart.  With ``stop_abs`` the stopping test is the
+    largest absolute primal violation of the map output (unscaled) instead of
+    the relative KKT."""
     st.evals += 1
     rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)
-    if max(rel) <= tol:
+    done = (max(rel) <= tol) if stop_abs is None else (kkt.abs_primal_inf(U, S.Dc * st.xh) <= stop_abs)
+    if done:
         return "optimal", (st.xh.copy(), st.yh.copy()), rel
     if st.evals % INFEAS_EVERY == 0:
         ray = st.yh - st.y_in
@@ -381,7 +429,7 @@ def halpern_evaluate(S, st: HState, U, tol: float):
     if restart_decision(r, st.r_anchor, st.r_prev, st.j, st.k):
         dx = float(np.linalg.norm(st.xh - st.x0))
         dy = float(np.linalg.norm(st.yh - st.y0))
-        st.omega = primal_weight_update(w, dx, dy)
+        st.omega = primal_weight_update(w, dx, dy, st.pw)
         wn = st.omega
         st.x = st.xh.copy()
         st.y = st.yh.copy()
@@ -401,17 +449,18 @@ def halpern_evaluate(S, st: HState, U, tol: float):
 
 def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
                   x0=None, y0=None, metric: str = "kkt", trace=None, trace_iters=(),
-                  omega0=None) -> Result:
+                  omega0=None, stop_abs=None, pw_gains=None) -> Result:
     """Run the Halpern variant; ``trace(k, state)`` after every step k in trace_iters
     (after the evaluation when k is a multiple of n_eval)."""
     st = halpern_initial_state(S, x0, y0, metric, omega0)
+    st.pw = PrimalWeightControl(*(DEFAULT_PW_GAINS if pw_gains is None else pw_gains))
     AT = S.A.T.tocsr()
     U = _unscaled_lp(S)
     trace_iters = set(trace_iters)
     while st.k < max_iter:
         halpern_step(S, st, AT)
         if st.k % n_eval == 0:
-            status, pt, rel = halpern_evaluate(S, st, U, tol)
+            status, pt, rel = halpern_evaluate(S, st, U, tol, stop_abs)
             if status is not None:
                 return Result(x=pt[0], y=pt[1], iters=st.k, status=status, rel=rel,
                               restarts=st.restarts, omega=st.omega, state=st,
@@ -421,3 +470,14 @@ def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N
     rel = kkt.relative_kkt(U, S.Dc * st.xh, S.Dr * st.yh)
     return Result(x=st.xh.copy(), y=st.yh.copy(), iters=st.k, status="iteration_limit", rel=rel,
                   restarts=st.restarts, omega=st.omega, state=st, which="map")
+
+
+def polish_primal(S, x, tol_abs: float = 1e-5, max_iter: int = 10_000, omega0=None,
+                  n_eval: int = N_EVAL, metric: str = "kkt", pw_gains=None) -> Result:
+    """Primal feasibility polishing (see the module docstring): the Halpern
+    variant on the feasibility problem (c = 0) from the scaled primal ``x``, a
+    zero dual and primal weight ``omega0`` (S.omega0 when None), until the
+    largest absolute violation of the unscaled rows is <= ``tol_abs``."""
+    F = dataclasses.replace(S, c=np.zeros_like(S.c))
+    return solve_halpern(F, tol=0.0, max_iter=max_iter, n_eval=n_eval, x0=x, metric=metric,
+                         omega0=omega0, stop_abs=tol_abs, pw_gains=pw_gains)

@@ -53,7 +53,8 @@ class uc_solve_opts(C.Structure):
                 ("no_reorder", C.c_int), ("no_pdl", C.c_int), ("algorithm", C.c_int),
                 ("restart_metric", C.c_int),
                 ("cancel", _P(C.c_int)), ("stages", C.c_int), ("lanes", C.c_int),
-                ("adaptive_step", C.c_int)]
+                ("adaptive_step", C.c_int), ("pw_kp", C.c_double), ("pw_ki", C.c_double),
+                ("pw_kd", C.c_double), ("polish", C.c_int), ("polish_max_iter", C.c_int)]
 
 
 class uc_device_lp(C.Structure):
@@ -72,7 +73,8 @@ class uc_stats(C.Structure):
                 ("upload_ms", C.c_double), ("primal_kernel_ms", C.c_double),
                 ("dual_kernel_ms", C.c_double), ("timed_launches", C.c_int),
                 ("kernel_launches", C.c_int), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
-                ("rejected_steps", C.c_int)]
+                ("rejected_steps", C.c_int), ("polish_iters", C.c_int),
+                ("abs_primal_unpolished", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -330,7 +332,9 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
                cancel=None, spmv_kernel: int = 0, algorithm: str = "halpern",
                restart_metric: str = "kkt", cta_rows: int = 0,
                rows_per_thread=None, pdl: bool = True, reorder: bool = True,
-               stages: int = 0, lanes: bool = False, adaptive_step: bool = False) -> tuple[uc_solve_opts, list]:
+               stages: int = 0, lanes: bool = False, adaptive_step: bool = False,
+               pw_gains=None, polish: bool = False, polish_max_iter: int = 0,
+               tol_abs_feas: float = 1e-5) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -348,6 +352,11 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.stages = int(stages)
     o.lanes = int(bool(lanes))
     o.adaptive_step = int(bool(adaptive_step))
+    o.polish = int(bool(polish))
+    o.polish_max_iter = int(polish_max_iter)
+    o.tol_abs_feas = float(tol_abs_feas)
+    if pw_gains is not None:   # (kp, ki, kd) of the primal-weight controller
+        o.pw_kp, o.pw_ki, o.pw_kd = (float(v) for v in pw_gains)
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)

@@ -79,6 +79,13 @@ struct Scalars {
     // division is a long FP64 sequence): the trial step's tau and sigma, 1 / wsum,
     // and 1 / (steps averaged) at the next evaluation of the constant-step variant
     double ad_tau, ad_sigma, inv_wsum, inv_next;
+    // primal-weight controller: gains, running sum and last value of the error
+    // e = ln(omega dx / dy) at restarts
+    double pw_kp, pw_ki, pw_kd, pw_isum, pw_eprev;
+    int pw_has;
+    // > 0: stop when the largest absolute violation of the unscaled rows is at
+    // most this (primal feasibility polishing), instead of the relative KKT test
+    double stop_abs;
 };
 // kkt_anchor / kkt_prev hold the restart metric's anchor and previous value
 // for the Halpern variant as well.
@@ -1136,6 +1143,24 @@ __device__ double kkt_w(double rp2, double rd2, double gap, double w) {
     return sqrt(w * w * rp2 + rd2 / (w * w) + gap * gap);
 }
 
+// Primal weight at a restart from the epoch's movement dx (primal), dy (dual).
+// The error e = ln(omega dx / dy) is zero when the weighted movements
+// omega dx^2 and dy^2 / omega balance.  The update is a PID controller on ln
+// omega: ln omega <- ln omega - (kp e + ki sum(e) + kd (e - e_prev)).  PDLP's
+// rule, omega <- exp(0.5 ln(dy/dx) + 0.5 ln omega), is the proportional part
+// with kp = 0.5 and is computed in that form.  omega is kept when dx or dy is
+// at most 1e-10.
+__device__ double primal_weight(Scalars *S, double w, double dx, double dy) {
+    if (!(dx > 1e-10 && dy > 1e-10)) return w;
+    if (S->pw_kp == 0.5 && S->pw_ki == 0.0 && S->pw_kd == 0.0) return exp(0.5 * log(dy / dx) + 0.5 * log(w));
+    const double e = log(w * dx / dy);
+    S->pw_isum += e;
+    const double de = S->pw_has ? e - S->pw_eprev : 0.0;
+    S->pw_eprev = e;
+    S->pw_has = 1;
+    return exp(log(w) - (S->pw_kp * e + S->pw_ki * S->pw_isum + S->pw_kd * de));
+}
+
 __global__ void k_control(Bufs b, int mode, int k_lps) {
     const int inst = blockIdx.x * blockDim.x + threadIdx.x;
     if (inst >= k_lps) return;
@@ -1186,7 +1211,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
         }
         S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
         S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
-        if (fmax(rel[0][0], fmax(rel[0][1], rel[0][2])) <= S->tol) {
+        if (S->stop_abs > 0.0 ? (T[RPU] <= S->stop_abs) : (fmax(rel[0][0], fmax(rel[0][1], rel[0][2])) <= S->tol)) {
             S->status = OPTIMAL;
             S->which = 0;
             b.status[inst] = S->status;
@@ -1207,8 +1232,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
                              ((double)j >= 0.36 * (double)k);
         if (restart) {
             const double dx = sqrt(T[DX2]), dy = sqrt(T[DY2]);
-            double wn = w;
-            if (dx > 1e-10 && dy > 1e-10) wn = exp(0.5 * log(dy / dx) + 0.5 * log(w));
+            const double wn = primal_weight(S, w, dx, dy);
             S->omega = wn;
             S->kkt_anchor = (S->metric == METRIC_KKT) ? kkt_w(T[RP2], T[RD2], gap[0], wn)
                                                       : sqrt(wn * fx2 + fy2 / wn);
@@ -1255,8 +1279,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
     if (restart) {
         const double *a = T + cand * kSlots;
         const double dx = sqrt(a[DX2]), dy = sqrt(a[DY2]);
-        double wn = w;
-        if (dx > 1e-10 && dy > 1e-10) wn = exp(0.5 * log(dy / dx) + 0.5 * log(w));
+        const double wn = primal_weight(S, w, dx, dy);
         S->omega = wn;
         S->kkt_anchor = kkt_w(a[RP2], a[RD2], gap[cand], wn);
         S->kkt_prev = INFINITY;
@@ -1567,6 +1590,9 @@ struct uc_session {
     // once, vectors interleaved (element j of LP r at j*K + r); K = 1 otherwise
     int K = 1;
     int64_t Mr = 0, Nr = 0;       // rows of A and of A^T as stored
+    // primal feasibility polishing in progress: LPs reset now stop on this
+    // absolute violation (0: the relative KKT test)
+    double polish_tol = 0.0;
     // period-strided 16-row groups read from slot records (row kernels, K = 1)
     bool strided = false;
     int64_t strided_rows_A = 0, strided_rows_AT = 0;
@@ -1836,6 +1862,10 @@ static Scalars make_scalars(const uc_session &X, const PsData &p, double omega =
     s.ad_tau = p.eta / w;
     s.ad_sigma = p.eta * w;
     s.inv_next = 1.0 / (double)X.o.n_eval;
+    s.pw_kp = X.o.pw_kp;
+    s.pw_ki = X.o.pw_ki;
+    s.pw_kd = X.o.pw_kd;
+    s.stop_abs = X.polish_tol;
     return s;
 }
 
@@ -2309,6 +2339,17 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         return UC_EINVAL;
     }
     X->algo = o.algorithm;
+    if (o.polish != 0 && o.polish != 1) { set_error("polish must be 0 or 1"); return UC_EINVAL; }
+    if (o.polish && (o.algorithm != ALG_HALPERN || o.lanes || o.adaptive_step || !(o.tol_abs_feas > 0.0) ||
+                     o.polish_max_iter < 0)) {
+        set_error("polish needs the Halpern algorithm, no lanes, tol_abs_feas > 0 and polish_max_iter >= 0");
+        return UC_EINVAL;
+    }
+    if (!(std::isfinite(o.pw_kp) && std::isfinite(o.pw_ki) && std::isfinite(o.pw_kd)) || o.pw_kp < 0 ||
+        o.pw_ki < 0 || o.pw_kd < 0) {
+        set_error("pw_kp, pw_ki and pw_kd must be finite and >= 0");
+        return UC_EINVAL;
+    }
     if (o.adaptive_step != 0 && o.adaptive_step != 1) { set_error("adaptive_step must be 0 or 1"); return UC_EINVAL; }
     X->adaptive = o.adaptive_step == 1;
     if (X->adaptive && (X->algo != ALG_AVERAGE || k != 1 || o.lanes || o.spmv_kernel == 2)) {
@@ -3341,6 +3382,99 @@ int uc_solve(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc
     return uc_solve_batch(&ps, 1, opts, stream, out);
 }
 
+namespace uc {
+namespace dev {
+
+// Relative KKT parts, the largest absolute row violation and the objectives of
+// a scaled presolved point (natural order) on the unscaled presolved LP, as
+// the device evaluation defines them (host loops, fixed order).
+static void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p, double &rel_d,
+                     double &rel_g, double &abs_p, double &pobj, double &dobj) {
+    double rpu = 0.0, rdu = 0.0, qy = 0.0, cx = 0.0, bnd = 0.0;
+    for (int i = 0; i < p.m(); i++) {
+        double ax = 0.0;
+        for (int32_t e = p.A.rowptr[i]; e < p.A.rowptr[i + 1]; e++) ax += p.A.val[e] * xs[p.A.colidx[e]];
+        double r = ax - p.q[i];
+        if (i >= p.m_eq && r > 0.0) r = 0.0;
+        rpu = std::max(rpu, std::fabs(r) / p.Dr[i]);
+        qy += p.q[i] * ys[i];
+    }
+    for (int j = 0; j < p.n(); j++) {
+        double t = 0.0;
+        for (int32_t e = p.AT.rowptr[j]; e < p.AT.rowptr[j + 1]; e++) t += p.AT.val[e] * ys[p.AT.colidx[e]];
+        const double lm = p.c[j] - t;
+        const bool lf = std::isfinite(p.l[j]), uf = std::isfinite(p.u[j]);
+        const double lp = (lf && uf) ? lm : lf ? std::max(lm, 0.0) : uf ? std::min(lm, 0.0) : 0.0;
+        rdu = std::max(rdu, std::fabs(lm - lp) / p.Dc[j]);
+        cx += p.c[j] * xs[j];
+        if (lf) bnd += p.l[j] * std::max(lp, 0.0);
+        if (uf) bnd += p.u[j] * std::min(lp, 0.0);
+    }
+    pobj = cx;
+    dobj = qy + bnd;
+    rel_p = rpu / (1.0 + p.q_inf);
+    rel_d = rdu / (1.0 + p.c_inf);
+    rel_g = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
+    abs_p = rpu;
+}
+
+// Primal feasibility polishing of the LPs of a finished session whose result
+// met the relative KKT tolerance but violates a row by more than tol_abs_feas
+// (absolute, unscaled): on the device their objective is cleared (c = 0), they
+// restart from the result's primal point with a zero dual and the final
+// primal weight, and iterate until the largest absolute row violation of the
+// map output is at most tol_abs_feas (or polish_max_iter iterations).  The
+// polished primal replaces the result's; its dual is kept, and the result's
+// KKT figures are evaluated again for the combined point.  The session's c is
+// left cleared: it is used for nothing afterwards.
+static int session_polish(uc_session &X, std::vector<uc_result *> &res) {
+    std::vector<int> todo;
+    for (int i = 0; i < X.k; i++)
+        if (res[i] && res[i]->stats.status == UC_OK && res[i]->stats.abs_primal > X.o.tol_abs_feas) todo.push_back(i);
+    for (int i = 0; i < X.k; i++)
+        if (res[i]) { res[i]->stats.abs_primal_unpolished = res[i]->stats.abs_primal; res[i]->stats.polish_iters = 0; }
+    if (todo.empty()) return UC_OK;
+    const int main_iter = X.o.max_iter;
+    X.o.max_iter = X.o.polish_max_iter ? X.o.polish_max_iter : 10000;
+    X.polish_tol = X.o.tol_abs_feas;
+    int rc = UC_OK;
+    for (int i : todo) {
+        const size_t cx = X.coff[i] * 8, nx = (X.coff[i + 1] - X.coff[i]) * 8;
+        if (nx && cudaMemsetAsync(X.D + X.L.c + cx, 0, nx, X.s) != cudaSuccess) { rc = UC_ECUDA; break; }
+        rc = session_set_start(X, i, res[i]->x_ret.data(), nullptr, res[i]->stats.omega);
+        if (rc) break;
+        rc = session_reset(X, i);
+        if (rc) break;
+    }
+    if (!rc) rc = session_run(X, max_replays(X));
+    for (int i : todo) {
+        if (rc) break;
+        uc_result *pr = nullptr;
+        const int st = session_result(X, i, &pr);
+        if (!pr) { rc = st; break; }
+        std::unique_ptr<uc_result> g(pr);
+        uc_result &r = *res[i];
+        r.stats.polish_iters = pr->stats.iters;
+        if (st == UC_OK) {   // the polish reached the tolerance
+            r.x_ret = pr->x_ret;
+            const PsData &p = *X.P[i];
+            double pobj, dobj;
+            host_kkt(p, r.x_ret.data(), r.y_ret.data(), r.stats.rel_primal, r.stats.rel_dual, r.stats.rel_gap,
+                     r.stats.abs_primal, pobj, dobj);
+            r.stats.dual_objective = dobj + p.obj_const;
+        }
+        r.stats.kernel_launches = pr->stats.kernel_launches;
+        r.stats.solve_ms += pr->stats.solve_ms;
+        r.stats.d2h_bytes += pr->stats.d2h_bytes;
+    }
+    X.o.max_iter = main_iter;
+    X.polish_tol = 0.0;
+    return rc;
+}
+
+}  // namespace dev
+}  // namespace uc
+
 int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *opts, void *stream,
                    uc_result **outs) {
     if (!ps || !outs || k < 1) { set_error("uc_solve_batch: bad arguments"); return UC_EINVAL; }
@@ -3358,6 +3492,11 @@ int uc_solve_batch(const uc_presolved *const *ps, int k, const uc_solve_opts *op
         int st = dev::session_result(*s, i, &outs[i]);
         if (!outs[i]) return st;
         if (st != UC_OK && overall == UC_OK) overall = st;
+    }
+    if (s->o.polish) {
+        std::vector<uc_result *> res(outs, outs + k);
+        rc = dev::session_polish(*s, res);
+        if (rc) return rc;
     }
     return overall;
 }

@@ -631,6 +631,9 @@ void uc_default_solve_opts(uc_solve_opts *o) {
     o->max_iter = 100000;
     o->n_eval = 64;
     o->use_graph = 1;
+    o->pw_kp = 0.5;
+    o->pw_ki = 0.0;
+    o->pw_kd = 0.0;
 }
 
 int uc_build_lp(const uc_problem *prob, uc_lp **out) {

@@ -6,7 +6,8 @@ device-resident session whose slots hold the base matrix; admitting a
 request replaces a free slot's right-hand side and bounds (uc_session_update_lp,
 no matrix upload), warm-starts it from the solved request with the nearest
 net-load vector, and resets just that slot while the other slots keep
-iterating.  Finished slots are harvested between short runs of CUDA-graph
+iterating.  A warm-started request that ends without meeting the tolerance
+is solved again from the cold start in its slot.  Finished slots are harvested between short runs of CUDA-graph
 replays and refilled from the queue (continuous batching).  The number of
 slots is capped by an HBM budget.  Host presolve (uc_presolve_reuse: the
 base LP's scaling is reused) runs on a thread pool as requests arrive.
@@ -22,6 +23,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import dataclasses
 import math
+import threading
 import time
 
 import numpy as np
@@ -48,6 +50,8 @@ class Request:
     omega: float = math.nan              # final primal weight
     x: np.ndarray | None = None          # returned point (scaled presolved)
     y: np.ndarray | None = None
+    retried_cold: bool = False           # the warm start failed and the request was solved cold
+    warm_iters: int = 0                  # iterations spent on the failed warm start
 
     @property
     def latency(self) -> float:
@@ -156,9 +160,21 @@ class Server:
                     st = self.sess.status(slot)
                     if st == 2:
                         continue
-                    r = running.pop(slot)
+                    r = running[slot]
                     res, rc = self.sess.result(slot)
                     stats = B.uc_get_stats(res)
+                    if rc != B.UC_OK and r.warm_from >= 0 and not r.retried_cold:
+                        # a warm start can stall the method (the neighbour's primal
+                        # weight can be far from this request's): solve it again from
+                        # the cold start in the same slot, which holds its LP already
+                        r.retried_cold = True
+                        r.warm_iters = stats["iters"]
+                        r.start_x = r.start_y = None     # the start the result comes from
+                        r.start_omega = 0.0
+                        self.sess.set_start(slot, None, None, 0.0)
+                        self.sess.reset(slot)
+                        continue
+                    running.pop(slot)
                     r.finished = clock() if realtime else sim_t
                     r.status = rc
                     r.iters = stats["iters"]
@@ -191,6 +207,7 @@ class Server:
                 "makespan_s": span, "gpu_busy_s": gpu_busy,
                 "mean_iters": float(np.mean([r.iters for r in reqs])),
                 "warm_started": int(sum(r.warm_from >= 0 for r in reqs)),
+                "retried_cold": int(sum(r.retried_cold for r in reqs)),
                 "all_optimal": bool(all(r.status == B.UC_OK for r in reqs))}
 
 
@@ -220,3 +237,144 @@ def sequential_baseline(requests: list[Request], base_problem, tol: float = 1e-4
     return {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "throughput_req_per_s": len(reqs) / (t - reqs[0].arrival), "mean_iters": float(np.mean(iters)),
             "note": "device time of cold solves replayed on a simulated clock; presolve not counted"}
+
+
+def session_bytes_estimate(ps, value_bits: int = 64, max_iter: int = 100_000) -> int:
+    """Device bytes of a one-LP session of `ps`, estimated from its sizes: the
+    matrix and its transpose (int32 indices, FP64 or FP32 values, row pointers),
+    the period-strided slot records, eight constant and start vectors and ten
+    state vectors per column or row, and the Halpern weight tables."""
+    n, m, _, nnz = B.uc_presolved_dims(ps)
+    vs = 4 if value_bits == 32 else 8
+    slot = 8 if value_bits == 32 else 16
+    per_col = 4 + 8 * 8 + 5 * 8 + slot
+    per_row = 4 + 4 * 8 + 5 * 8 + slot
+    tables = 2 * 8 * min(max_iter + 1, 1 << 22)
+    return int(1.05 * (2 * nnz * (4 + vs) + n * per_col + m * per_row + tables) + (1 << 20))
+
+
+class MixedServer:
+    """Continuous batching of UC requests on grids of any size.
+
+    A shared-matrix session needs one scaled matrix for all its slots, so
+    requests on different grids cannot share one.  Here every admitted request
+    gets a session of its own, with its own CUDA stream, driven by a worker
+    thread: requests that arrive while others are on the GPU are admitted in
+    arrival order as soon as a worker is free and the HBM budget holds their
+    session (estimated from their sizes, then measured for each grid seen), and
+    the kernels of the running sessions overlap on the device.  Presolve runs on
+    a thread pool as requests arrive; a request on a grid already seen reuses
+    that grid's scaling (uc_presolve_reuse).  Each session's arithmetic is its
+    own, so a request's iterates and solution are those of a solve alone, bit
+    for bit (tested).
+    """
+
+    def __init__(self, max_active: int = 4, hbm_budget_gb: float = 150.0, tol: float = 1e-4,
+                 max_iter: int = 100_000, value_bits: int = 64, presolve_workers: int = 8,
+                 keep_solutions: bool = False):
+        self.max_active = max(1, int(max_active))
+        self.budget = float(hbm_budget_gb) * 1e9
+        self.tol = tol
+        self.max_iter = max_iter
+        self.value_bits = value_bits
+        self.keep = keep_solutions
+        self.pool = cf.ThreadPoolExecutor(max_workers=presolve_workers)
+        self.workers = cf.ThreadPoolExecutor(max_workers=self.max_active)
+        self.bases: list = []          # presolved base LP of every grid seen
+        self.grid_bytes: dict = {}     # measured session bytes by LP sizes
+        self.lock = threading.Lock()
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+        self.workers.shutdown(wait=True)
+
+    def _presolve(self, req: Request):
+        lp = B.uc_build_lp(req.problem)
+        with self.lock:
+            bases = list(self.bases)
+        for base in bases:
+            try:
+                return B.uc_presolve_reuse(base, lp)
+            except B.UCError:
+                continue
+        ps = B.uc_presolve(lp, value_bits=self.value_bits)
+        with self.lock:
+            self.bases.append(ps)
+        return ps
+
+    def _need(self, ps) -> int:
+        key = B.uc_presolved_dims(ps)
+        return self.grid_bytes.get(key, session_bytes_estimate(ps, self.value_bits, self.max_iter))
+
+    def _solve(self, r: Request, ps, t0: float):
+        import torch
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            sess = B.Session([ps], tol=self.tol, max_iter=self.max_iter)
+            nbytes = sess.device_bytes()
+            sess.reset(-1)
+            sess.run()
+            res, rc = sess.result(0)
+            stats = B.uc_get_stats(res)
+            n, m, _, _ = B.uc_presolved_dims(ps)
+            x, y = B.uc_get_iterate(res, 2, n, m)
+            sess.close()
+        r.finished = time.perf_counter() - t0
+        r.status = rc
+        r.iters = stats["iters"]
+        r.objective = stats["objective"]
+        r.rel_kkt = max(stats["rel_primal"], stats["rel_dual"], stats["rel_gap"])
+        r.omega = stats["omega"]
+        if self.keep:
+            r.x, r.y = x, y
+        return nbytes
+
+    def serve(self, requests: list[Request]) -> dict:
+        """Serve the requests (arrival times in seconds from now); returns metrics."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        futures = {}
+        queue: list[Request] = []
+        running = {}                   # future -> (request, reserved bytes, size key)
+        used = 0
+        peak_active = 0
+        nxt = 0
+        done = 0
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                r = reqs[nxt]
+                futures[r.rid] = self.pool.submit(self._presolve, r)
+                queue.append(r)
+                nxt += 1
+            while queue and futures[queue[0].rid].done() and len(running) < self.max_active:
+                ps = futures[queue[0].rid].result()
+                need = self._need(ps)
+                if running and used + need > self.budget:
+                    break                   # wait for memory (one request always runs)
+                r = queue.pop(0)
+                del futures[r.rid]
+                r.admitted = time.perf_counter() - t0
+                r.slot = len(running)
+                f = self.workers.submit(self._solve, r, ps, t0)
+                running[f] = (r, need, B.uc_presolved_dims(ps))
+                used += need
+                peak_active = max(peak_active, len(running))
+            finished = [f for f in running if f.done()]
+            for f in finished:
+                r, need, key = running.pop(f)
+                nbytes = f.result()
+                self.grid_bytes[key] = nbytes
+                used -= need
+                done += 1
+            if not finished:
+                waits = [reqs[nxt].arrival - now] if nxt < len(reqs) else []
+                time.sleep(min([0.002] + [w for w in waits if w > 0]))
+        lat = np.array([r.latency for r in reqs])
+        span = max(r.finished for r in reqs) - min(r.arrival for r in reqs)
+        return {"requests": len(reqs), "max_active": self.max_active, "peak_active": peak_active,
+                "hbm_budget_gb": self.budget / 1e9,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "mean_latency_s": float(lat.mean()), "throughput_req_per_s": len(reqs) / span,
+                "makespan_s": span, "mean_iters": float(np.mean([r.iters for r in reqs])),
+                "all_optimal": bool(all(r.status == B.UC_OK for r in reqs))}

@@ -77,6 +77,8 @@ def test_server_results_same_alone_and_in_the_mix(B, slots):
     m = srv.serve(reqs, realtime=False)
     srv.close()
     assert m["all_optimal"] and m["slots"] == slots and m["warm_started"] >= 1
+    # a warm start that fails is solved again cold (its start fields then say cold)
+    assert all(r.start_y is None for r in reqs if r.retried_cold)
     assert m["lanes"] == (slots == 4)
     assert any(r.admitted > 0 and r.slot >= 0 for r in reqs)
     base_ps = B.uc_presolve(B.uc_build_lp(base))
@@ -124,3 +126,47 @@ def test_two_rows_per_thread_equal_one_row(B, K, vbits):
                 np.testing.assert_array_equal(y1, y2)
             s1, s2 = B.uc_get_stats(r1), B.uc_get_stats(r2)
             assert (s1["restarts"], s1["omega"]) == (s2["restarts"], s2["omega"])
+
+
+def _mixed_requests():
+    from paper_2607_03627_gb300.serve import Request
+    a, b = ucgen.tiny(0), ucgen.tiny(4)           # two grids of the same size class
+    c = ucgen.make_problem(7, B=37, L=53, G=11, T=5, lo=0.5, hi=0.9, noise=0.05, zero_pmin_frac=0.2)
+    probs = [ucgen.served_request(a, 0, 0), b, c, ucgen.served_request(a, 0, 1), ucgen.served_request(b, 0, 2), c]
+    return [Request(rid=i, problem=P, arrival=0.02 * i) for i, P in enumerate(probs)]
+
+
+def test_mixed_server_results_same_alone_and_in_the_mix(B):
+    from paper_2607_03627_gb300.serve import MixedServer
+    reqs = _mixed_requests()
+    srv = MixedServer(max_active=3, tol=KKT_TOL, keep_solutions=True)
+    m = srv.serve(reqs)
+    srv.close()
+    assert m["all_optimal"] and m["peak_active"] >= 2          # grids of different sizes overlapped
+    for r in reqs:
+        ps = B.uc_presolve(B.uc_build_lp(r.problem))
+        res, rc = B.uc_solve(ps, tol=KKT_TOL)
+        assert rc == B.UC_OK
+        n, m_, _, _ = B.uc_presolved_dims(ps)
+        x, y = B.uc_get_iterate(res, 2, n, m_)
+        np.testing.assert_array_equal(x, r.x)
+        np.testing.assert_array_equal(y, r.y)
+        assert B.uc_get_stats(res)["iters"] == r.iters
+        raw, ps_o, _ = oracle_pipeline(r.problem)
+        xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+        assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+
+
+def test_mixed_server_admits_by_hbm_budget(B):
+    from paper_2607_03627_gb300.serve import MixedServer, session_bytes_estimate
+    reqs = _mixed_requests()
+    big = max(session_bytes_estimate(B.uc_presolve(B.uc_build_lp(r.problem))) for r in reqs)
+    srv = MixedServer(max_active=4, hbm_budget_gb=big / 1e9, tol=KKT_TOL)
+    m = srv.serve(reqs)
+    srv.close()
+    assert m["all_optimal"] and m["peak_active"] == 1        # the budget holds one session at a time
+    # and the estimate is an upper bound on what a session takes
+    ps = B.uc_presolve(B.uc_build_lp(reqs[0].problem))
+    sess = B.Session([ps], tol=KKT_TOL)
+    assert sess.device_bytes() <= session_bytes_estimate(ps)
+    sess.close()

@@ -149,7 +149,7 @@ MUTANTS = {
     "weight on the wrong block of the residual": [("math.sqrt(w * fx2 + fy2 / w)", "math.sqrt(fx2 / w + w * fy2)")],
     "r_prev left unchanged": [("st.r_prev = r\n", "st.r_prev = st.r_prev\n")],
     "j not reset": [("st.j = 0", "st.j = st.j")],
-    "primal weight rule inverted": [("primal_weight_update(w, dx, dy)", "primal_weight_update(w, dy, dx)")],
+    "primal weight rule inverted": [("primal_weight_update(w, dx, dy, st.pw)", "primal_weight_update(w, dy, dx, st.pw)")],
 }
 
 

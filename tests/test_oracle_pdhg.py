@@ -120,6 +120,32 @@ def test_primal_weight_rule_scripted():
     assert pdhg.primal_weight_update(3.0, 1.0, 1e-11) == 3.0
 
 
+def test_primal_weight_controller_by_hand():
+    # e = ln(omega dx / dy); ln omega <- ln omega - (kp e + ki sum e + kd (e - e_prev))
+    ctl = pdhg.PrimalWeightControl(kp=0.3, ki=0.02, kd=0.3)
+    # omega = 1, dx = 1, dy = e^2: e1 = -2, no derivative yet: ln omega = 2 (0.3 + 0.02) = 0.64
+    w1 = pdhg.primal_weight_update(1.0, 1.0, math.exp(2.0), ctl)
+    assert w1 == pytest.approx(math.exp(0.64), rel=1e-14)
+    # dx = 1, dy = e^0.64 * e^1: e2 = 0.64 - 1.64 = -1, sum = -3, de = +1:
+    # ln omega = 0.64 - (-0.3 - 0.06 + 0.3) = 0.70
+    w2 = pdhg.primal_weight_update(w1, 1.0, math.exp(1.64), ctl)
+    assert w2 == pytest.approx(math.exp(0.70), rel=1e-14)
+    # a step with no movement keeps omega and the controller's state
+    assert pdhg.primal_weight_update(w2, 0.0, 1.0, ctl) == w2 and ctl.isum == pytest.approx(-3.0)
+
+
+@pytest.mark.parametrize("gains", [pdhg.PDLP_GAINS, pdhg.DEFAULT_PW_GAINS, (0.3, 0.02, 0.3)])
+def test_primal_weight_controller_settles_on_the_balance(gains):
+    # a plant whose movement ratio dy/dx = rho does not depend on omega: the
+    # controller's only rest point has e = 0, i.e. omega = rho
+    for rho in (1e-3, 0.7, 250.0):
+        ctl = pdhg.PrimalWeightControl(*gains)
+        w = 1.0
+        for _ in range(200):
+            w = pdhg.primal_weight_update(w, 1.0, rho, ctl)
+        assert abs(math.log(w / rho)) <= 1e-6, (gains, rho, w)
+
+
 def test_first_evaluation_restarts():
     P = ucgen.micro(1, B=6, L=8, G=3, T=4)
     raw, ps, S = _pipeline(P)
