@@ -476,7 +476,7 @@ def run_reference(args):
 
 def run_batch(args):
     """64 uneven UC LPs (buses log-uniform in [300, 6049], T in {24, 48}, seeds
-    1-64) in one block-diagonal session with FP32 matrix values and autotuned
+    1-64) in one block-diagonal session with FP32 (or, --value-bits 64, FP64) matrix values and autotuned
     row splits, against one-at-a-time FP64 solves of the same LPs."""
     import numpy as np
     import torch
@@ -488,21 +488,23 @@ def run_batch(args):
     from paper_2607_03627_gb300.batch import presolve_all, solve_batch
     from paper_2607_03627_gb300.tune import Tuner
     probs = [ucgen.batch_member(s) for s in range(1, args.batch + 1)]
+    vb = args.value_bits
     t0 = time.perf_counter()
-    ps32 = presolve_all(probs, value_bits=32)
+    ps32 = presolve_all(probs, value_bits=vb)
     presolve_s = time.perf_counter() - t0
     tuner = Tuner()
     kw = dict(restart_metric=args.restart_metric, pw_gains=_gains(args))
-    solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)      # warm-up + tuning
+    solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=vb, **kw)      # warm-up + tuning
     with ClockSampler(0) as clk:
-        res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=32, **kw)
+        res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=vb, **kw)
     st32 = [B.uc_get_stats(r) for r, _ in res32]
     line = {"metric": METRIC, "value": args.batch / (info["solve_ms"] / 1e3), "unit": "UC LP/s",
             "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": info["solve_ms"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32-values/f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-values/f64" if vb == 32 else "f64",
+            "data": "synthetic",
             "config": {"workload": f"{args.batch} UC LPs, buses log-uniform in [300, 6049], T 24/48, seeds 1-{args.batch}",
                        "total_nnz": int(sum(B.uc_presolved_dims(p)[3] for p in ps32)),
-                       "matrix_values": "fp32", "vectors": "fp64", "tol_rel_kkt": TOL},
+                       "matrix_values": f"fp{vb}", "vectors": "fp64", "tol_rel_kkt": TOL},
             "rows_per_thread": info["rows_per_thread"], "all_optimal": all(s["status"] == 0 for s in st32),
             "per_lp": [{"buses": P.B, "T": P.T, "iters": s["iters"], "status": s["status_name"],
                         "rel_kkt": max(s["rel_primal"], s["rel_dual"], s["rel_gap"])} for P, s in zip(probs, st32)],
@@ -695,6 +697,8 @@ def main():
                     choices=["paper", "paper-fp32", "tiny", "batch64", "served", "served-mixed", "paper-lanes"])
     ap.add_argument("--lanes", type=int, default=4, help="paper-lanes: LPs in the shared-matrix session (2 or 4)")
     ap.add_argument("--batch", type=int, default=64, help="batch64: number of LPs")
+    ap.add_argument("--value-bits", type=int, default=32, choices=[32, 64],
+                    help="batch64: matrix values of the batched session (the one-at-a-time baseline is FP64)")
     ap.add_argument("--requests", type=int, default=45, help="served: requests (45 per wave)")
     ap.add_argument("--slots", type=int, default=2, help="served: session slots (served-mixed: sessions at once)")
     ap.add_argument("--hbm-budget-gb", type=float, default=150.0, help="served: HBM budget for admission")

@@ -195,6 +195,8 @@ typedef struct {
     int64_t d2h_bytes;           /* device -> host bytes of this result (+ status polls) */
     int rejected_steps;          /* adaptive step size: attempts that were rejected (else 0) */
     int polish_iters;            /* iterations of the polishing phase (0: not run) */
+    int superbasic;              /* uc_crossover results: variables left strictly between their bounds
+                                    (0: the point is a vertex) */
     double abs_primal_unpolished; /* abs_primal of the point before polishing */
 } uc_stats;
 
@@ -323,6 +325,27 @@ void uc_session_free(uc_session *s);
 int uc_get_solution(const uc_result *res, double *p, double *u, double *v, double *theta,
                     double *f, double *shed, double *lmp, uc_stats *stats);
 /* Raw-LP primal [raw n] and dual [raw m] of the returned point. */
+/* Crossover: from the returned point of a finished solve to a vertex (basic
+ * solution) of the presolved LP -- the stage that follows PDHG in the paper's
+ * GPU arm (Sec. II-C, Alg. 1 "Solver 1"; Sec. III-C).  Host only.  The point is
+ * clipped to its bounds, phase 1 of a bounded revised simplex (dense basis
+ * inverse, nonbasic variables allowed strictly inside their bounds) removes
+ * the row residuals, phase 2 optimises, and a primal push moves every variable
+ * left inside its bounds to a bound or into the basis.  *out is a new result
+ * (free with uc_free_result) whose returned point is the vertex and whose dual
+ * is the simplex multipliers; its stats carry the pivots in `iters`, the KKT
+ * figures of the vertex and `superbasic` = 0 for a vertex.  max_pivots <= 0:
+ * 50 (n + m).  UC_EINVAL for LPs with more than 20000 rows (the basis inverse
+ * is dense) or a result without a returned point; UC_EITERLIMIT at the pivot
+ * limit; UC_EINFEASIBLE when phase 1 ends with a residual; the caller keeps
+ * `res`. */
+int uc_crossover(const uc_result *res, int64_t max_pivots, uc_result **out);
+
+/* A result holding a caller's point (x [n], y [m], scaled presolved LP, the
+ * LP's own order; host memory, copied) with its KKT figures, e.g. to run
+ * uc_crossover or uc_get_solution on a point from elsewhere.  Host only. */
+int uc_result_from_point(const uc_presolved *ps, const double *x, const double *y, uc_result **out);
+
 int uc_get_raw_solution(const uc_result *res, double *x, double *y);
 /* Presolved-space, SCALED iterates: which = 0 current iterate, 1 the average
  * since the last restart (averaging variant) or the restart anchor (Halpern

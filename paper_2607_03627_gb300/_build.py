@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libucpdhg.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-HOST_SOURCES = ["uc_host.cpp"]
+HOST_SOURCES = ["uc_host.cpp", "uc_crossover.cpp"]
 DEVICE_SOURCES = ["uc_device.cu"]
 HEADERS = [os.path.join(CSRC, "uc_internal.h"), os.path.join(INCLUDE, "uc_pdhg.h")]
 

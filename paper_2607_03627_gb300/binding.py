@@ -73,7 +73,7 @@ class uc_stats(C.Structure):
                 ("upload_ms", C.c_double), ("primal_kernel_ms", C.c_double),
                 ("dual_kernel_ms", C.c_double), ("timed_launches", C.c_int),
                 ("kernel_launches", C.c_int), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
-                ("rejected_steps", C.c_int), ("polish_iters", C.c_int),
+                ("rejected_steps", C.c_int), ("polish_iters", C.c_int), ("superbasic", C.c_int),
                 ("abs_primal_unpolished", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -96,6 +96,8 @@ _SIGS = {
     "uc_solve_batch": (C.c_int, [_P(C.c_void_p), C.c_int, _P(uc_solve_opts), C.c_void_p, _P(C.c_void_p)]),
     "uc_get_solution": (C.c_int, [C.c_void_p, _d, _d, _d, _d, _d, _d, _d, _P(uc_stats)]),
     "uc_get_raw_solution": (C.c_int, [C.c_void_p, _d, _d]),
+    "uc_crossover": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_void_p)]),
+    "uc_result_from_point": (C.c_int, [C.c_void_p, _d, _d, _P(C.c_void_p)]),
     "uc_get_iterate": (C.c_int, [C.c_void_p, C.c_int, _d, _d]),
     "uc_presolved_device_order": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32)]),
     "uc_presolved_strided_groups": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int64), _P(C.c_int32),
@@ -410,6 +412,25 @@ def uc_get_solution(res, T: int, B: int, L: int, G: int) -> dict:
            "uc_get_solution")
     d["stats"] = st.as_dict()
     return d
+
+
+def uc_crossover(res, max_pivots: int = 0):
+    """A vertex of the presolved LP from a result's returned point (host);
+    returns (vertex result, status)."""
+    out = C.c_void_p()
+    rc = lib.uc_crossover(res.ptr, int(max_pivots), C.byref(out))
+    if not out.value:
+        raise UCError(rc, "uc_crossover")
+    return ResultHandle(out.value, keep=res), rc
+
+
+def uc_result_from_point(ps, x, y):
+    """A result holding the scaled presolved point (x, y) (host only)."""
+    xa, ya = _f64(x), _f64(y)
+    out = C.c_void_p()
+    _check(lib.uc_result_from_point(ps.ptr, _ptr(xa, C.c_double), _ptr(ya, C.c_double), C.byref(out)),
+           "uc_result_from_point")
+    return ResultHandle(out.value, keep=ps)
 
 
 def uc_get_raw_solution(res, raw_n: int, raw_m: int):

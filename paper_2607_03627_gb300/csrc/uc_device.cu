@@ -3385,39 +3385,6 @@ int uc_solve(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc
 namespace uc {
 namespace dev {
 
-// Relative KKT parts, the largest absolute row violation and the objectives of
-// a scaled presolved point (natural order) on the unscaled presolved LP, as
-// the device evaluation defines them (host loops, fixed order).
-static void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p, double &rel_d,
-                     double &rel_g, double &abs_p, double &pobj, double &dobj) {
-    double rpu = 0.0, rdu = 0.0, qy = 0.0, cx = 0.0, bnd = 0.0;
-    for (int i = 0; i < p.m(); i++) {
-        double ax = 0.0;
-        for (int32_t e = p.A.rowptr[i]; e < p.A.rowptr[i + 1]; e++) ax += p.A.val[e] * xs[p.A.colidx[e]];
-        double r = ax - p.q[i];
-        if (i >= p.m_eq && r > 0.0) r = 0.0;
-        rpu = std::max(rpu, std::fabs(r) / p.Dr[i]);
-        qy += p.q[i] * ys[i];
-    }
-    for (int j = 0; j < p.n(); j++) {
-        double t = 0.0;
-        for (int32_t e = p.AT.rowptr[j]; e < p.AT.rowptr[j + 1]; e++) t += p.AT.val[e] * ys[p.AT.colidx[e]];
-        const double lm = p.c[j] - t;
-        const bool lf = std::isfinite(p.l[j]), uf = std::isfinite(p.u[j]);
-        const double lp = (lf && uf) ? lm : lf ? std::max(lm, 0.0) : uf ? std::min(lm, 0.0) : 0.0;
-        rdu = std::max(rdu, std::fabs(lm - lp) / p.Dc[j]);
-        cx += p.c[j] * xs[j];
-        if (lf) bnd += p.l[j] * std::max(lp, 0.0);
-        if (uf) bnd += p.u[j] * std::min(lp, 0.0);
-    }
-    pobj = cx;
-    dobj = qy + bnd;
-    rel_p = rpu / (1.0 + p.q_inf);
-    rel_d = rdu / (1.0 + p.c_inf);
-    rel_g = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
-    abs_p = rpu;
-}
-
 // Primal feasibility polishing of the LPs of a finished session whose result
 // met the relative KKT tolerance but violates a row by more than tol_abs_feas
 // (absolute, unscaled): on the device their objective is cleared (c = 0), they
@@ -3459,7 +3426,7 @@ static int session_polish(uc_session &X, std::vector<uc_result *> &res) {
             r.x_ret = pr->x_ret;
             const PsData &p = *X.P[i];
             double pobj, dobj;
-            host_kkt(p, r.x_ret.data(), r.y_ret.data(), r.stats.rel_primal, r.stats.rel_dual, r.stats.rel_gap,
+            uc::host_kkt(p, r.x_ret.data(), r.y_ret.data(), r.stats.rel_primal, r.stats.rel_dual, r.stats.rel_gap,
                      r.stats.abs_primal, pobj, dobj);
             r.stats.dual_objective = dobj + p.obj_const;
         }

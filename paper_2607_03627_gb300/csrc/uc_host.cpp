@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <limits>
 #include <new>
 #include <thread>
@@ -570,6 +571,39 @@ static double power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, 
     return std::sqrt(lam);
 }
 
+// Relative KKT parts, the largest absolute row violation and the objectives of
+// a scaled presolved point (natural order) on the unscaled presolved LP, as
+// the device evaluation defines them (host loops, fixed order).
+void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p, double &rel_d,
+                     double &rel_g, double &abs_p, double &pobj, double &dobj) {
+    double rpu = 0.0, rdu = 0.0, qy = 0.0, cx = 0.0, bnd = 0.0;
+    for (int i = 0; i < p.m(); i++) {
+        double ax = 0.0;
+        for (int32_t e = p.A.rowptr[i]; e < p.A.rowptr[i + 1]; e++) ax += p.A.val[e] * xs[p.A.colidx[e]];
+        double r = ax - p.q[i];
+        if (i >= p.m_eq && r > 0.0) r = 0.0;
+        rpu = std::max(rpu, std::fabs(r) / p.Dr[i]);
+        qy += p.q[i] * ys[i];
+    }
+    for (int j = 0; j < p.n(); j++) {
+        double t = 0.0;
+        for (int32_t e = p.AT.rowptr[j]; e < p.AT.rowptr[j + 1]; e++) t += p.AT.val[e] * ys[p.AT.colidx[e]];
+        const double lm = p.c[j] - t;
+        const bool lf = std::isfinite(p.l[j]), uf = std::isfinite(p.u[j]);
+        const double lp = (lf && uf) ? lm : lf ? std::max(lm, 0.0) : uf ? std::min(lm, 0.0) : 0.0;
+        rdu = std::max(rdu, std::fabs(lm - lp) / p.Dc[j]);
+        cx += p.c[j] * xs[j];
+        if (lf) bnd += p.l[j] * std::max(lp, 0.0);
+        if (uf) bnd += p.u[j] * std::min(lp, 0.0);
+    }
+    pobj = cx;
+    dobj = qy + bnd;
+    rel_p = rpu / (1.0 + p.q_inf);
+    rel_d = rdu / (1.0 + p.c_inf);
+    rel_g = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
+    abs_p = rpu;
+}
+
 void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
                std::vector<double> &y) {
     const RawLp &raw = *ps.raw;
@@ -805,6 +839,63 @@ int uc_presolved_export(const uc_presolved *h, int32_t *rowptr, int32_t *colidx,
     if (scalars) {
         scalars[0] = p.eta; scalars[1] = p.omega0; scalars[2] = p.norm_A;
         scalars[3] = p.obj_const; scalars[4] = p.q_inf; scalars[5] = p.c_inf; scalars[6] = p.norm_bound;
+    }
+    return UC_OK;
+}
+
+int uc_result_from_point(const uc_presolved *ps, const double *x, const double *y, uc_result **out) {
+    if (!ps || !x || !y || !out) { set_error("uc_result_from_point: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    try {
+        auto r = std::make_unique<uc_result>();
+        r->ps = ps->d;
+        const int n = ps->d->n(), m = ps->d->m();
+        r->x_ret.assign(x, x + n);
+        r->y_ret.assign(y, y + m);
+        r->x_cur = r->x_avg = r->x_ret;
+        r->y_cur = r->y_avg = r->y_ret;
+        uc_stats &o = r->stats;
+        std::memset(&o, 0, sizeof o);
+        double pobj, dobj;
+        host_kkt(*ps->d, x, y, o.rel_primal, o.rel_dual, o.rel_gap, o.abs_primal, pobj, dobj);
+        o.dual_objective = dobj + ps->d->obj_const;
+        o.abs_primal_unpolished = o.abs_primal;
+        o.status = UC_OK;
+        *out = r.release();
+    } catch (const std::bad_alloc &) {
+        set_error("uc_result_from_point: out of host memory");
+        return UC_ENOMEM;
+    }
+    return UC_OK;
+}
+
+int uc_crossover(const uc_result *res, int64_t max_pivots, uc_result **out) {
+    if (!res || !out) { set_error("uc_crossover: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    if (res->x_ret.empty()) { set_error("uc_crossover: the result holds no returned point"); return UC_EINVAL; }
+    try {
+        auto v = std::make_unique<uc_result>();
+        v->ps = res->ps;
+        int pivots = 0, left = 0;
+        const int rc = crossover(*res->ps, res->x_ret, max_pivots, v->x_ret, v->y_ret, pivots, left);
+        if (rc) return rc;
+        v->x_cur = v->x_avg = v->x_ret;
+        v->y_cur = v->y_avg = v->y_ret;
+        uc_stats &o = v->stats;
+        o = res->stats;
+        o.status = UC_OK;
+        o.iters = pivots;
+        o.superbasic = left;
+        double pobj, dobj;
+        host_kkt(*res->ps, v->x_ret.data(), v->y_ret.data(), o.rel_primal, o.rel_dual, o.rel_gap, o.abs_primal,
+                 pobj, dobj);
+        o.dual_objective = dobj + res->ps->obj_const;
+        o.polish_iters = 0;
+        o.abs_primal_unpolished = o.abs_primal;
+        *out = v.release();
+    } catch (const std::bad_alloc &) {
+        set_error("uc_crossover: out of host memory");
+        return UC_ENOMEM;
     }
     return UC_OK;
 }

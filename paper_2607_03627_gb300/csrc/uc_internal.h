@@ -75,6 +75,17 @@ struct PsData {
 // fails, UC_ENOMEM when device memory is short.
 int device_power_norm(const Csr &A, const Csr &AT, int max_iter, double tol, double *out);
 
+// Relative KKT parts, largest absolute row violation and objectives of a
+// scaled presolved point (natural order) on the unscaled presolved LP.
+void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p, double &rel_d,
+              double &rel_g, double &abs_p, double &pobj, double &dobj);
+
+// Crossover of a scaled presolved primal point to a vertex (uc_crossover.cpp):
+// the vertex x_out, the simplex multipliers y_out (both scaled), the pivots
+// taken and the variables left strictly between their bounds.
+int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots, std::vector<double> &x_out,
+              std::vector<double> &y_out, int &pivots, int &superbasic_left);
+
 // Host-side postsolve: scaled presolved (x_s, y_s) -> raw (x, y).
 void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
                std::vector<double> &y);
