@@ -341,6 +341,23 @@ int uc_get_solution(const uc_result *res, double *p, double *u, double *v, doubl
  * `res`. */
 int uc_crossover(const uc_result *res, int64_t max_pivots, uc_result **out);
 
+/* The host simplex of uc_crossover from the cold start (each column at its
+ * bound nearest 0, an artificial per row): an optimal vertex of the presolved
+ * LP on the CPU, the CPU arm of uc_solve_concurrent.  cancel (nullable): a
+ * nonzero value stops it at its next pivot with UC_ECANCELLED.  Same limits
+ * and status codes as uc_crossover; stats.solve_ms is its wall time. */
+int uc_simplex_solve(const uc_presolved *ps, int64_t max_pivots, const volatile int *cancel, uc_result **out);
+
+/* Alg. 1 of the paper (Sec. II-C): the device PDHG (uc_solve with *opts, on
+ * the calling thread) and the host simplex (uc_simplex_solve, on a second
+ * thread) run at once on the same LP; the first to end optimal stops the other
+ * through its cancel flag, and its result is returned (*winner: 0 device,
+ * 1 host).  An arm that ends without an optimal result does not stop the
+ * other; the host arm refuses LPs of more than 20000 rows, so on those the
+ * device arm runs alone.  opts->cancel is replaced by the race's own flag. */
+int uc_solve_concurrent(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc_result **out,
+                        int *winner);
+
 /* A result holding a caller's point (x [n], y [m], scaled presolved LP, the
  * LP's own order; host memory, copied) with its KKT figures, e.g. to run
  * uc_crossover or uc_get_solution on a point from elsewhere.  Host only. */

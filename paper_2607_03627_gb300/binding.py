@@ -98,6 +98,8 @@ _SIGS = {
     "uc_get_raw_solution": (C.c_int, [C.c_void_p, _d, _d]),
     "uc_crossover": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_void_p)]),
     "uc_result_from_point": (C.c_int, [C.c_void_p, _d, _d, _P(C.c_void_p)]),
+    "uc_simplex_solve": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int), _P(C.c_void_p)]),
+    "uc_solve_concurrent": (C.c_int, [C.c_void_p, _P(uc_solve_opts), C.c_void_p, _P(C.c_void_p), _P(C.c_int)]),
     "uc_get_iterate": (C.c_int, [C.c_void_p, C.c_int, _d, _d]),
     "uc_presolved_device_order": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32)]),
     "uc_presolved_strided_groups": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int64), _P(C.c_int32),
@@ -422,6 +424,32 @@ def uc_crossover(res, max_pivots: int = 0):
     if not out.value:
         raise UCError(rc, "uc_crossover")
     return ResultHandle(out.value, keep=res), rc
+
+
+def uc_simplex_solve(ps, max_pivots: int = 0, cancel=None):
+    """The host simplex from the cold start (CPU arm); returns (result, status).
+    ``cancel``: a ctypes.c_int another thread may set to stop it."""
+    out = C.c_void_p()
+    rc = lib.uc_simplex_solve(ps.ptr, int(max_pivots), None if cancel is None else C.byref(cancel),
+                              C.byref(out))
+    if not out.value:
+        raise UCError(rc, "uc_simplex_solve")
+    return ResultHandle(out.value, keep=ps), rc
+
+
+def uc_solve_concurrent(ps, **kw):
+    """Alg. 1: device PDHG and host simplex at once, the first optimal one wins;
+    returns (result, status, winner) with winner 0 (device) or 1 (host)."""
+    stream, alloc = _torch_stream_and_allocator()
+    o, keep = solve_opts(**kw)
+    o.alloc = alloc.alloc
+    o.free = alloc.free
+    out = C.c_void_p()
+    win = C.c_int(-1)
+    rc = lib.uc_solve_concurrent(ps.ptr, C.byref(o), stream, C.byref(out), C.byref(win))
+    if not out.value:
+        raise UCError(rc, "uc_solve_concurrent")
+    return ResultHandle(out.value, keep=ps), rc, win.value
 
 
 def uc_result_from_point(ps, x, y):

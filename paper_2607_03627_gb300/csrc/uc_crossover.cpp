@@ -30,10 +30,13 @@
 // kRefactor pivots, so the crossover is for LPs with up to kMaxRows rows.
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "uc_internal.h"
@@ -42,7 +45,6 @@ namespace uc {
 namespace {
 
 constexpr double kInf = std::numeric_limits<double>::infinity();
-constexpr double kFeasTol = 1e-9;     // primal feasibility of basic variables (scaled LP)
 constexpr double kOptTol = 1e-9;      // reduced-cost optimality
 constexpr double kPivTol = 1e-9;      // smallest pivot element taken
 constexpr int kRefactor = 100;
@@ -62,6 +64,7 @@ struct Simplex {
     std::vector<double> Binv;                   // m x m, row-major
     int pivots = 0, since_refactor = 0, degenerate = 0;
     int64_t max_pivots = 0;
+    const volatile int *cancel = nullptr;       // nonzero: stop at the next pivot
 
     void column(int j, std::vector<double> &dense) const {
         std::fill(dense.begin(), dense.end(), 0.0);
@@ -191,10 +194,11 @@ struct Simplex {
         return 0;
     }
     // simplex iterations on the current cost vector: 0 optimal, 1 unbounded,
-    // 3 singular basis, 4 pivot limit
+    // 3 singular basis, 4 pivot limit, 5 cancelled
     int iterate(std::vector<double> &y, std::vector<double> &alpha) {
         for (;;) {
             if (pivots >= max_pivots) return 4;
+            if (cancel && *cancel) return 5;
             duals(y);
             int enter = -1, dir = 0;
             double best = kOptTol;
@@ -221,7 +225,7 @@ struct Simplex {
 
 // Crossover of a finished solve's returned point (see the top of the file).
 int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots, std::vector<double> &x_out,
-              std::vector<double> &y_out, int &pivots, int &superbasic_left) {
+              std::vector<double> &y_out, int &pivots, int &superbasic_left, const volatile int *cancel) {
     const int m = p.m(), n = p.n();
     if (m > kMaxRows) {
         set_error("uc_crossover: %d rows; the dense-basis crossover takes at most %d", m, kMaxRows);
@@ -233,6 +237,7 @@ int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots
     S.ns = m - p.m_eq;
     S.nv = n + S.ns + m;
     S.max_pivots = max_pivots > 0 ? max_pivots : 50LL * (n + m);
+    S.cancel = cancel;
     S.cp.assign((size_t)S.nv + 1, 0);
     // structural columns from A^T rows, surplus -e_i for ">=" rows, artificials later
     for (int j = 0; j < n; j++) {
@@ -289,6 +294,7 @@ int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots
     for (int i = 0; i < m; i++) S.Binv[(size_t)i * m + i] = res[i] >= 0.0 ? 1.0 : -1.0;
     std::vector<double> y(m), alpha(m);
     int rc = S.iterate(y, alpha);
+    if (rc == 5) { set_error("uc_crossover: cancelled"); return UC_ECANCELLED; }
     if (rc == 4) { set_error("uc_crossover: pivot limit in phase 1"); return UC_EITERLIMIT; }
     if (rc) { set_error("uc_crossover: phase 1 failed (%d)", rc); return UC_ENUMERIC; }
     double infeas = 0.0;
@@ -304,6 +310,7 @@ int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots
     S.degenerate = 0;
     for (int round = 0; round < 4; round++) {
         rc = S.iterate(y, alpha);
+        if (rc == 5) { set_error("uc_crossover: cancelled"); return UC_ECANCELLED; }
         if (rc == 4) { set_error("uc_crossover: pivot limit in phase 2"); return UC_EITERLIMIT; }
         if (rc) { set_error("uc_crossover: phase 2 failed (%d)", rc); return rc == 1 ? UC_EUNBOUNDED : UC_ENUMERIC; }
         // primal push: superbasics to a bound or into the basis
@@ -330,4 +337,90 @@ int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots
     return UC_OK;
 }
 
+// A vertex-optimal result of the LP by the host simplex from the cold start
+// (every column at its bound nearest 0): the CPU arm of the concurrent solve.
+static int simplex_result(const std::shared_ptr<const PsData> &p, int64_t max_pivots, const volatile int *cancel,
+                          uc_result **out) {
+    std::vector<double> x0(p->n());
+    for (int j = 0; j < p->n(); j++) x0[j] = std::min(std::max(0.0, p->l[j]), p->u[j]);
+    auto r = std::make_unique<uc_result>();
+    r->ps = p;
+    int pivots = 0, left = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = crossover(*p, x0, max_pivots, r->x_ret, r->y_ret, pivots, left, cancel);
+    if (rc) return rc;
+    r->x_cur = r->x_avg = r->x_ret;
+    r->y_cur = r->y_avg = r->y_ret;
+    uc_stats &o = r->stats;
+    std::memset(&o, 0, sizeof o);
+    o.status = UC_OK;
+    o.iters = pivots;
+    o.superbasic = left;
+    double pobj, dobj;
+    host_kkt(*p, r->x_ret.data(), r->y_ret.data(), o.rel_primal, o.rel_dual, o.rel_gap, o.abs_primal, pobj, dobj);
+    o.dual_objective = dobj + p->obj_const;
+    o.abs_primal_unpolished = o.abs_primal;
+    o.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = r.release();
+    return UC_OK;
+}
+
 }  // namespace uc
+
+int uc_simplex_solve(const uc_presolved *ps, int64_t max_pivots, const volatile int *cancel, uc_result **out) {
+    if (!ps || !out) { uc::set_error("uc_simplex_solve: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    try {
+        return uc::simplex_result(ps->d, max_pivots, cancel, out);
+    } catch (const std::bad_alloc &) {
+        uc::set_error("uc_simplex_solve: out of host memory");
+        return UC_ENOMEM;
+    }
+}
+
+// Alg. 1 of the paper (Sec. II-C): both arms on the same LP at once -- the
+// device PDHG (uc_solve) on the calling thread and the host simplex on a
+// second thread -- and the first arm to end optimal stops the other through
+// its cancel flag.  An arm that ends without an optimal result (iteration
+// limit, an LP too large for the dense simplex) does not stop the other.
+int uc_solve_concurrent(const uc_presolved *ps, const uc_solve_opts *opts, void *stream, uc_result **out,
+                        int *winner) {
+    if (!ps || !out) { uc::set_error("uc_solve_concurrent: null argument"); return UC_EINVAL; }
+    *out = nullptr;
+    if (winner) *winner = -1;
+    uc_solve_opts o;
+    uc_default_solve_opts(&o);
+    if (opts) o = *opts;
+    volatile int stop_gpu = 0, stop_cpu = 0;
+    o.cancel = &stop_gpu;
+    uc_result *cpu_res = nullptr;
+    int cpu_rc = UC_EINVAL;
+    std::string cpu_err;
+    std::thread cpu([&]() {
+        cpu_rc = uc_simplex_solve(ps, 0, &stop_cpu, &cpu_res);
+        if (cpu_rc == UC_OK) stop_gpu = 1;
+        else cpu_err = uc_last_error();
+    });
+    uc_result *gpu_res = nullptr;
+    const int gpu_rc = uc_solve(ps, &o, stream, &gpu_res);
+    if (gpu_rc == UC_OK) stop_cpu = 1;
+    cpu.join();
+    std::unique_ptr<uc_result> g(gpu_res), c(cpu_res);
+    if (gpu_rc == UC_OK && !(cpu_rc == UC_OK && cpu_res->stats.solve_ms < gpu_res->stats.solve_ms)) {
+        if (winner) *winner = 0;
+        *out = g.release();
+        return UC_OK;
+    }
+    if (cpu_rc == UC_OK) {
+        if (winner) *winner = 1;
+        *out = c.release();
+        return UC_OK;
+    }
+    if (gpu_res) {                          // neither optimal: the device result as it ended
+        if (winner) *winner = 0;
+        *out = g.release();
+        return gpu_rc;
+    }
+    uc::set_error("uc_solve_concurrent: no arm returned a result (device %d; host: %s)", gpu_rc, cpu_err.c_str());
+    return gpu_rc ? gpu_rc : cpu_rc;
+}

@@ -84,7 +84,7 @@ void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p
 // the vertex x_out, the simplex multipliers y_out (both scaled), the pivots
 // taken and the variables left strictly between their bounds.
 int crossover(const PsData &p, const std::vector<double> &xs, int64_t max_pivots, std::vector<double> &x_out,
-              std::vector<double> &y_out, int &pivots, int &superbasic_left);
+              std::vector<double> &y_out, int &pivots, int &superbasic_left, const volatile int *cancel = nullptr);
 
 // Host-side postsolve: scaled presolved (x_s, y_s) -> raw (x, y).
 void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,

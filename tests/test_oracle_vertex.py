@@ -84,3 +84,30 @@ def test_crossover_rejects_results_without_a_point_and_big_lps(B):
     res = B.uc_result_from_point(ps, np.zeros(n), np.zeros(m))
     with pytest.raises(B.UCError, match="rows"):
         B.uc_crossover(res)
+
+
+def test_host_simplex_arm_reaches_the_simplex_optimum(B):
+    # the CPU arm of the concurrent solve, from the cold start, on a micro UC LP
+    P = ucgen.micro(2, B=5, L=6, G=3, T=3)
+    raw = olp.build_lp(P)
+    ps_o = ops.presolve(raw)
+    ref = simplex.solve_lp(raw)
+    r, rc = B.uc_simplex_solve(B.uc_presolve(B.uc_build_lp(P)))
+    assert rc == B.UC_OK and B.uc_get_stats(r)["superbasic"] == 0
+    xr, yr = B.uc_get_raw_solution(r, raw.n, raw.m)
+    assert abs(float(raw.c @ xr) - ref.obj) <= 1e-9 * abs(ref.obj)
+    assert vertex.is_vertex(ps_o.lp, xr[ps_o.col_map])
+
+
+def test_host_simplex_arm_stops_when_cancelled(B):
+    import ctypes
+    import threading
+    import time
+    ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(1)))
+    flag = ctypes.c_int(0)
+    timer = threading.Timer(0.2, lambda: setattr(flag, "value", 1))
+    timer.start()
+    t0 = time.perf_counter()
+    with pytest.raises(B.UCError, match="cancelled"):
+        B.uc_simplex_solve(ps, cancel=flag)
+    assert time.perf_counter() - t0 < 5.0
