@@ -47,28 +47,29 @@ MAX_ITER = 100_000
 # DRAM bytes per launch of the iteration kernels from one ncu capture with
 # --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern
 # (profiles/pdhg_kernels_grid6049.md): valid only for the kernel source they
-# were taken on (the hash of the row kernels' section of uc_device.cu) and the
-# launch shape (threads per CTA, rows per thread).
-NCU_TRAFFIC = {
-    ("paper", "halpern", "k_primal"): {"src": "7af00afb8c03e5fd", "launch": (128, 1), "bytes": 65662336 + 2434176},
-    ("paper", "halpern", "k_dual"): {"src": "7af00afb8c03e5fd", "launch": (128, 1), "bytes": 44714496 + 1490432},
-}
+# were taken on (the hash of the row kernels' section of uc_device.cu, the
+# device layout and the strided-slot builder) and the launch shape (threads per
+# CTA, rows per thread).
+NCU_TRAFFIC = {}
 NCU_TRAFFIC_RPT2 = {
-    ("paper", "halpern", "k_primal"): {"src": "7af00afb8c03e5fd", "launch": (128, 2), "bytes": 65927808 + 1882624},
-    ("paper", "halpern", "k_dual"): {"src": "7af00afb8c03e5fd", "launch": (128, 2), "bytes": 44738816 + 1195520},
+    ("paper", "halpern", "k_primal"): {"src": "544ca1434cab5eaa", "launch": (128, 2), "bytes": 34107136 + 2486016},
+    ("paper", "halpern", "k_dual"): {"src": "544ca1434cab5eaa", "launch": (128, 2), "bytes": 15715072 + 1178624},
 }
 
 
 def _src_hash():
     """sha256 (16 hex digits) of the row kernels and their helpers in uc_device.cu,
-    and of the code that lays the LP out in device order."""
+    of the code that lays the LP out in device order and of the builder of the
+    period-strided slot records."""
     with open(os.path.join(ROOT, "paper_2607_03627_gb300", "csrc", "uc_device.cu")) as f:
         src = f.read()
     a = src.index("// FP64 is scarce on this GPU")
     b = src.index("// staged iteration kernels (Halpern)")
     c = src.index("// Device view of an LP.")
     d = src.index("// same scaled matrix (structure, values as stored, equality rows)")
-    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()[:16]
+    e = src.index("// Slot records of the period-strided groups")
+    f_ = src.index("// natural-order vector -> device order")
+    return hashlib.sha256((src[a:b] + src[c:d] + src[e:f_]).encode()).hexdigest()[:16]
 
 
 def _peaks():
@@ -231,7 +232,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     lp = B.uc_build_lp(P)
     pw_dev = 0 if args.power_host else 1
-    ps = B.uc_presolve(lp, value_bits=vbits, power_device=pw_dev)
+    ps = B.uc_presolve(lp, value_bits=vbits, power_device=pw_dev, aggressive=int(args.aggressive))
     presolve_s = time.perf_counter() - t0
     n, m, m_eq, nnz = B.uc_presolved_dims(ps)
     vs = 4 if vbits == 32 else 8
@@ -333,7 +334,7 @@ def run_ours(args):
         h2d = d2h = 0
         for _ in range(args.e2e_steps):
             lp2 = B.uc_build_lp(P)
-            ps2 = B.uc_presolve(lp2, value_bits=vbits, power_device=pw_dev)
+            ps2 = B.uc_presolve(lp2, value_bits=vbits, power_device=pw_dev, aggressive=int(args.aggressive))
             r2, rc2 = B.uc_solve(ps2, tol=TOL, max_iter=args.max_iter, algorithm=args.algorithm,
                                  adaptive_step=args.adaptive_step,
                                  restart_metric=args.restart_metric)
@@ -377,6 +378,7 @@ def run_ours(args):
             "config": dict(desc, n=n, m=m, nnz=nnz, matrix_values=f"fp{vbits}", vectors="fp64",
                            tol_rel_kkt=TOL, max_iter=args.max_iter, n_eval=64,
                            algorithm=args.algorithm, restart_metric=args.restart_metric,
+                           presolve="aggressive" if args.aggressive else "default",
                            adaptive_step=bool(args.adaptive_step),
                            rows_per_thread=rpt, cta_rows=cta or 128,
                            l2="inputs larger than L2 (working set %.0f MB > 126 MB)" % ((bp + bd) / 1e6),
@@ -725,6 +727,8 @@ def main():
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
     ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
+    ap.add_argument("--aggressive", action="store_true",
+                    help="paper configs: aggressive presolve (doubleton equations substituted)")
     ap.add_argument("--no-polish", action="store_true",
                     help="skip the untimed feasibility-polishing solve reported beside the line")
     ap.add_argument("--pw-gains", default=None,

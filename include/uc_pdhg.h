@@ -81,6 +81,12 @@ typedef struct {
     double power_tol;            /* relative change that stops it (default 1e-10) */
     int value_bits;              /* 64: FP64 matrix values on device; 32: FP32 (default 64) */
     int threads;                 /* host threads for presolve (0 = hardware concurrency) */
+    int aggressive;              /* 1: also substitute doubleton equations a_f x_f + a_s x_s = q whose
+                                    x_s appears in no other row (on the UC LP: the balance rows of
+                                    leaf buses without units hold only the line flow and the shed
+                                    column): x_s's bounds move onto x_f and its cost into x_f's, the
+                                    row and x_s leave the LP, postsolve recovers both (the paper's
+                                    tuned, more aggressive presolve, Sec. II-D).  0: off (default) */
     int power_device;            /* 1: run the power iteration for ||A_s||_2 on the current CUDA
                                     device (same steps and stopping rule, fixed-order device
                                     reductions; A_s and A_s^T are copied to device memory for the

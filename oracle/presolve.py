@@ -14,7 +14,14 @@ to every load so that the reduced structure does not depend on the load:
                     the row is dropped;
          1 entry a x_j:  equality fixes l_j = u_j = q / a;  ">=" tightens
                     l_j (a > 0) or u_j (a < 0) to q / a; the row is dropped;
-    3. every active column with no entry in an active row is fixed at the bound
+    3. (aggressive presolve only) doubleton equations: equality rows are swept in order; a row with two
+       entries a_f x_f + a_s x_s = q in active columns, one of which (x_s) has
+       no other entry in an active row, is solved for x_s (when both qualify,
+       x_s is the one with the larger index).  x_s's bounds become bounds on
+       x_f -- x_f = (q - a_s x_s) / a_f for x_s in [l_s, u_s] -- intersected
+       with x_f's own, x_s's cost moves to x_f (c_f -= c_s a_f / a_s, constant
+       c_s q / a_s), and the row and x_s leave the LP;
+    4. every active column with no entry in an active row is fixed at the bound
        its cost prefers (l if c > 0, u if c < 0, else l, u or 0 when finite).
   Surviving rows and columns keep their original order.
 
@@ -65,11 +72,24 @@ class Presolved:
     raw_n: int
     raw_m: int
     fixed: list               # (raw col, value) in the order fixed
-    removed_rows: list        # (raw row, raw col or -1, coef, kind 'E'/'I', tightened)
+    removed_rows: list        # (raw row, raw col or -1, coef, kind 'E'/'I', tightened) or a Doubleton
     raw: LP
 
 
-def presolve(raw: LP) -> Presolved:
+@dataclasses.dataclass
+class Doubleton:
+    """A doubleton equation a_f x_f + a_s x_s = q removed by solving for x_s."""
+    row: int
+    s: int
+    a_s: float
+    f: int
+    a_f: float
+    q: float
+    lo_from_s: bool           # x_f's lower bound came from x_s's bounds
+    hi_from_s: bool           # x_f's upper bound came from x_s's bounds
+
+
+def presolve(raw: LP, aggressive: bool = False) -> Presolved:
     A = raw.A.tocsr()
     n, m = raw.n, raw.m
     l = raw.l.copy()
@@ -81,6 +101,7 @@ def presolve(raw: LP) -> Presolved:
     fixed = []
     removed = []
     xfix = np.zeros(n)
+    c = raw.c.copy()
     Acsc = A.tocsc()
 
     changed = True
@@ -94,7 +115,7 @@ def presolve(raw: LP) -> Presolved:
                     i = Acsc.indices[k]
                     if row_on[i]:
                         q[i] -= Acsc.data[k] * v
-                obj_const += raw.c[j] * v
+                obj_const += c[j] * v
                 xfix[j] = v
                 col_on[j] = False
                 fixed.append((j, v))
@@ -137,7 +158,43 @@ def presolve(raw: LP) -> Presolved:
                 row_on[i] = False
                 removed.append((i, j, a, "E" if is_eq else "I", tightened))
                 changed = True
-        # 3. empty columns
+        # 3. doubleton equations with a column singleton
+        def active_entries(j):
+            return sum(1 for k in range(Acsc.indptr[j], Acsc.indptr[j + 1]) if row_on[Acsc.indices[k]])
+        for i in range(raw.m_eq if aggressive else 0):
+            if not row_on[i]:
+                continue
+            ents = [(A.indices[k], A.data[k]) for k in range(A.indptr[i], A.indptr[i + 1])
+                    if col_on[A.indices[k]]]
+            if len(ents) != 2:
+                continue
+            (j1, a1), (j2, a2) = ents
+            single = [jj for jj in (j1, j2) if active_entries(jj) == 1]
+            if not single:
+                continue
+            js = max(single)
+            (jf, af), (_, a_s) = ((j1, a1), (j2, a2)) if js == j2 else ((j2, a2), (j1, a1))
+            v1 = (q[i] - a_s * l[js]) / af
+            v2 = (q[i] - a_s * u[js]) / af
+            lo, hi = min(v1, v2), max(v1, v2)
+            lo_from = bool(lo > l[jf])
+            hi_from = bool(hi < u[jf])
+            if lo_from:
+                l[jf] = lo
+            if hi_from:
+                u[jf] = hi
+            if l[jf] > u[jf] + 1e-9:
+                raise Infeasible(f"doubleton row {i}: bounds of column {jf} cross")
+            if l[jf] > u[jf]:
+                u[jf] = l[jf]
+            c[jf] = c[jf] - c[js] * af / a_s
+            obj_const += c[js] * q[i] / a_s
+            row_on[i] = False
+            col_on[js] = False
+            removed.append(Doubleton(row=i, s=js, a_s=a_s, f=jf, a_f=af, q=q[i],
+                                     lo_from_s=lo_from, hi_from_s=hi_from))
+            changed = True
+        # 4. empty columns
         for j in range(n):
             if not col_on[j]:
                 continue
@@ -148,7 +205,7 @@ def presolve(raw: LP) -> Presolved:
                     break
             if used:
                 continue
-            cj = raw.c[j]
+            cj = c[j]
             if cj > 0:
                 v = l[j]
             elif cj < 0:
@@ -168,7 +225,7 @@ def presolve(raw: LP) -> Presolved:
     Ared = A[row_map][:, col_map].tocsr()
     Ared.sort_indices()
     m_eq = int(np.count_nonzero(row_map < raw.m_eq))
-    red = LP(A=Ared, q=q[row_map].copy(), c=raw.c[col_map].copy(),
+    red = LP(A=Ared, q=q[row_map].copy(), c=c[col_map].copy(),
              l=l[col_map].copy(), u=u[col_map].copy(), m_eq=m_eq, obj_const=obj_const)
     ps = Presolved(lp=red, col_map=col_map, row_map=row_map, raw_n=n, raw_m=m,
                    fixed=fixed, removed_rows=removed, raw=raw)
@@ -188,13 +245,30 @@ def postsolve(ps: Presolved, x: np.ndarray, y: np.ndarray | None = None):
     raw = ps.raw
     xr = ps._xfix.copy()
     xr[ps.col_map] = x
+    for d in reversed(ps.removed_rows):          # substituted columns, last removed first
+        if isinstance(d, Doubleton):
+            xr[d.s] = (d.q - d.a_f * xr[d.f]) / d.a_s
     if y is None:
         return xr, None
     yr = np.zeros(ps.raw_m)
     yr[ps.row_map] = y
     # reduced costs in the raw LP with the rows known so far
     lam = raw.c - raw.A.T @ yr
-    for (i, j, a, kind, tightened) in reversed(ps.removed_rows):
+    for entry in reversed(ps.removed_rows):
+        if isinstance(entry, Doubleton):
+            d = entry
+            # x_f at a bound that came from x_s's bounds: the row's dual makes
+            # x_f's reduced cost zero (x_s then sits at its bound); otherwise it
+            # makes x_s's zero
+            on_lo = d.lo_from_s and abs(xr[d.f] - ps._tight_l[d.f]) <= 1e-9 * (1 + abs(xr[d.f]))
+            on_hi = d.hi_from_s and abs(xr[d.f] - ps._tight_u[d.f]) <= 1e-9 * (1 + abs(xr[d.f]))
+            if on_lo or on_hi:
+                yr[d.row] = (lam[d.f] + d.a_f * yr[d.row]) / d.a_f
+            else:
+                yr[d.row] = (lam[d.s] + d.a_s * yr[d.row]) / d.a_s
+            lam = raw.c - raw.A.T @ yr
+            continue
+        (i, j, a, kind, tightened) = entry
         if j < 0 or not tightened:
             continue
         if kind == "E":

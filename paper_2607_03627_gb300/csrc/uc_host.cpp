@@ -339,11 +339,13 @@ static int build(const uc_problem *P, RawLp &lp) {
 // Presolve
 // ---------------------------------------------------------------------------
 static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<double> &qr,
-                           std::vector<double> &cr, std::vector<double> &lr, std::vector<double> &ur) {
+                           std::vector<double> &cr, std::vector<double> &lr, std::vector<double> &ur,
+                           bool aggressive) {
     const Csr &A = raw.A;
     const int n = A.cols, m = A.rows;
     Csr AT = transpose(A);
-    std::vector<double> l = raw.l, u = raw.u, q = raw.q;
+    std::vector<double> l = raw.l, u = raw.u, q = raw.q, c = raw.c;
+    ps.aggressive = aggressive;
     std::vector<char> col_on(n, 1), row_on(m, 1);
     ps.xfix.assign(n, 0.0);
     double obj_const = 0.0;
@@ -355,7 +357,7 @@ static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<
             double v = l[j];
             for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1]; k++)
                 if (row_on[AT.colidx[k]]) q[AT.colidx[k]] -= AT.val[k] * v;
-            obj_const += raw.c[j] * v;
+            obj_const += c[j] * v;
             ps.xfix[j] = v;
             col_on[j] = 0;
             changed = true;
@@ -396,12 +398,57 @@ static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<
                 changed = true;
             }
         }
+        // doubleton equations a_f x_f + a_s x_s = q whose x_s has no other entry
+        // in an active row (aggressive presolve): solve for x_s, move its bounds
+        // onto x_f and its cost into x_f's, drop the row and x_s
+        auto active_entries = [&](int j) {
+            int cnt = 0;
+            for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1]; k++) cnt += row_on[AT.colidx[k]];
+            return cnt;
+        };
+        for (int i = 0; aggressive && i < raw.m_eq; i++) {
+            if (!row_on[i]) continue;
+            int cnt = 0, j1 = -1, j2 = -1;
+            double a1 = 0.0, a2 = 0.0;
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                if (!col_on[A.colidx[k]]) continue;
+                if (cnt == 0) { j1 = A.colidx[k]; a1 = A.val[k]; }
+                else { j2 = A.colidx[k]; a2 = A.val[k]; }
+                cnt++;
+            }
+            if (cnt != 2) continue;
+            const bool s1 = active_entries(j1) == 1, s2 = active_entries(j2) == 1;
+            if (!s1 && !s2) continue;
+            const int js = (s1 && s2) ? std::max(j1, j2) : (s1 ? j1 : j2);
+            const int jf = js == j1 ? j2 : j1;
+            const double as = js == j1 ? a1 : a2, af = js == j1 ? a2 : a1;
+            const double v1 = (q[i] - as * l[js]) / af, v2 = (q[i] - as * u[js]) / af;
+            const double lo = std::min(v1, v2), hi = std::max(v1, v2);
+            const bool lo_from = lo > l[jf], hi_from = hi < u[jf];
+            if (lo_from) l[jf] = lo;
+            if (hi_from) u[jf] = hi;
+            if (l[jf] > u[jf] + tol) { set_error("presolve: doubleton row %d crosses the bounds of column %d", i, jf); return UC_EINFEASIBLE; }
+            if (l[jf] > u[jf]) u[jf] = l[jf];
+            c[jf] = c[jf] - c[js] * af / as;
+            obj_const += c[js] * q[i] / as;
+            row_on[i] = 0;
+            col_on[js] = 0;
+            RemovedRow r{i, js, as, true, false};
+            r.doubleton = true;
+            r.f = jf;
+            r.a_f = af;
+            r.q = q[i];
+            r.lo_from_s = lo_from;
+            r.hi_from_s = hi_from;
+            ps.removed.push_back(r);
+            changed = true;
+        }
         for (int j = 0; j < n; j++) {                        // empty columns
             if (!col_on[j]) continue;
             bool used = false;
             for (int32_t k = AT.rowptr[j]; k < AT.rowptr[j + 1] && !used; k++) used = row_on[AT.colidx[k]];
             if (used) continue;
-            double cj = raw.c[j], v;
+            double cj = c[j], v;
             if (cj > 0) v = l[j];
             else if (cj < 0) v = u[j];
             else v = std::isfinite(l[j]) ? l[j] : (std::isfinite(u[j]) ? u[j] : 0.0);
@@ -428,7 +475,7 @@ static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<
     }
     ps.m_eq = 0;
     for (int32_t i : ps.row_map) ps.m_eq += (i < raw.m_eq);
-    for (int32_t j : ps.col_map) { cr.push_back(raw.c[j]); lr.push_back(l[j]); ur.push_back(u[j]); }
+    for (int32_t j : ps.col_map) { cr.push_back(c[j]); lr.push_back(l[j]); ur.push_back(u[j]); }
     ps.l_tight = l;
     ps.u_tight = u;
     ps.obj_const = obj_const;
@@ -609,11 +656,13 @@ void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector
     const RawLp &raw = *ps.raw;
     x = ps.xfix;
     for (size_t k = 0; k < ps.col_map.size(); k++) x[ps.col_map[k]] = ps.Dc[k] * xs[k];
+    for (auto it = ps.removed.rbegin(); it != ps.removed.rend(); ++it)   // substituted columns
+        if (it->doubleton) x[it->col] = (it->q - it->a_f * x[it->f]) / it->a;
     y.assign(raw.A.rows, 0.0);
     if (!ys) return;
     for (size_t k = 0; k < ps.row_map.size(); k++) y[ps.row_map[k]] = ps.Dr[k] * ys[k];
     bool any = false;
-    for (auto &r : ps.removed) any |= (r.col >= 0 && r.tightened);
+    for (auto &r : ps.removed) any |= (r.col >= 0 && (r.tightened || r.doubleton));
     if (!any) return;
     Csr AT = transpose(raw.A);
     auto redcost = [&](int j) {
@@ -622,6 +671,17 @@ void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector
         return s;
     };
     for (auto it = ps.removed.rbegin(); it != ps.removed.rend(); ++it) {
+        if (it->doubleton) {
+            // x_f at a bound that came from x_s's bounds: the row's dual zeroes
+            // x_f's reduced cost (x_s then sits at its bound); otherwise x_s's
+            const int f = it->f;
+            const double tf = 1e-9 * (1.0 + std::fabs(x[f]));
+            const bool on = (it->lo_from_s && std::fabs(x[f] - ps.l_tight[f]) <= tf) ||
+                            (it->hi_from_s && std::fabs(x[f] - ps.u_tight[f]) <= tf);
+            const double yi = y[it->row];
+            y[it->row] = on ? (redcost(f) + it->a_f * yi) / it->a_f : (redcost(it->col) + it->a * yi) / it->a;
+            continue;
+        }
         if (it->col < 0 || !it->tightened) continue;
         int j = it->col;
         double lam = redcost(j);
@@ -719,11 +779,12 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
     if (o.value_bits != 64 && o.value_bits != 32) { set_error("uc_presolve: value_bits must be 32 or 64"); return UC_EINVAL; }
     if (o.ruiz_iters < 0 || o.power_max_iter < 1) { set_error("uc_presolve: bad iteration counts"); return UC_EINVAL; }
     if (o.power_device != 0 && o.power_device != 1) { set_error("uc_presolve: power_device must be 0 or 1"); return UC_EINVAL; }
+    if (o.aggressive != 0 && o.aggressive != 1) { set_error("uc_presolve: aggressive must be 0 or 1"); return UC_EINVAL; }
     int threads = o.threads > 0 ? o.threads : (int)std::max(1u, std::thread::hardware_concurrency());
     try {
         auto ps = std::make_shared<PsData>();
         ps->raw = lp->d;
-        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u);
+        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, o.aggressive != 0);
         if (rc) return rc;
         ps->raw_reduced_val = ps->A.val;
         double qi = 0.0, ci = 0.0;
@@ -771,7 +832,7 @@ int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **
     try {
         auto ps = std::make_shared<PsData>();
         ps->raw = lp->d;
-        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u);
+        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, b.aggressive);
         if (rc) return rc;
         if (ps->col_map != b.col_map || ps->row_map != b.row_map || ps->A.val != b.raw_reduced_val) {
             set_error("uc_presolve_reuse: presolve removed different rows or columns than for the base LP");

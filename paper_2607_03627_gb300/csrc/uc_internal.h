@@ -39,10 +39,16 @@ struct RawLp {
 
 struct RemovedRow {
     int row;          // raw row
-    int col;          // raw column of a singleton row, -1 for an empty row
+    int col;          // raw column of a singleton row, -1 for an empty row; the
+                      // substituted column s of a doubleton equation
     double a;         // its coefficient
     bool eq;
     bool tightened;   // the row moved a bound
+    // doubleton equation a_f x_f + a x_s = q solved for x_s (aggressive presolve)
+    bool doubleton = false;
+    int f = -1;
+    double a_f = 0.0, q = 0.0;
+    bool lo_from_s = false, hi_from_s = false;   // x_f's bound came from x_s's
 };
 
 // Everything the device solve and the postsolve need.
@@ -61,7 +67,8 @@ struct PsData {
     std::vector<RemovedRow> removed;
     std::vector<double> raw_reduced_val;   // reduced matrix values before scaling
     double eta = 1.0, omega0 = 1.0, norm_A = 0.0, obj_const = 0.0;
-    double norm_bound = 0.0;               // max(certified upper bound, norm_A); eta = 0.998 / it
+    double norm_bound = 0.0;
+    bool aggressive = false;               // presolve substituted doubleton equations               // max(certified upper bound, norm_A); eta = 0.998 / it
     double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
     int value_bits = 64;
     int n() const { return A.cols; }

@@ -193,3 +193,31 @@ def test_warm_start_with_primal_weight_per_iterate(B):
         res, rc = B.uc_solve(ps, tol=0.0, max_iter=K, warm_x=x0, warm_y=y0, warm_omega=ref_sol.omega)
         x, y = B.uc_get_iterate(res, 0, n, m)
         assert rel_inf(x, out[K][0]) <= ITERATE_RTOL and rel_inf(y, out[K][1]) <= ITERATE_RTOL, K
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_aggressive_presolve_parity_and_gates(B, seed):
+    # the device solve of the aggressively presolved LP (doubleton equations
+    # substituted) follows the oracle's PDHG on its own aggressive presolve
+    # and meets the gates on the raw LP after the doubleton postsolve
+    from oracle import presolve as ops
+    g = golden_tiny()
+    P = ucgen.tiny(seed)
+    raw = olp.build_lp(P)
+    ps_o = ops.presolve(raw, aggressive=True)
+    S = ops.scale(ps_o.lp)
+    ref = oracle_trace(S, [1, 64, 65, 200])
+    ps = B.uc_presolve(B.uc_build_lp(P), aggressive=1)
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    assert (n, m) == (ps_o.lp.n, ps_o.lp.m)
+    for K in (1, 64, 65, 200):
+        x, y, st = _device_iterates(B, ps, n, m, K)
+        xo, yo, restarts, omega, _, _ = ref[K]
+        assert st["restarts"] == restarts
+        assert rel_inf(x, xo) <= ITERATE_RTOL and rel_inf(y, yo) <= ITERATE_RTOL, K
+    res, rc = B.uc_solve(ps, tol=KKT_TOL)
+    assert rc == B.UC_OK
+    xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+    assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+    opt = g["objective_by_seed"][str(seed)]
+    assert abs(raw_objective(raw, xr) - opt) / max(1.0, abs(opt)) <= OBJ_GAP_TOL

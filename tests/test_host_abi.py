@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import ucgen
-from oracle import lp as olp, presolve as ops
+from oracle import kkt, lp as olp, presolve as ops
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -57,11 +57,12 @@ def test_builder_matches_oracle_exactly(B, P):
         np.testing.assert_array_equal(d[k], getattr(ref, k))
 
 
+@pytest.mark.parametrize("aggressive", [0, 1], ids=["default", "aggressive"])
 @pytest.mark.parametrize("P", list(_problems()), ids=lambda P: P.name or "strict")
-def test_presolve_and_scaling_match_oracle(B, P):
-    ps_o = ops.presolve(olp.build_lp(P))
+def test_presolve_and_scaling_match_oracle(B, P, aggressive):
+    ps_o = ops.presolve(olp.build_lp(P), aggressive=bool(aggressive))
     S = ops.scale(ps_o.lp)
-    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P)))
+    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P), aggressive=aggressive))
     assert (d["n"], d["m"], d["m_eq"]) == (ps_o.lp.n, ps_o.lp.m, ps_o.lp.m_eq)
     np.testing.assert_array_equal(d["col_map"], ps_o.col_map)
     np.testing.assert_array_equal(d["row_map"], ps_o.row_map)
@@ -328,3 +329,23 @@ def test_presolve_reuse_equals_a_full_presolve_on_the_host(B, which):
         assert re[k] == full[k], k
     with pytest.raises(B.UCError, match="matrix differs"):
         B.uc_presolve_reuse(ps0, B.uc_build_lp(ucgen.tiny(4) if which == "tiny" else ucgen.tiny(0)))
+
+
+def test_aggressive_postsolve_matches_oracle(B):
+    # the host postsolve of a point of the aggressively presolved 30-bus LP (the
+    # oracle simplex optimum of that LP) equals the oracle's: substituted shed
+    # columns and the duals of the removed doubleton rows included
+    from oracle import simplex
+    P = ucgen.tiny(0)
+    raw = olp.build_lp(P)
+    ps_o = ops.presolve(raw, aggressive=True)
+    assert any(isinstance(d, ops.Doubleton) for d in ps_o.removed_rows)
+    S = ops.scale(ps_o.lp)
+    r = simplex.solve_lp(ps_o.lp)
+    xo, yo = ops.postsolve(ps_o, r.x, r.y)
+    ps = B.uc_presolve(B.uc_build_lp(P), aggressive=1)
+    res = B.uc_result_from_point(ps, r.x / S.Dc, r.y / S.Dr)
+    xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+    np.testing.assert_allclose(xr, xo, rtol=1e-9, atol=1e-9 * np.max(np.abs(xo)))
+    np.testing.assert_allclose(yr, yo, rtol=1e-9, atol=1e-9 * np.max(np.abs(yo)))
+    assert max(kkt.relative_kkt(raw, xr, yr)) <= 1e-8

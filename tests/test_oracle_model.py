@@ -98,15 +98,28 @@ def test_kkt_sign_conventions():
     assert r.rd[0] == -2.0 and r.rd[1] == -1.0  # lower-bounded columns need lam >= 0
 
 
+@pytest.mark.parametrize("aggressive", [False, True], ids=["default", "aggressive"])
 @pytest.mark.parametrize("seed", range(3))
-def test_presolve_preserves_optimum(seed):
+def test_presolve_preserves_optimum(seed, aggressive):
     P = ucgen.make_problem(seed, B=10, L=13, G=5, T=4, lo=0.4, hi=0.8, noise=0.05,
                            zero_pmin_frac=0.4)
     raw = olp.build_lp(P)
-    ps = ops.presolve(raw)
-    assert ps.lp.n == raw.n - P.T                      # theta_ref fixed each period
+    ps = ops.presolve(raw, aggressive=aggressive)
+    # doubleton equations (aggressive presolve): the balance row of a bus with one line and no unit
+    # holds that line's flow and the bus's shed column only; the shed column
+    # (a column singleton) is solved for, in every period
+    deg = np.bincount(np.concatenate([P.line_from, P.line_to]), minlength=P.B)
+    units = np.bincount(P.gen_bus, minlength=P.B)
+    leaf = np.flatnonzero((deg == 1) & (units == 0))
+    dbl = [d for d in ps.removed_rows if isinstance(d, ops.Doubleton)]
+    assert len(dbl) == (P.T * len(leaf) if aggressive else 0)
+    for d in dbl:
+        assert raw.row_kind[d.row] == olp.ROW_BAL and raw.row_idx[d.row] in leaf
+        assert raw.col_kind[d.s] == olp.COL_S and raw.col_idx[d.s] == raw.row_idx[d.row]
+        assert raw.col_kind[d.f] == olp.COL_F
+    assert ps.lp.n == raw.n - P.T - len(dbl)           # theta_ref fixed each period
     n_zero = int(np.count_nonzero(P.pmin == 0.0))
-    assert ps.lp.m == raw.m - P.T * n_zero              # p >= 0 singleton rows
+    assert ps.lp.m == raw.m - P.T * n_zero - len(dbl)   # p >= 0 singleton rows
     r_raw = simplex.solve_lp(raw)
     r_red = simplex.solve_lp(ps.lp)
     assert r_raw.status == r_red.status == "optimal"
@@ -208,3 +221,21 @@ def test_commitment_enumeration_equals_lp_when_integral():
     assert np.allclose(sol["u"], np.round(sol["u"]), atol=1e-9)
     mip_opt, _ = brute.commitment_enum(P)
     assert abs(mip_opt - r.obj) <= 1e-9 * abs(r.obj)
+
+
+def test_aggressive_presolve_on_the_30_bus_lp():
+    # doubleton equations at every leaf bus without units; the reduced LP has the
+    # raw optimum, and postsolve recovers primal and dual points that are
+    # KKT-optimal on the raw LP (the recovered rows' duals included)
+    P = ucgen.tiny(0)
+    raw = olp.build_lp(P)
+    base = ops.presolve(raw)
+    ps = ops.presolve(raw, aggressive=True)
+    dbl = [d for d in ps.removed_rows if isinstance(d, ops.Doubleton)]
+    assert len(dbl) > 0 and ps.lp.n == base.lp.n - len(dbl) and ps.lp.m == base.lp.m - len(dbl)
+    r_raw = simplex.solve_lp(raw)
+    r_red = simplex.solve_lp(ps.lp)
+    assert abs(r_raw.obj - r_red.obj) <= 1e-9 * abs(r_raw.obj)
+    xr, yr = ops.postsolve(ps, r_red.x, r_red.y)
+    assert max(kkt.relative_kkt(raw, xr, yr)) <= 1e-8
+    assert abs(float(raw.c @ xr) - r_raw.obj) <= 1e-9 * abs(r_raw.obj)
