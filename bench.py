@@ -726,7 +726,7 @@ def main():
     ap.add_argument("--cta-rows", type=int, default=0, help="threads per CTA of the iteration kernels (0: 128)")
     ap.add_argument("--rows-per-thread", type=int, default=0,
                     help="row split of the iteration kernels (0: autotuned, else 1, 2 or 4)")
-    ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr"])
+    ap.add_argument("--restart-metric", default="kkt", choices=["kkt", "fpr", "fprp"])
     ap.add_argument("--aggressive", action="store_true",
                     help="paper configs: aggressive presolve (doubleton equations substituted)")
     ap.add_argument("--no-polish", action="store_true",

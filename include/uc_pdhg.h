@@ -142,7 +142,9 @@ typedef struct {
     int algorithm;               /* 0 (default): restarted reflected Halpern PDHG; 1: PDLP iterate
                                     averaging with KKT restarts (both with constant step sizes) */
     int restart_metric;          /* Halpern restarts: 0 (default) weighted KKT of the map output,
-                                    1 fixed-point residual of the last step */
+                                    1 fixed-point residual of the last step, sqrt(omega |dx|^2 +
+                                    |dy|^2 / omega); 2 that residual in the norm of the PDHG map's
+                                    metric, sqrt(omega |dx|^2 + |dy|^2 / omega - 2 eta dy.A dx) */
     const volatile int *cancel;  /* nullable; a nonzero value (set from another thread) stops the
                                     solve at its next replay boundary with UC_ECANCELLED -- the
                                     "terminate the other solver" step of Alg. 1 */

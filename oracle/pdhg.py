@@ -51,13 +51,17 @@ constant step.  With T the PDHG map above and z = (x, y):
           z <- w (2 z_hat - z) + (1 - w) z0,   w = (j+1)/(j+2)
           (full reflection; z0 = anchor of the current restart epoch)
   every n_eval steps: relative KKT of z_hat (the last map output) -> stop;
-          restart metric r = KKT_omega(z_hat) ("kkt") or the fixed-point
+          restart metric r = KKT_omega(z_hat) ("kkt"), the fixed-point
           residual sqrt(omega ||x_in - x_hat||^2 + ||y_in - y_hat||^2 / omega)
-          of the last step ("fpr"); the same three restart tests with r in
+          of the last step ("fpr"), or that residual in the norm of the PDHG
+          map's metric, sqrt(omega ||dx||^2 + ||dy||^2 / omega - 2 eta dy.A dx)
+          with (dx, dy) = z_in - z_hat ("fprp": eta times the squared norm
+          ||dx||^2 / tau + ||dy||^2 / sigma - 2 dy.A dx, in which the PDHG map
+          is nonexpansive); the same three restart tests with r in
           place of KKT_c and r_anchor in place of KKT_anchor;
           on restart: omega from dx = ||x_hat - x0||, dy = ||y_hat - y0||,
           z = z0 = z_hat, j = 0, r_anchor = r re-weighted with the new omega.
-The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr".
+The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr" and "fprp".
 
 Primal feasibility polishing (after a solve that met the relative KKT
 tolerance).  The paper's PDHG runs with an absolute feasibility tolerance of
@@ -422,10 +426,13 @@ def halpern_evaluate(S, st: HState, U, tol: float, stop_abs=None):
     w = st.omega
     fx2 = float(np.dot(st.x_in - st.xh, st.x_in - st.xh))
     fy2 = float(np.dot(st.y_in - st.yh, st.y_in - st.yh))
+    cross = 0.0
+    if st.metric == "fprp":
+        cross = float(np.dot(st.y_in - st.yh, S.A @ (st.x_in - st.xh)))
     if st.metric == "kkt":
         r, parts = weighted(S, st.xh, st.yh, w)
     else:
-        r = math.sqrt(w * fx2 + fy2 / w)
+        r = math.sqrt(max(w * fx2 + fy2 / w - 2.0 * S.eta * cross, 0.0))
     if restart_decision(r, st.r_anchor, st.r_prev, st.j, st.k):
         dx = float(np.linalg.norm(st.xh - st.x0))
         dy = float(np.linalg.norm(st.yh - st.y0))
@@ -436,7 +443,7 @@ def halpern_evaluate(S, st: HState, U, tol: float, stop_abs=None):
         st.x0 = st.x.copy()
         st.y0 = st.y.copy()
         st.r_anchor = (kkt.weighted_kkt(parts[0], parts[1], parts[2], wn) if st.metric == "kkt"
-                       else math.sqrt(wn * fx2 + fy2 / wn))
+                       else math.sqrt(max(wn * fx2 + fy2 / wn - 2.0 * S.eta * cross, 0.0)))
         st.r_prev = math.inf
         st.j = 0
         st.tau = S.eta / wn

@@ -366,7 +366,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
         keep.append(rp)
         o.rows_per_thread = _ptr(rp, C.c_int32)
     o.algorithm = {"halpern": 0, "average": 1}[algorithm]
-    o.restart_metric = {"kkt": 0, "fpr": 1}[restart_metric]
+    o.restart_metric = {"kkt": 0, "fpr": 1, "fprp": 2}[restart_metric]
     if warm_x is not None:
         wx = _f64(warm_x); keep.append(wx); o.warm_x = _ptr(wx, C.c_double)
     if warm_y is not None:

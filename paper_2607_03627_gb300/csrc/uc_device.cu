@@ -56,7 +56,7 @@ constexpr int kInfeasEvery = 4;
 constexpr double kInfeasEps = 1e-8;
 enum Action { ACT_NONE = 0, ACT_RESTART = 1, ACT_FINISH = 2 };
 enum Algo { ALG_HALPERN = 0, ALG_AVERAGE = 1 };
-enum Metric { METRIC_KKT = 0, METRIC_FPR = 1 };
+enum Metric { METRIC_KKT = 0, METRIC_FPR = 1, METRIC_FPRP = 2 };
 
 // Per-LP solver state, resident in device memory and only changed by k_control.
 struct Scalars {
@@ -69,7 +69,7 @@ struct Scalars {
     double inv_j;                                    // 1 / iterations averaged at the last evaluation
     int restarts, evals;
     int algo;        // ALG_HALPERN or ALG_AVERAGE
-    int metric;      // Halpern restart metric: METRIC_KKT or METRIC_FPR
+    int metric;      // Halpern restart metric: METRIC_KKT, METRIC_FPR or METRIC_FPRP
     // adaptive step size (averaging variant): trial step, weight of the last
     // attempt (its step if accepted, else 0), step-weighted sum since the
     // restart, buffer of the current iterate, accepted attempts
@@ -998,7 +998,10 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                                   : (S->status == RUNNING && S->k_base + S->n_eval <= S->max_iter);
     if (live) {
         const bool halp = S->algo == ALG_HALPERN && mode == 1;
-        const bool fpr = halp && S->metric == METRIC_FPR;   // fixed-point residual terms needed
+        const bool fpr = halp && S->metric != METRIC_KKT;   // fixed-point residual terms needed
+        // the PDHG-norm residual also needs (y_in - y_hat).A (x_in - x_hat), summed
+        // in candidate 1's CX slot (unused by the Halpern variant)
+        const bool fprp = halp && S->metric == METRIC_FPRP;
         // infeasibility direction dy = y_hat - y_in: q.dy in slot QY, the bound part
         // of its objective in BND, the y_I < 0 and reduced-cost cone violations
         // (unscaled) as maxima in RPU and RDU, all of the second record
@@ -1021,12 +1024,13 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
         if (rows) {
             const VT *__restrict__ v = static_cast<const VT *>(b.A_v);
             for (int i = sg.begin + threadIdx.x; i < sg.end; i += kThreads) {
-                double ax0 = 0.0, ax1 = 0.0;
+                double ax0 = 0.0, ax1 = 0.0, axin = 0.0;
                 for (int k = b.A_rp[i]; k < b.A_rp[i + 1]; k++) {
                     const size_t j = at(b.A_ci[k]);
                     const double a = widen(v[k]);
                     ax0 += a * x[j];
                     if (avg) ax1 += a * (xav[j] * inv_j);
+                    if (fprp) axin += a * b.x[1][j];
                 }
                 const size_t ii = at(i);
                 const double qi = b.q[ii], idr = b.inv_Dr[ii], yh = b.ya[ii];
@@ -1049,6 +1053,7 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
                 } else if (fpr) {
                     const double d = b.y[1][ii] - y0;
                     acc[kSlots + DY2] += d * d;
+                    if (fprp) acc[kSlots + CX] += d * (axin - ax0);
                 }
                 if (ray) {
                     const double dy = y0 - b.y[1][ii];
@@ -1182,7 +1187,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
         rel[cnd][2] = fabs(gap[cnd]) / (1.0 + fabs(pobj[cnd]) + fabs(dobj[cnd]));
     }
     if (mode == 0) {                     // initial anchor (no residual yet for the fixed-point metric)
-        S->kkt_anchor = (S->algo == ALG_HALPERN && S->metric == METRIC_FPR) ? INFINITY : K[0];
+        S->kkt_anchor = (S->algo == ALG_HALPERN && S->metric != METRIC_KKT) ? INFINITY : K[0];
         S->kkt_prev = INFINITY;
         S->rel_p = rel[0][0]; S->rel_d = rel[0][1]; S->rel_g = rel[0][2];
         S->abs_p = T[RPU]; S->pobj = pobj[0]; S->dobj = dobj[0];
@@ -1226,7 +1231,8 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
                 return;
             }
         }
-        const double r = (S->metric == METRIC_KKT) ? K[0] : sqrt(w * fx2 + fy2 / w);
+        const double cross = (S->metric == METRIC_FPRP) ? T[kSlots + CX] : 0.0;
+        const double r = (S->metric == METRIC_KKT) ? K[0] : sqrt(fmax(w * fx2 + fy2 / w - 2.0 * S->eta * cross, 0.0));
         const bool restart = (r <= 0.2 * S->kkt_anchor) ||
                              (r <= 0.8 * S->kkt_anchor && r > S->kkt_prev) ||
                              ((double)j >= 0.36 * (double)k);
@@ -1235,7 +1241,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
             const double wn = primal_weight(S, w, dx, dy);
             S->omega = wn;
             S->kkt_anchor = (S->metric == METRIC_KKT) ? kkt_w(T[RP2], T[RD2], gap[0], wn)
-                                                      : sqrt(wn * fx2 + fy2 / wn);
+                                                      : sqrt(fmax(wn * fx2 + fy2 / wn - 2.0 * S->eta * cross, 0.0));
             S->kkt_prev = INFINITY;
             S->j_base = 0;
             S->restarts += 1;
@@ -2334,8 +2340,8 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
         set_error("stages must be 0 or 2..%d", kStMaxStages);
         return UC_EINVAL;
     }
-    if (o.algorithm < 0 || o.algorithm > 1 || o.restart_metric < 0 || o.restart_metric > 1) {
-        set_error("algorithm and restart_metric must be 0 or 1");
+    if (o.algorithm < 0 || o.algorithm > 1 || o.restart_metric < 0 || o.restart_metric > 2) {
+        set_error("algorithm must be 0 or 1 and restart_metric 0, 1 or 2");
         return UC_EINVAL;
     }
     X->algo = o.algorithm;

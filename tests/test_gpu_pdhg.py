@@ -34,7 +34,7 @@ def _device_iterates(B, ps, n, m, K, **kw):
 KS = [1, 2, 3, 17, 63, 64, 65, 127, 128, 129, 191, 192, 193, 200]
 
 
-VARIANTS = [("halpern", "kkt"), ("halpern", "fpr"), ("average", "kkt")]
+VARIANTS = [("halpern", "kkt"), ("halpern", "fpr"), ("halpern", "fprp"), ("average", "kkt")]
 
 
 @pytest.mark.parametrize("variant,metric", VARIANTS)

@@ -131,7 +131,25 @@ def _check_restart_lands_on_fixed_point(evaluate):
         pdhg.halpern_step(S, st, AT)
 
 
-PINS = [_check_restart_fpr, _check_restart_kkt, _check_no_restart, _check_restart_lands_on_fixed_point]
+# The PDHG-norm residual ("fprp"): dx = x_in - x_hat = (0, 3), dy = y_in - y_hat = 4,
+# A dx = 3, so dy.A dx = 12; without scaling eta = 0.998 / sqrt(||A||_1 ||A||_inf)
+# = 0.998 / sqrt(2).  r_omega = sqrt(omega 9 + 16 / omega - 24 eta).
+def _check_fprp(evaluate):
+    S = _one_row_lp()
+    eta = 0.998 / math.sqrt(2.0)
+    assert S.eta == pytest.approx(eta, rel=1e-15)
+    st = _state(S, "fprp", omega=4.0, r_anchor=5.0, r_prev=math.inf, j=10, k=64)
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.restarts == 0
+    assert st.r_prev == pytest.approx(math.sqrt(36.0 + 4.0 - 24.0 * eta), rel=1e-14)
+    st = _state(S, "fprp", omega=1.0, r_anchor=100.0, r_prev=math.inf, j=10, k=64)
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.restarts == 1 and st.omega == pytest.approx(2.0, rel=1e-14)
+    assert st.r_anchor == pytest.approx(math.sqrt(18.0 + 8.0 - 24.0 * eta), rel=1e-14)
+
+
+PINS = [_check_restart_fpr, _check_restart_kkt, _check_no_restart, _check_restart_lands_on_fixed_point,
+        _check_fprp]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__[7:])
@@ -145,8 +163,10 @@ MUTANTS = {
     "movement measured from z, not z0": [("np.linalg.norm(st.xh - st.x0)", "np.linalg.norm(st.xh - st.x)")],
     "movement measured from the step input": [("np.linalg.norm(st.yh - st.y0)", "np.linalg.norm(st.yh - st.y_in)")],
     "anchor value with the old weight (kkt)": [("parts[2], wn)", "parts[2], w)")],
-    "anchor value with the old weight (fpr)": [("math.sqrt(wn * fx2 + fy2 / wn)", "math.sqrt(w * fx2 + fy2 / w)")],
-    "weight on the wrong block of the residual": [("math.sqrt(w * fx2 + fy2 / w)", "math.sqrt(fx2 / w + w * fy2)")],
+    "anchor value with the old weight (fpr)": [("max(wn * fx2 + fy2 / wn", "max(w * fx2 + fy2 / w")],
+    "weight on the wrong block of the residual": [("max(w * fx2 + fy2 / w", "max(fx2 / w + w * fy2")],
+    "cross term of the PDHG norm dropped": [("cross = float(np.dot(", "cross = 0.0 * float(np.dot(")],
+    "cross term with the wrong sign": [("fy2 / w - 2.0 * S.eta * cross", "fy2 / w + 2.0 * S.eta * cross")],
     "r_prev left unchanged": [("st.r_prev = r\n", "st.r_prev = st.r_prev\n")],
     "j not reset": [("st.j = 0", "st.j = st.j")],
     "primal weight rule inverted": [("primal_weight_update(w, dx, dy, st.pw)", "primal_weight_update(w, dy, dx, st.pw)")],

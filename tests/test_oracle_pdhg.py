@@ -158,7 +158,7 @@ def test_first_evaluation_restarts():
 # ---------------------------------------------------------------------------
 # Halpern variant (the default)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("metric", ["kkt", "fpr"])
+@pytest.mark.parametrize("metric", ["kkt", "fpr", "fprp"])
 @pytest.mark.parametrize("seed", range(3))
 def test_halpern_reaches_simplex_objective(seed, metric):
     P = ucgen.make_problem(seed, B=12, L=16, G=4, T=6, lo=0.4, hi=0.8, noise=0.05,
