@@ -32,6 +32,7 @@
 #include <functional>
 #include <limits>
 #include <queue>
+#include <thread>
 #include <vector>
 
 #include "uc_internal.h"
@@ -1679,6 +1680,26 @@ static std::vector<int32_t> entity_order(int begin, int end, const std::vector<i
     bool ok = ent.size() == nraw && per.size() == nraw && (int64_t)map.size() >= end;
     for (int r = begin; ok && r < end; r++) ok = map[r] >= 0 && (size_t)map[r] < nraw;
     if (!ok) return o;
+    // the (kind, entity, period) label packed into one ordered 64-bit key (kind:
+    // 8 bits, entity: 32, period: 24); labels of one LP are distinct, so sorting
+    // (key, index) pairs gives the order of a stable sort by label
+    bool packable = true;
+    std::vector<std::pair<uint64_t, int32_t>> kv;
+    kv.reserve(o.size());
+    for (int32_t r : o) {
+        const int32_t rr = map[r];
+        packable &= kind[rr] >= 0 && ent[rr] >= 0 && per[rr] >= 0 && per[rr] < (1 << 24);
+        kv.push_back({((uint64_t)(uint8_t)kind[rr] << 56) | ((uint64_t)(uint32_t)ent[rr] << 24) | (uint64_t)per[rr], r});
+    }
+    if (packable) {
+        std::sort(kv.begin(), kv.end());
+        bool distinct = true;
+        for (size_t t = 1; t < kv.size() && distinct; t++) distinct = kv[t].first != kv[t - 1].first;
+        if (distinct) {
+            for (size_t t = 0; t < kv.size(); t++) o[t] = kv[t].second;
+            return o;
+        }
+    }
     std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) {
         const int32_t ra = map[a], rb = map[b];
         if (kind[ra] != kind[rb]) return kind[ra] < kind[rb];
@@ -1686,6 +1707,21 @@ static std::vector<int32_t> entity_order(int begin, int end, const std::vector<i
         return per[ra] < per[rb];
     });
     return o;
+}
+
+// Run three independent host tasks at once; an exception in any of them
+// (out of host memory) is rethrown on the calling thread after all end.
+template <typename F1, typename F2, typename F3>
+static void parallel3(F1 &&f1, F2 &&f2, F3 &&f3) {
+    std::exception_ptr e1, e2;
+    std::thread t1([&] { try { f1(); } catch (...) { e1 = std::current_exception(); } });
+    std::thread t2([&] { try { f2(); } catch (...) { e2 = std::current_exception(); } });
+    std::exception_ptr e3;
+    try { f3(); } catch (...) { e3 = std::current_exception(); }
+    t1.join();
+    t2.join();
+    for (auto &e : {e1, e2, e3})
+        if (e) std::rethrow_exception(e);
 }
 
 static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsData> &src, bool reorder,
@@ -1702,9 +1738,12 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     }
     static const RawLp kNoLabels;
     const RawLp &R = p.raw ? *p.raw : kNoLabels;
-    window_order(p.A.rowptr, entity_order(0, p.m_eq, p.row_map, R.row_kind, R.row_idx, R.row_t), prow);
-    window_order(p.A.rowptr, entity_order(p.m_eq, m, p.row_map, R.row_kind, R.row_idx, R.row_t), prow);
-    window_order(p.AT.rowptr, entity_order(0, n, p.col_map, R.col_kind, R.col_idx, R.col_t), pcol);
+    // the three orders are independent: equality rows, ">=" rows, columns (host threads)
+    std::vector<int32_t> prow_ge;
+    parallel3([&] { window_order(p.A.rowptr, entity_order(0, p.m_eq, p.row_map, R.row_kind, R.row_idx, R.row_t), prow); },
+              [&] { window_order(p.A.rowptr, entity_order(p.m_eq, m, p.row_map, R.row_kind, R.row_idx, R.row_t), prow_ge); },
+              [&] { window_order(p.AT.rowptr, entity_order(0, n, p.col_map, R.col_kind, R.col_idx, R.col_t), pcol); });
+    prow.insert(prow.end(), prow_ge.begin(), prow_ge.end());
     std::vector<int32_t> irow(m), icol(n);
     for (int i = 0; i < m; i++) irow[prow[i]] = i;
     for (int j = 0; j < n; j++) icol[pcol[j]] = j;
@@ -1729,8 +1768,8 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
             out.rowptr.push_back((int32_t)out.colidx.size());
         }
     };
-    permute_csr(p.A, p.A_val32, prow, icol, d->A, d->A_val32);
-    permute_csr(p.AT, p.AT_val32, pcol, irow, d->AT, d->AT_val32);
+    parallel3([&] { permute_csr(p.A, p.A_val32, prow, icol, d->A, d->A_val32); },
+              [&] { permute_csr(p.AT, p.AT_val32, pcol, irow, d->AT, d->AT_val32); }, [] {});
     auto gather = [](const std::vector<double> &v, const std::vector<int32_t> &order) {
         std::vector<double> o(order.size());
         for (size_t t = 0; t < order.size(); t++) o[t] = v[order[t]];
