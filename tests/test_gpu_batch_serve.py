@@ -170,3 +170,31 @@ def test_mixed_server_admits_by_hbm_budget(B):
     sess = B.Session([ps], tol=KKT_TOL)
     assert sess.device_bytes() <= session_bytes_estimate(ps)
     sess.close()
+
+
+MID_SEEDS = [5, 6, 11, 18, 27, 40, 52, 57]   # batch recipe, 456 to 1,438 buses, T 24 and 48
+
+
+@pytest.mark.slow
+def test_batch_of_uneven_mid_size_lps_meets_the_kkt_gate(B):
+    # eight LPs of the batch recipe (300-1,500 buses) in one block-diagonal
+    # session with uneven row splits: every result's KKT is re-evaluated by the
+    # oracle on its own presolve, and one of them equals its single solve bit for bit
+    probs = [ucgen.batch_member(s) for s in MID_SEEDS]
+    pss = [B.uc_presolve(B.uc_build_lp(P)) for P in probs]
+    results, rc = B.uc_solve_batch(pss, tol=KKT_TOL, rows_per_thread=[1, 2, 1, 4, 2, 1, 2, 1])
+    assert rc == B.UC_OK
+    for P, r in zip(probs, results):
+        raw, ps_o, _ = oracle_pipeline(P)
+        xr, yr = B.uc_get_raw_solution(r, raw.n, raw.m)
+        assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6), P.name
+        sol = B.uc_get_solution(r, P.T, P.B, P.L, P.G)
+        bal = sol["p"].sum(axis=1) + sol["shed"].sum(axis=1) - P.load.sum(axis=1)
+        assert np.max(np.abs(bal)) <= P.B * KKT_TOL * (1 + np.max(np.abs(ps_o.lp.q))), P.name
+    n, m, _, _ = B.uc_presolved_dims(pss[3])
+    single, _ = B.uc_solve(pss[3], tol=KKT_TOL)
+    for which in (0, 2):
+        xa, ya = B.uc_get_iterate(single, which, n, m)
+        xb, yb = B.uc_get_iterate(results[3], which, n, m)
+        np.testing.assert_array_equal(xa, xb)
+        np.testing.assert_array_equal(ya, yb)
