@@ -245,7 +245,7 @@ def run_ours(args):
                      stages=args.stages,
                      rows_per_thread=[rpt], cta_rows=cta,
                      algorithm=args.algorithm, restart_metric=args.restart_metric, pdl=not args.no_pdl,
-                     adaptive_step=args.adaptive_step, pw_gains=_gains(args),
+                     adaptive_step=args.adaptive_step, pw_gains=_gains(args), pw_guard=args.pw_guard,
                      reorder=not args.no_reorder)
 
     def solve_once():
@@ -358,7 +358,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rp_, rcp = B.uc_solve(ps, tol=TOL, max_iter=args.max_iter, rows_per_thread=[rpt], cta_rows=cta,
-                              pw_gains=_gains(args), polish=True, tol_abs_feas=1e-5)
+                              pw_gains=_gains(args), pw_guard=args.pw_guard, polish=True, tol_abs_feas=1e-5)
         sp = B.uc_get_stats(rp_)
         polish = {"status": sp["status_name"], "main_iters": sp["iters"], "polish_iters": sp["polish_iters"],
                   "abs_primal_before": sp["abs_primal_unpolished"], "abs_primal_after": sp["abs_primal"],
@@ -495,7 +495,7 @@ def run_batch(args):
     ps32 = presolve_all(probs, value_bits=vb)
     presolve_s = time.perf_counter() - t0
     tuner = Tuner()
-    kw = dict(restart_metric=args.restart_metric, pw_gains=_gains(args))
+    kw = dict(restart_metric=args.restart_metric, pw_gains=_gains(args), pw_guard=args.pw_guard)
     solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=vb, **kw)      # warm-up + tuning
     with ClockSampler(0) as clk:
         res32, info = solve_batch(ps32, tol=TOL, max_iter=args.max_iter, tuner=tuner, value_bits=vb, **kw)
@@ -506,7 +506,8 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"{args.batch} UC LPs, buses log-uniform in [300, 6049], T 24/48, seeds 1-{args.batch}",
                        "total_nnz": int(sum(B.uc_presolved_dims(p)[3] for p in ps32)),
-                       "matrix_values": f"fp{vb}", "vectors": "fp64", "tol_rel_kkt": TOL},
+                       "matrix_values": f"fp{vb}", "vectors": "fp64", "tol_rel_kkt": TOL,
+                       "max_iter": args.max_iter},
             "rows_per_thread": info["rows_per_thread"], "all_optimal": all(s["status"] == 0 for s in st32),
             "per_lp": [{"buses": P.B, "T": P.T, "iters": s["iters"], "status": s["status_name"],
                         "rel_kkt": max(s["rel_primal"], s["rel_dual"], s["rel_gap"])} for P, s in zip(probs, st32)],
@@ -733,6 +734,8 @@ def main():
                     help="skip the untimed feasibility-polishing solve reported beside the line")
     ap.add_argument("--pw-gains", default=None,
                     help="primal-weight controller gains kp,ki,kd (default: the library's)")
+    ap.add_argument("--pw-guard", type=float, default=None,
+                    help="residual-balance guard kappa on the primal-weight update (0: off; default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -179,6 +179,14 @@ typedef struct {
                                     combined point.  0: off (default) */
     int polish_max_iter;         /* iteration limit of the polishing phase (0: 10000); if it is
                                     reached the result keeps its unpolished primal */
+    double pw_guard;             /* residual-balance guard on the primal-weight update, kappa >= 1
+                                    (0: off).  At a restart the controller's new omega is kept
+                                    only if it moves toward balancing the relative residuals of the
+                                    restart point: a decrease is dropped when rel_primal > kappa *
+                                    rel_dual, an increase when rel_dual > kappa * rel_primal (a larger
+                                    omega is a larger dual step, which works on primal
+                                    infeasibility).  Halpern variant.  UC_EINVAL for a negative,
+                                    non-finite or (0, 1) value */
 } uc_solve_opts;
 
 typedef struct {

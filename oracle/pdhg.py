@@ -63,6 +63,13 @@ constant step.  With T the PDHG map above and z = (x, y):
           z = z0 = z_hat, j = 0, r_anchor = r re-weighted with the new omega.
 The initial r_anchor is KKT_omega(z0) for "kkt" and +inf for "fpr" and "fprp".
 
+The primal-weight update at a restart is PDLP's rule by default, written as a
+proportional controller on ln omega (primal_weight_update, with the PID
+generalisation as an option), optionally followed by a residual-balance guard
+(guard_weight, option pw_guard): the new weight is kept only if it does not
+move against the balance of the restart point's relative primal and dual
+residuals by more than a factor kappa.
+
 Primal feasibility polishing (after a solve that met the relative KKT
 tolerance).  The paper's PDHG runs with an absolute feasibility tolerance of
 1e-5 beside the 1e-4 convergence tolerance (Sec. II-D).  A point that meets
@@ -271,6 +278,22 @@ def primal_weight_update(omega, dx, dy, ctl: PrimalWeightControl | None = None) 
     return math.exp(math.log(omega) - (ctl.kp * e + ctl.ki * ctl.isum + ctl.kd * de))
 
 
+def guard_weight(omega, omega_new, rel_p, rel_d, kappa) -> float:
+    """Residual-balance guard on a primal-weight update.  A larger omega is a
+    larger dual step sigma = eta omega, which works on primal infeasibility
+    (the dual ascent direction is the primal residual), and a smaller omega a
+    larger primal step, which works on dual infeasibility -- the residual
+    balancing of ADMM and adaptive PDHG (Boyd et al. 2011, Sec. 3.4.1;
+    Goldstein et al. 2015).  The controller's omega_new is dropped (omega kept)
+    when it moves against the balance of the relative residuals of the restart
+    point by more than the factor kappa: a decrease while rel_p > kappa rel_d,
+    an increase while rel_d > kappa rel_p.  kappa = 0 turns the guard off."""
+    if kappa > 0.0 and ((omega_new < omega and rel_p > kappa * rel_d) or
+                        (omega_new > omega and rel_d > kappa * rel_p)):
+        return omega
+    return omega_new
+
+
 def evaluate(S, st: State, U, tol: float, adaptive: bool = False):
     """Evaluation after an n_eval block; returns (done, which, point) and
     applies a restart to ``st`` when the test fires."""
@@ -370,6 +393,7 @@ class HState:
     restarts: int = 0
     evals: int = 0
     pw: PrimalWeightControl = dataclasses.field(default_factory=PrimalWeightControl)
+    pw_guard: float = 0.0    # residual-balance guard kappa (see guard_weight; 0: off)
 
 
 INFEAS_EVERY = 4      # evaluations between infeasibility tests
@@ -436,7 +460,7 @@ def halpern_evaluate(S, st: HState, U, tol: float, stop_abs=None):
     if restart_decision(r, st.r_anchor, st.r_prev, st.j, st.k):
         dx = float(np.linalg.norm(st.xh - st.x0))
         dy = float(np.linalg.norm(st.yh - st.y0))
-        st.omega = primal_weight_update(w, dx, dy, st.pw)
+        st.omega = guard_weight(w, primal_weight_update(w, dx, dy, st.pw), rel[0], rel[1], st.pw_guard)
         wn = st.omega
         st.x = st.xh.copy()
         st.y = st.yh.copy()
@@ -456,11 +480,12 @@ def halpern_evaluate(S, st: HState, U, tol: float, stop_abs=None):
 
 def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N_EVAL,
                   x0=None, y0=None, metric: str = "kkt", trace=None, trace_iters=(),
-                  omega0=None, stop_abs=None, pw_gains=None) -> Result:
+                  omega0=None, stop_abs=None, pw_gains=None, pw_guard: float = 0.0) -> Result:
     """Run the Halpern variant; ``trace(k, state)`` after every step k in trace_iters
     (after the evaluation when k is a multiple of n_eval)."""
     st = halpern_initial_state(S, x0, y0, metric, omega0)
     st.pw = PrimalWeightControl(*(DEFAULT_PW_GAINS if pw_gains is None else pw_gains))
+    st.pw_guard = float(pw_guard)
     AT = S.A.T.tocsr()
     U = _unscaled_lp(S)
     trace_iters = set(trace_iters)
@@ -480,11 +505,11 @@ def solve_halpern(S, tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = N
 
 
 def polish_primal(S, x, tol_abs: float = 1e-5, max_iter: int = 10_000, omega0=None,
-                  n_eval: int = N_EVAL, metric: str = "kkt", pw_gains=None) -> Result:
+                  n_eval: int = N_EVAL, metric: str = "kkt", pw_gains=None, pw_guard: float = 0.0) -> Result:
     """Primal feasibility polishing (see the module docstring): the Halpern
     variant on the feasibility problem (c = 0) from the scaled primal ``x``, a
     zero dual and primal weight ``omega0`` (S.omega0 when None), until the
     largest absolute violation of the unscaled rows is <= ``tol_abs``."""
     F = dataclasses.replace(S, c=np.zeros_like(S.c))
     return solve_halpern(F, tol=0.0, max_iter=max_iter, n_eval=n_eval, x0=x, metric=metric,
-                         omega0=omega0, stop_abs=tol_abs, pw_gains=pw_gains)
+                         omega0=omega0, stop_abs=tol_abs, pw_gains=pw_gains, pw_guard=pw_guard)

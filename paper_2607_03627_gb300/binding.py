@@ -54,7 +54,8 @@ class uc_solve_opts(C.Structure):
                 ("restart_metric", C.c_int),
                 ("cancel", _P(C.c_int)), ("stages", C.c_int), ("lanes", C.c_int),
                 ("adaptive_step", C.c_int), ("pw_kp", C.c_double), ("pw_ki", C.c_double),
-                ("pw_kd", C.c_double), ("polish", C.c_int), ("polish_max_iter", C.c_int)]
+                ("pw_kd", C.c_double), ("polish", C.c_int), ("polish_max_iter", C.c_int),
+                ("pw_guard", C.c_double)]
 
 
 class uc_device_lp(C.Structure):
@@ -338,7 +339,7 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
                rows_per_thread=None, pdl: bool = True, reorder: bool = True,
                stages: int = 0, lanes: bool = False, adaptive_step: bool = False,
                pw_gains=None, polish: bool = False, polish_max_iter: int = 0,
-               tol_abs_feas: float = 1e-5) -> tuple[uc_solve_opts, list]:
+               tol_abs_feas: float = 1e-5, pw_guard=None) -> tuple[uc_solve_opts, list]:
     o = uc_solve_opts()
     lib.uc_default_solve_opts(C.byref(o))
     keep = []
@@ -361,6 +362,8 @@ def solve_opts(tol: float = 1e-4, max_iter: int = 100_000, n_eval: int = 64, use
     o.tol_abs_feas = float(tol_abs_feas)
     if pw_gains is not None:   # (kp, ki, kd) of the primal-weight controller
         o.pw_kp, o.pw_ki, o.pw_kd = (float(v) for v in pw_gains)
+    if pw_guard is not None:   # residual-balance guard kappa (0: off)
+        o.pw_guard = float(pw_guard)
     if rows_per_thread is not None:
         rp = np.ascontiguousarray(rows_per_thread, dtype=np.int32)
         keep.append(rp)

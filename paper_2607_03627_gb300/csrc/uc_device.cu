@@ -84,6 +84,8 @@ struct Scalars {
     // e = ln(omega dx / dy) at restarts
     double pw_kp, pw_ki, pw_kd, pw_isum, pw_eprev;
     int pw_has;
+    // residual-balance guard on the weight update (0: off, else kappa >= 1)
+    double pw_guard;
     // > 0: stop when the largest absolute violation of the unscaled rows is at
     // most this (primal feasibility polishing), instead of the relative KKT test
     double stop_abs;
@@ -1167,6 +1169,16 @@ __device__ double primal_weight(Scalars *S, double w, double dx, double dy) {
     return exp(log(w) - (S->pw_kp * e + S->pw_ki * S->pw_isum + S->pw_kd * de));
 }
 
+// Residual-balance guard: a larger omega is a larger dual step, which works on
+// primal infeasibility, and a smaller one the reverse.  The controller's new
+// weight wn is dropped (omega kept) when it moves against the balance of the
+// relative residuals of the restart point by more than the factor kappa.
+__device__ double guard_weight(const Scalars *S, double w, double wn, double rel_p, double rel_d) {
+    const double kap = S->pw_guard;
+    if (kap > 0.0 && ((wn < w && rel_p > kap * rel_d) || (wn > w && rel_d > kap * rel_p))) return w;
+    return wn;
+}
+
 __global__ void k_control(Bufs b, int mode, int k_lps) {
     const int inst = blockIdx.x * blockDim.x + threadIdx.x;
     if (inst >= k_lps) return;
@@ -1239,7 +1251,7 @@ __global__ void k_control(Bufs b, int mode, int k_lps) {
                              ((double)j >= 0.36 * (double)k);
         if (restart) {
             const double dx = sqrt(T[DX2]), dy = sqrt(T[DY2]);
-            const double wn = primal_weight(S, w, dx, dy);
+            const double wn = guard_weight(S, w, primal_weight(S, w, dx, dy), rel[0][0], rel[0][1]);
             S->omega = wn;
             S->kkt_anchor = (S->metric == METRIC_KKT) ? kkt_w(T[RP2], T[RD2], gap[0], wn)
                                                       : sqrt(fmax(wn * fx2 + fy2 / wn - 2.0 * S->eta * cross, 0.0));
@@ -1910,6 +1922,7 @@ static Scalars make_scalars(const uc_session &X, const PsData &p, double omega =
     s.pw_kp = X.o.pw_kp;
     s.pw_ki = X.o.pw_ki;
     s.pw_kd = X.o.pw_kd;
+    s.pw_guard = X.o.pw_guard;
     s.stop_abs = X.polish_tol;
     return s;
 }
@@ -2393,6 +2406,10 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     if (!(std::isfinite(o.pw_kp) && std::isfinite(o.pw_ki) && std::isfinite(o.pw_kd)) || o.pw_kp < 0 ||
         o.pw_ki < 0 || o.pw_kd < 0) {
         set_error("pw_kp, pw_ki and pw_kd must be finite and >= 0");
+        return UC_EINVAL;
+    }
+    if (!std::isfinite(o.pw_guard) || o.pw_guard < 0 || (o.pw_guard > 0 && o.pw_guard < 1)) {
+        set_error("pw_guard must be 0 (off) or a finite value >= 1");
         return UC_EINVAL;
     }
     if (o.adaptive_step != 0 && o.adaptive_step != 1) { set_error("adaptive_step must be 0 or 1"); return UC_EINVAL; }

@@ -29,7 +29,7 @@ def oracle_pipeline(P):
     return raw, ps, S
 
 
-def oracle_trace(S, ks, n_eval=pdhg.N_EVAL, variant="halpern", metric="kkt"):
+def oracle_trace(S, ks, n_eval=pdhg.N_EVAL, variant="halpern", metric="kkt", **kw):
     """Oracle current iterates after each step count in ks (tol 0: never stops):
     {k: (x, y, restarts, omega, x_map, y_map)}; x_map/y_map are the last PDHG
     map output for the Halpern variant (None for the averaging variant)."""
@@ -41,15 +41,15 @@ def oracle_trace(S, ks, n_eval=pdhg.N_EVAL, variant="halpern", metric="kkt"):
                   None if xm is None else xm.copy(), None if ym is None else ym.copy())
     if variant == "halpern":
         pdhg.solve_halpern(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, metric=metric, trace=rec,
-                           trace_iters=ks)
+                           trace_iters=ks, **kw)
     else:
         pdhg.solve(S, tol=0.0, max_iter=max(ks), n_eval=n_eval, trace=rec, trace_iters=ks)
     return out
 
 
-def oracle_solve(S, tol, variant="halpern", metric="kkt"):
+def oracle_solve(S, tol, variant="halpern", metric="kkt", **kw):
     if variant == "halpern":
-        return pdhg.solve_halpern(S, tol=tol, metric=metric)
+        return pdhg.solve_halpern(S, tol=tol, metric=metric, **kw)
     return pdhg.solve(S, tol=tol)
 
 

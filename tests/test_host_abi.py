@@ -234,6 +234,9 @@ def _c_solve(B, pss, **kw):
     (dict(rows_per_thread=[3]), "rows_per_thread must be"),
     (dict(adaptive_step=True), "adaptive_step needs"),                  # Halpern
     (dict(algorithm="average", spmv_kernel=2), "staged kernels need"),
+    (dict(pw_gains=(-0.5, 0.0, 0.0)), "pw_kp, pw_ki and pw_kd must be"),
+    (dict(pw_guard=0.5), "pw_guard must be 0"),
+    (dict(pw_guard=float("nan")), "pw_guard must be 0"),
 ])
 def test_solve_rejects_bad_options_before_touching_the_device(B, kw, msg):
     ps = B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)))

@@ -148,8 +148,41 @@ def _check_fprp(evaluate):
     assert st.r_anchor == pytest.approx(math.sqrt(18.0 + 8.0 - 24.0 * eta), rel=1e-14)
 
 
+# The residual-balance guard on the weight update.  At z_hat the relative
+# residuals are rel_p = 6 / (1 + |q|) = 3 and rel_d = 18 / (1 + |c|_inf) = 6: the
+# dual residual leads, so an increase of omega (toward a larger dual step,
+# which works on the primal residual) is dropped once rel_d > kappa rel_p, and a
+# decrease is never dropped.
+def _check_guard(evaluate):
+    S = _one_row_lp()
+    # kappa = 1: 1 -> 2 would widen the imbalance (6 > 1 * 3): omega stays 1 and
+    # the anchor value, the steps and the restart itself use omega = 1
+    st = _state(S, "kkt", omega=1.0, r_anchor=1e6, r_prev=math.inf, j=10, k=64)
+    st.pw_guard = 1.0
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.restarts == 1 and st.omega == 1.0
+    assert st.r_anchor == pytest.approx(_kkt_by_hand(1.0), rel=1e-14)
+    assert st.tau == pytest.approx(S.eta, rel=1e-15) and st.j == 0
+    np.testing.assert_array_equal(st.x0, [3.0, 4.0])
+    # kappa = 2: 6 > 2 * 3 is false, the update stands
+    st = _state(S, "kkt", omega=1.0, r_anchor=1e6, r_prev=math.inf, j=10, k=64)
+    st.pw_guard = 2.0
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.omega == pytest.approx(2.0, rel=1e-14)
+    # a decrease, 16 -> exp(0.5 ln 4 + 0.5 ln 16) = 8, moves toward balance: kept
+    # (KKT_16 = sqrt(256 * 36 + 324 / 256 + 181^2) = 204.9 <= 0.2e6: a restart)
+    st = _state(S, "kkt", omega=16.0, r_anchor=1e6, r_prev=math.inf, j=10, k=64)
+    st.pw_guard = 1.0
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.restarts == 1 and st.omega == pytest.approx(8.0, rel=1e-14)
+    # guard off: the plain update
+    st = _state(S, "kkt", omega=1.0, r_anchor=1e6, r_prev=math.inf, j=10, k=64)
+    evaluate(S, st, pdhg._unscaled_lp(S), -1.0)
+    assert st.omega == pytest.approx(2.0, rel=1e-14)
+
+
 PINS = [_check_restart_fpr, _check_restart_kkt, _check_no_restart, _check_restart_lands_on_fixed_point,
-        _check_fprp]
+        _check_fprp, _check_guard]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__[7:])
@@ -190,3 +223,27 @@ def test_each_planted_mistake_fails_a_pin(name):
         except AssertionError:
             failed.append(pin.__name__)
     assert failed, f"no pin caught the planted mistake: {name}"
+
+
+GUARD_MUTANTS = {
+    "guard directions swapped": [("omega_new < omega and rel_p", "omega_new > omega and rel_p"),
+                                 ("omega_new > omega and rel_d", "omega_new < omega and rel_d")],
+    "guard compares the residuals the wrong way": [("rel_d > kappa * rel_p", "rel_p > kappa * rel_d")],
+    "guard with a non-strict comparison": [("rel_d > kappa * rel_p", "rel_d >= kappa * rel_p")],
+    "guard without the factor kappa": [("rel_d > kappa * rel_p", "rel_d > rel_p")],
+    "guard always on": [("if kappa > 0.0 and (", "if kappa >= 0.0 and (")],
+}
+
+
+@pytest.mark.parametrize("name", sorted(GUARD_MUTANTS))
+def test_each_planted_guard_mistake_fails_the_guard_pin(name):
+    src = textwrap.dedent(inspect.getsource(pdhg.guard_weight))
+    for old, new in GUARD_MUTANTS[name]:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    ns = dict(vars(pdhg))
+    exec(compile(src, "<mutant>", "exec"), ns)
+    # halpern_evaluate compiled in the same namespace calls the planted guard
+    exec(compile(textwrap.dedent(inspect.getsource(pdhg.halpern_evaluate)), "<mutant>", "exec"), ns)
+    with pytest.raises(AssertionError):
+        _check_guard(ns["halpern_evaluate"])
