@@ -46,14 +46,14 @@ MAX_ITER = 100_000
 
 # DRAM bytes per launch of the iteration kernels from one ncu capture with
 # --cache-control none (steady-state L2), 6,049-bus LP, FP64 values, Halpern
-# (profiles/pdhg_kernels_grid6049.md): valid only for the kernel source they
-# were taken on (the hash of the row kernels' section of uc_device.cu, the
-# device layout and the strided-slot builder) and the launch shape (threads per
-# CTA, rows per thread).
+# (profiles/pdhg_kernels_grid6049.md; mean read + mean written over three
+# launches): valid only for the kernel source they were taken on (the hash of
+# the row kernels' section of uc_device.cu, the device layout and the
+# strided-slot builder) and the launch shape (threads per CTA, rows per thread).
 NCU_TRAFFIC = {}
 NCU_TRAFFIC_RPT2 = {
-    ("paper", "halpern", "k_primal"): {"src": "544ca1434cab5eaa", "launch": (128, 2), "bytes": 34107136 + 2486016},
-    ("paper", "halpern", "k_dual"): {"src": "544ca1434cab5eaa", "launch": (128, 2), "bytes": 15715072 + 1178624},
+    ("paper", "halpern", "k_primal"): {"src": "e5a319d16b4d6fd1", "launch": (128, 2), "bytes": 36105216 + 4938496},
+    ("paper", "halpern", "k_dual"): {"src": "e5a319d16b4d6fd1", "launch": (128, 2), "bytes": 16612949 + 2451627},
 }
 
 
