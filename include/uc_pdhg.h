@@ -92,6 +92,19 @@ typedef struct {
                                     reductions; A_s and A_s^T are copied to device memory for the
                                     duration of the call); UC_ECUDA without a device.  0: host
                                     threads (default) */
+    int eliminate_angles;        /* 1: substitute the free bus angles out before the other
+                                    reductions.  Per period a breadth-first spanning tree of the grid
+                                    is grown from the reference bus (each bus's lines in row order);
+                                    the tree lines' flow rows and every angle column leave the LP,
+                                    and each other line's flow row f_l - (theta_a - theta_b) / x_l = 0
+                                    becomes f_l - (1/x_l) (sum of +-x_e f_e over the tree path from
+                                    a to b) = 0 (Kirchhoff's voltage law on its fundamental cycle,
+                                    each entry computed as -+s (1/x_l) / (1/x_e) from the stored
+                                    1/x).  The LP is equivalent; postsolve puts the angles back down
+                                    the tree and gives a tree line's flow row the dual that its flow
+                                    column's reduced cost needs.  Row and column maps still point at
+                                    the LP as built.  UC_EINVAL if a period's grid is not connected or
+                                    has no single angle fixed at 0.  0: off (default) */
 } uc_presolve_opts;
 
 /* Device memory callback: return `bytes` bytes of device memory usable on

@@ -51,7 +51,7 @@ import dataclasses
 import numpy as np
 import scipy.sparse as sp
 
-from .lp import LP
+from .lp import COL_F, COL_TH, LP, ROW_FLOW
 
 RUIZ_ITERS = 10
 PC_ALPHA = 1.0
@@ -89,7 +89,171 @@ class Doubleton:
     hi_from_s: bool           # x_f's upper bound came from x_s's bounds
 
 
-def presolve(raw: LP, aggressive: bool = False) -> Presolved:
+@dataclasses.dataclass
+class AngleElimination:
+    """The LP with the bus angles substituted out along a spanning tree (see
+    eliminate_angles), and what restore_angles needs to put them back."""
+    lp: LP                    # raw columns but the angles, raw rows but the tree lines' flow rows
+    col_keep: np.ndarray      # its column -> raw column
+    row_keep: np.ndarray      # its row -> raw row
+    roots: list               # per period: the reference bus's angle column
+    tree: list                # per period, in breadth-first order: (angle col, parent's angle col,
+                              #   flow col of the tree line, s, 1/x of the line)
+    tree_row_of: dict         # flow col of a tree line -> its (removed) raw flow row
+
+
+def eliminate_angles(raw: LP) -> AngleElimination:
+    """Substitute the free bus angles out of the raw UC LP (Sec. II-A's DC
+    network; the paper's aggressive presolve substitutes free columns, Sec.
+    II-D).  Per period, the flow-definition rows f_l - inv_l (theta_a - theta_b)
+    = 0 (a = from bus, b = to bus, inv_l = 1/x_l) define a graph on the angle
+    columns.  A breadth-first spanning tree is grown from the reference bus
+    (the angle column fixed at 0), visiting each bus's lines in row order.  A
+    tree line's flow row gives theta_child - theta_parent = s f_e / inv_e (s = +1
+    when the child is the line's from end, else -1), so every angle difference
+    is a sum of tree flows along the tree path.  The tree lines' rows and all
+    angle columns leave the LP, and the row of every other line becomes
+      f_l - inv_l (sum_{e on a's path up} s_e f_e / inv_e
+                   - sum_{e on b's path up} s_e f_e / inv_e) = 0,
+    the two paths cut at their common part (Kirchhoff's voltage law on the
+    line's fundamental cycle).  The LP is equivalent; the other rows have no
+    angle entry."""
+    A = raw.A.tocsr()
+    th = raw.col_kind == COL_TH
+    flow_rows = np.flatnonzero(raw.row_kind == ROW_FLOW)
+    new_rows = {}
+    drop = set()
+    roots, tree, tree_row_of = [], [], {}
+    for t in sorted(set(int(v) for v in raw.col_t[th])):
+        nodes = [int(j) for j in np.flatnonzero(th & (raw.col_t == t))]
+        fixed0 = [j for j in nodes if raw.l[j] == 0.0 and raw.u[j] == 0.0]
+        if len(fixed0) != 1:
+            raise ValueError(f"period {t}: expected one reference angle, found {len(fixed0)}")
+        root = fixed0[0]
+        edges = []            # (row, flow col, from angle col, to angle col, inv)
+        for i in flow_rows[raw.row_t[flow_rows] == t]:
+            fc = a = b = None
+            inv = 0.0
+            for k in range(A.indptr[i], A.indptr[i + 1]):
+                j, v = int(A.indices[k]), float(A.data[k])
+                if raw.col_kind[j] == COL_F:
+                    fc = j
+                elif v < 0:
+                    a = j
+                else:
+                    b, inv = j, v
+            edges.append((int(i), fc, a, b, inv))
+        adj = {j: [] for j in nodes}
+        for e, (_, _, a, b, _) in enumerate(edges):
+            adj[a].append((b, e))
+            adj[b].append((a, e))
+        parent = {root: None}
+        order = [root]
+        for v in order:                          # breadth-first: order grows while read
+            for w, e in adj[v]:
+                if w not in parent:
+                    parent[w] = (v, e)
+                    order.append(w)
+        if len(order) != len(nodes):
+            raise ValueError(f"period {t}: the grid is not connected")
+
+        def up(v):
+            path = []
+            while parent[v] is not None:
+                p_, e = parent[v]
+                path.append((e, 1.0 if edges[e][2] == v else -1.0))
+                v = p_
+            return path
+
+        in_tree = {parent[w][1] for w in order[1:]}
+        for e, (i, fc, a, b, inv) in enumerate(edges):
+            if e in in_tree:
+                drop.add(i)
+                tree_row_of[fc] = i
+                continue
+            pa, pb = up(a), up(b)
+            while pa and pb and pa[-1] == pb[-1]:
+                pa.pop()
+                pb.pop()
+            row = {fc: 1.0}
+            for g, sg in pa:
+                row[edges[g][1]] = -sg * inv / edges[g][4]
+            for g, sg in pb:
+                row[edges[g][1]] = sg * inv / edges[g][4]
+            new_rows[int(i)] = row
+        roots.append(root)
+        tree.append([(w, parent[w][0], edges[parent[w][1]][1], 1.0 if edges[parent[w][1]][2] == w else -1.0,
+                      edges[parent[w][1]][4]) for w in order[1:]])
+    col_keep = np.flatnonzero(~th)
+    newcol = -np.ones(raw.n, np.int64)
+    newcol[col_keep] = np.arange(col_keep.size)
+    row_keep = np.array([i for i in range(raw.m) if i not in drop], np.int64)
+    indptr, indices, data = [0], [], []
+    for i in row_keep:
+        if i in new_rows:
+            ents = new_rows[i]
+        else:
+            ents = {int(A.indices[k]): float(A.data[k]) for k in range(A.indptr[i], A.indptr[i + 1])}
+        row = sorted((int(newcol[j]), v) for j, v in ents.items())
+        if any(j < 0 for j, _ in row):
+            raise ValueError(f"row {i} has an angle entry but is no flow row")
+        indices += [j for j, _ in row]
+        data += [v for _, v in row]
+        indptr.append(len(indices))
+    At = sp.csr_matrix((np.array(data, float), np.array(indices, np.int64), np.array(indptr, np.int64)),
+                       shape=(row_keep.size, col_keep.size))
+    lp = LP(A=At, q=raw.q[row_keep].copy(), c=raw.c[col_keep].copy(), l=raw.l[col_keep].copy(),
+            u=raw.u[col_keep].copy(), m_eq=int(np.count_nonzero(row_keep < raw.m_eq)), obj_const=raw.obj_const,
+            col_kind=raw.col_kind[col_keep], col_t=raw.col_t[col_keep], col_idx=raw.col_idx[col_keep],
+            row_kind=raw.row_kind[row_keep], row_t=raw.row_t[row_keep], row_idx=raw.row_idx[row_keep])
+    return AngleElimination(lp=lp, col_keep=col_keep, row_keep=row_keep, roots=roots, tree=tree,
+                            tree_row_of=tree_row_of)
+
+
+def restore_angles(E: AngleElimination, raw: LP, x: np.ndarray, y: np.ndarray | None = None):
+    """Map a point of E.lp to the raw LP: the angles from the reference bus's
+    value down the tree, theta_child = theta_parent + s f_e / inv_e; the dual
+    of a tree line's flow row from the reduced cost of its flow column, which
+    the substitution moved into the rows it entered: y_e = sum over the
+    substituted rows r holding f_e of (coefficient) * y_r."""
+    xr = np.zeros(raw.n)
+    xr[E.col_keep] = x
+    for root, tr in zip(E.roots, E.tree):
+        xr[root] = raw.l[root]
+        for w, p_, fc, sg, inv in tr:
+            xr[w] = xr[p_] + sg * xr[fc] / inv
+    if y is None:
+        return xr, None
+    yr = np.zeros(raw.m)
+    yr[E.row_keep] = y
+    A = E.lp.A.tocsr()
+    for r in range(A.shape[0]):
+        if E.lp.row_kind[r] != ROW_FLOW:
+            continue
+        for k in range(A.indptr[r], A.indptr[r + 1]):
+            fc = int(E.col_keep[A.indices[k]])
+            if fc in E.tree_row_of:
+                yr[E.tree_row_of[fc]] += A.data[k] * y[r]
+    return xr, yr
+
+
+def presolve(raw: LP, aggressive: bool = False, angles: bool = False) -> Presolved:
+    """The reductions of the module docstring; with ``angles`` the bus angles
+    are first substituted out (eliminate_angles), and the returned maps still
+    point at raw columns and rows (``fixed`` and ``removed_rows`` then refer to
+    the angle-free LP)."""
+    if not angles:
+        return _reduce(raw, aggressive)
+    E = eliminate_angles(raw)
+    inner = _reduce(E.lp, aggressive)
+    ps = Presolved(lp=inner.lp, col_map=E.col_keep[inner.col_map], row_map=E.row_keep[inner.row_map],
+                   raw_n=raw.n, raw_m=raw.m, fixed=inner.fixed, removed_rows=inner.removed_rows, raw=raw)
+    ps._inner = inner
+    ps._angles = E
+    return ps
+
+
+def _reduce(raw: LP, aggressive: bool = False) -> Presolved:
     A = raw.A.tocsr()
     n, m = raw.n, raw.m
     l = raw.l.copy()
@@ -242,6 +406,10 @@ def postsolve(ps: Presolved, x: np.ndarray, y: np.ndarray | None = None):
     except a singleton row whose bound is active in the reduced solution and
     was tightened by that row: it takes the column's reduced cost / a.
     """
+    E = getattr(ps, "_angles", None)
+    if E is not None:
+        xt, yt = postsolve(ps._inner, x, y)
+        return restore_angles(E, ps.raw, xt, yt)
     raw = ps.raw
     xr = ps._xfix.copy()
     xr[ps.col_map] = x

@@ -15,10 +15,10 @@ from . import binding as B
 from .tune import Tuner, bucket_of
 
 
-def presolve_all(problems, value_bits: int = 64, workers: int = 8):
-    """uc_build_lp + uc_presolve for every problem, on host threads."""
+def presolve_all(problems, value_bits: int = 64, workers: int = 8, **kw):
+    """uc_build_lp + uc_presolve (options ``kw``) for every problem, on host threads."""
     def one(P):
-        return B.uc_presolve(B.uc_build_lp(P), value_bits=value_bits)
+        return B.uc_presolve(B.uc_build_lp(P), value_bits=value_bits, **kw)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         return list(ex.map(one, problems))
 

@@ -37,7 +37,7 @@ class uc_problem(C.Structure):
 class uc_presolve_opts(C.Structure):
     _fields_ = [("ruiz_iters", C.c_int), ("pock_chambolle", C.c_int), ("power_max_iter", C.c_int),
                 ("power_tol", C.c_double), ("value_bits", C.c_int), ("threads", C.c_int),
-                ("aggressive", C.c_int), ("power_device", C.c_int)]
+                ("aggressive", C.c_int), ("power_device", C.c_int), ("eliminate_angles", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -336,6 +336,183 @@ static int build(const uc_problem *P, RawLp &lp) {
 }
 
 // ---------------------------------------------------------------------------
+// Angle elimination (presolve option eliminate_angles).  Per period the flow
+// rows f_l - inv_l (theta_a - theta_b) = 0 (a = from bus, b = to bus, inv_l =
+// 1/x_l as stored) define a graph on the angle columns.  A breadth-first
+// spanning tree is grown from the reference bus (the angle fixed at 0),
+// visiting each bus's lines in row order.  A tree line's row gives
+// theta_child - theta_parent = s f_e / inv_e (s = +1 when the child is the
+// line's from end), so an angle difference is a sum of tree flows along the
+// tree path.  The tree lines' rows and the angle columns leave the LP; the
+// row of every other line becomes
+//   f_l - inv_l (sum over a's path up of s f_e / inv_e - the same for b) = 0,
+// the paths cut at their common part (its fundamental cycle).
+// ---------------------------------------------------------------------------
+int eliminate_angles(const RawLp &raw, RawLp &out, AngleElim &E) {
+    const Csr &A = raw.A;
+    const int n = A.cols, m = A.rows;
+    std::vector<int> periods;
+    for (int j = 0; j < n; j++)
+        if (raw.col_kind[j] == COL_TH) periods.push_back(raw.col_t[j]);
+    std::sort(periods.begin(), periods.end());
+    periods.erase(std::unique(periods.begin(), periods.end()), periods.end());
+    std::vector<std::vector<int>> th_of(periods.size()), rows_of(periods.size());
+    auto pidx = [&](int t) { return (int)(std::lower_bound(periods.begin(), periods.end(), t) - periods.begin()); };
+    for (int j = 0; j < n; j++)
+        if (raw.col_kind[j] == COL_TH) th_of[pidx(raw.col_t[j])].push_back(j);
+    for (int i = 0; i < m; i++)
+        if (raw.row_kind[i] == ROW_FLOW) {
+            const auto it = std::lower_bound(periods.begin(), periods.end(), raw.row_t[i]);
+            if (it == periods.end() || *it != raw.row_t[i]) { set_error("eliminate_angles: flow row %d has no angles", i); return UC_EINVAL; }
+            rows_of[it - periods.begin()].push_back(i);
+        }
+    struct Edge { int row, fc, a, b; double inv; };
+    std::vector<char> drop(m, 0);
+    std::vector<std::vector<std::pair<int, double>>> new_row(m);   // substituted rows (raw columns)
+    std::vector<char> has_new(m, 0);
+    E.roots.clear();
+    E.tree.clear();
+    E.tree_row.assign(n, -1);
+    std::vector<int> local(n, -1);
+    for (size_t p = 0; p < periods.size(); p++) {
+        const std::vector<int> &nodes = th_of[p];
+        int root = -1, nroot = 0;
+        for (int j : nodes)
+            if (raw.l[j] == 0.0 && raw.u[j] == 0.0) { root = j; nroot++; }
+        if (nroot != 1) { set_error("eliminate_angles: period %d has %d angles fixed at 0, not one", periods[p], nroot); return UC_EINVAL; }
+        for (size_t k = 0; k < nodes.size(); k++) local[nodes[k]] = (int)k;
+        std::vector<Edge> edges;
+        for (int i : rows_of[p]) {
+            Edge e{i, -1, -1, -1, 0.0};
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                const int j = A.colidx[k];
+                const double v = A.val[k];
+                if (raw.col_kind[j] == COL_F) e.fc = j;
+                else if (v < 0) e.a = j;
+                else { e.b = j; e.inv = v; }
+            }
+            if (e.fc < 0 || e.a < 0 || e.b < 0 || local[e.a] < 0 || local[e.b] < 0) {
+                set_error("eliminate_angles: flow row %d is not f - (theta_a - theta_b) / x", i);
+                return UC_EINVAL;
+            }
+            edges.push_back(e);
+        }
+        const int nn = (int)nodes.size();
+        std::vector<std::vector<std::pair<int, int>>> adj(nn);   // (local node, edge)
+        for (int e = 0; e < (int)edges.size(); e++) {
+            adj[local[edges[e].a]].push_back({local[edges[e].b], e});
+            adj[local[edges[e].b]].push_back({local[edges[e].a], e});
+        }
+        std::vector<int> par(nn, -2), pedge(nn, -1), order;
+        order.reserve(nn);
+        par[local[root]] = -1;
+        order.push_back(local[root]);
+        for (size_t h = 0; h < order.size(); h++) {
+            const int v = order[h];
+            for (auto &we : adj[v])
+                if (par[we.first] == -2) { par[we.first] = v; pedge[we.first] = we.second; order.push_back(we.first); }
+        }
+        if ((int)order.size() != nn) { set_error("eliminate_angles: the grid of period %d is not connected", periods[p]); return UC_EINVAL; }
+        std::vector<char> in_tree(edges.size(), 0);
+        for (int k = 1; k < nn; k++) in_tree[pedge[order[k]]] = 1;
+        auto up = [&](int v, std::vector<std::pair<int, double>> &path) {   // (edge, s) from v to the root
+            path.clear();
+            while (par[v] >= 0) {
+                const int e = pedge[v];
+                path.push_back({e, local[edges[e].a] == v ? 1.0 : -1.0});
+                v = par[v];
+            }
+        };
+        std::vector<std::pair<int, double>> pa, pb;
+        for (int e = 0; e < (int)edges.size(); e++) {
+            const Edge &L = edges[e];
+            if (in_tree[e]) { drop[L.row] = 1; E.tree_row[L.fc] = L.row; continue; }
+            up(local[L.a], pa);
+            up(local[L.b], pb);
+            while (!pa.empty() && !pb.empty() && pa.back() == pb.back()) { pa.pop_back(); pb.pop_back(); }
+            auto &row = new_row[L.row];
+            row.push_back({L.fc, 1.0});
+            for (auto &gs : pa) row.push_back({edges[gs.first].fc, -gs.second * L.inv / edges[gs.first].inv});
+            for (auto &gs : pb) row.push_back({edges[gs.first].fc, gs.second * L.inv / edges[gs.first].inv});
+            has_new[L.row] = 1;
+        }
+        E.roots.push_back(root);
+        for (int k = 1; k < nn; k++) {
+            const int w = order[k];
+            const Edge &L = edges[pedge[w]];
+            E.tree.push_back({nodes[w], nodes[par[w]], L.fc, local[L.a] == w ? 1.0 : -1.0, L.inv});
+        }
+        for (int j : nodes) local[j] = -1;
+    }
+    std::vector<int32_t> newcol(n, -1);
+    E.col_keep.clear();
+    for (int j = 0; j < n; j++)
+        if (raw.col_kind[j] != COL_TH) { newcol[j] = (int32_t)E.col_keep.size(); E.col_keep.push_back(j); }
+    E.row_keep.clear();
+    for (int i = 0; i < m; i++)
+        if (!drop[i]) E.row_keep.push_back(i);
+    out = RawLp{};
+    out.B = raw.B; out.L = raw.L; out.G = raw.G; out.T = raw.T; out.nc = raw.nc; out.has_shed = raw.has_shed;
+    const int nk = (int)E.col_keep.size(), mk = (int)E.row_keep.size();
+    out.A.rows = mk;
+    out.A.cols = nk;
+    out.A.rowptr.assign(1, 0);
+    std::vector<std::pair<int, double>> ents;
+    for (int r = 0; r < mk; r++) {
+        const int i = E.row_keep[r];
+        ents.clear();
+        if (has_new[i]) {
+            for (auto &jv : new_row[i]) ents.push_back({newcol[jv.first], jv.second});
+        } else {
+            for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++) {
+                if (newcol[A.colidx[k]] < 0) { set_error("eliminate_angles: row %d has an angle entry but is no flow row", i); return UC_EINVAL; }
+                ents.push_back({newcol[A.colidx[k]], A.val[k]});
+            }
+        }
+        std::sort(ents.begin(), ents.end(), [](const std::pair<int, double> &x, const std::pair<int, double> &y) { return x.first < y.first; });
+        for (auto &jv : ents) { out.A.colidx.push_back(jv.first); out.A.val.push_back(jv.second); }
+        out.A.rowptr.push_back((int32_t)out.A.colidx.size());
+    }
+    out.m_eq = 0;
+    for (int i : E.row_keep) out.m_eq += i < raw.m_eq ? 1 : 0;
+    for (int i : E.row_keep) {
+        out.q.push_back(raw.q[i]); out.row_kind.push_back(raw.row_kind[i]);
+        out.row_t.push_back(raw.row_t[i]); out.row_idx.push_back(raw.row_idx[i]);
+    }
+    for (int j : E.col_keep) {
+        out.c.push_back(raw.c[j]); out.l.push_back(raw.l[j]); out.u.push_back(raw.u[j]);
+        out.col_kind.push_back(raw.col_kind[j]); out.col_t.push_back(raw.col_t[j]); out.col_idx.push_back(raw.col_idx[j]);
+    }
+    return UC_OK;
+}
+
+// A point of the angle-free LP on the LP as built: the angles from the
+// reference value down the tree, theta_child = theta_parent + s f_e / inv_e;
+// a tree line's flow row takes the dual that keeps its flow column's reduced
+// cost, sum over the substituted rows r holding f_e of (coefficient) y_r.
+static void restore_angles(const AngleElim &E, const RawLp &orig, const RawLp &work, std::vector<double> &x,
+                           std::vector<double> &y, bool duals) {
+    std::vector<double> xo(orig.A.cols, 0.0);
+    for (size_t k = 0; k < E.col_keep.size(); k++) xo[E.col_keep[k]] = x[k];
+    for (int r : E.roots) xo[r] = orig.l[r];
+    for (const auto &nd : E.tree) xo[nd.col] = xo[nd.parent] + nd.s * xo[nd.fcol] / nd.inv;
+    x.swap(xo);
+    std::vector<double> yo(orig.A.rows, 0.0);
+    if (duals) {
+        for (size_t k = 0; k < E.row_keep.size(); k++) yo[E.row_keep[k]] = y[k];
+        const Csr &W = work.A;
+        for (int r = 0; r < W.rows; r++) {
+            if (work.row_kind[r] != ROW_FLOW) continue;
+            for (int32_t k = W.rowptr[r]; k < W.rowptr[r + 1]; k++) {
+                const int tr = E.tree_row[E.col_keep[W.colidx[k]]];
+                if (tr >= 0) yo[tr] += W.val[k] * y[r];
+            }
+        }
+    }
+    y.swap(yo);
+}
+
+// ---------------------------------------------------------------------------
 // Presolve
 // ---------------------------------------------------------------------------
 static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<double> &qr,
@@ -651,8 +828,18 @@ void host_kkt(const PsData &p, const double *xs, const double *ys, double &rel_p
     abs_p = rpu;
 }
 
+static void postsolve_reduced(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
+                              std::vector<double> &y);
+
 void postsolve(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
                std::vector<double> &y) {
+    postsolve_reduced(ps, xs, ys, x, y);
+    if (ps.angles) restore_angles(*ps.angles, *ps.orig, *ps.raw, x, y, ys != nullptr);
+}
+
+// to the LP the reductions started from
+static void postsolve_reduced(const PsData &ps, const double *xs, const double *ys, std::vector<double> &x,
+                              std::vector<double> &y) {
     const RawLp &raw = *ps.raw;
     x = ps.xfix;
     for (size_t k = 0; k < ps.col_map.size(); k++) x[ps.col_map[k]] = ps.Dc[k] * xs[k];
@@ -708,6 +895,7 @@ const char *uc_last_error(void) { return g_err.c_str(); }
 
 void uc_default_presolve_opts(uc_presolve_opts *o) {
     if (!o) return;
+    std::memset(o, 0, sizeof *o);
     o->ruiz_iters = 10;
     o->pock_chambolle = 1;
     o->power_max_iter = 500;
@@ -780,11 +968,20 @@ int uc_presolve(const uc_lp *lp, const uc_presolve_opts *opts, uc_presolved **ou
     if (o.ruiz_iters < 0 || o.power_max_iter < 1) { set_error("uc_presolve: bad iteration counts"); return UC_EINVAL; }
     if (o.power_device != 0 && o.power_device != 1) { set_error("uc_presolve: power_device must be 0 or 1"); return UC_EINVAL; }
     if (o.aggressive != 0 && o.aggressive != 1) { set_error("uc_presolve: aggressive must be 0 or 1"); return UC_EINVAL; }
+    if (o.eliminate_angles != 0 && o.eliminate_angles != 1) { set_error("uc_presolve: eliminate_angles must be 0 or 1"); return UC_EINVAL; }
     int threads = o.threads > 0 ? o.threads : (int)std::max(1u, std::thread::hardware_concurrency());
     try {
         auto ps = std::make_shared<PsData>();
-        ps->raw = lp->d;
-        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, o.aggressive != 0);
+        ps->raw = ps->orig = lp->d;
+        if (o.eliminate_angles) {
+            auto work = std::make_shared<RawLp>();
+            auto E = std::make_shared<AngleElim>();
+            const int rc0 = eliminate_angles(*lp->d, *work, *E);
+            if (rc0) return rc0;
+            ps->raw = work;
+            ps->angles = E;
+        }
+        int rc = presolve_reduce(*ps->raw, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, o.aggressive != 0);
         if (rc) return rc;
         ps->raw_reduced_val = ps->A.val;
         double qi = 0.0, ci = 0.0;
@@ -823,7 +1020,21 @@ int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **
     if (!base || !lp || !out) { set_error("uc_presolve_reuse: null argument"); return UC_EINVAL; }
     *out = nullptr;
     const PsData &b = *base->d;
-    const RawLp &r0 = *b.raw, &r1 = *lp->d;
+    std::shared_ptr<const RawLp> work = lp->d;
+    std::shared_ptr<AngleElim> E;
+    if (b.angles) {   // the same substitution as the base's (same grid, so the same trees)
+        try {
+            auto w = std::make_shared<RawLp>();
+            E = std::make_shared<AngleElim>();
+            const int rc0 = eliminate_angles(*lp->d, *w, *E);
+            if (rc0) return rc0;
+            work = w;
+        } catch (const std::bad_alloc &) {
+            set_error("uc_presolve_reuse: out of host memory");
+            return UC_ENOMEM;
+        }
+    }
+    const RawLp &r0 = *b.raw, &r1 = *work;
     if (r0.A.rows != r1.A.rows || r0.A.cols != r1.A.cols || r0.m_eq != r1.m_eq ||
         r0.A.rowptr != r1.A.rowptr || r0.A.colidx != r1.A.colidx || r0.A.val != r1.A.val) {
         set_error("uc_presolve_reuse: the LP's matrix differs from the base LP's");
@@ -831,8 +1042,10 @@ int uc_presolve_reuse(const uc_presolved *base, const uc_lp *lp, uc_presolved **
     }
     try {
         auto ps = std::make_shared<PsData>();
-        ps->raw = lp->d;
-        int rc = presolve_reduce(*lp->d, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, b.aggressive);
+        ps->raw = work;
+        ps->orig = lp->d;
+        ps->angles = E;
+        int rc = presolve_reduce(*work, *ps, ps->A, ps->q, ps->c, ps->l, ps->u, b.aggressive);
         if (rc) return rc;
         if (ps->col_map != b.col_map || ps->row_map != b.row_map || ps->A.val != b.raw_reduced_val) {
             set_error("uc_presolve_reuse: presolve removed different rows or columns than for the base LP");
@@ -895,8 +1108,11 @@ int uc_presolved_export(const uc_presolved *h, int32_t *rowptr, int32_t *colidx,
     if (u) std::memcpy(u, p.u.data(), p.u.size() * 8);
     if (Dr) std::memcpy(Dr, p.Dr.data(), p.Dr.size() * 8);
     if (Dc) std::memcpy(Dc, p.Dc.data(), p.Dc.size() * 8);
-    if (col_map) std::memcpy(col_map, p.col_map.data(), p.col_map.size() * 4);
-    if (row_map) std::memcpy(row_map, p.row_map.data(), p.row_map.size() * 4);
+    // maps into the LP as built (through the angle elimination's maps when it ran)
+    for (size_t k = 0; col_map && k < p.col_map.size(); k++)
+        col_map[k] = p.angles ? p.angles->col_keep[p.col_map[k]] : p.col_map[k];
+    for (size_t k = 0; row_map && k < p.row_map.size(); k++)
+        row_map[k] = p.angles ? p.angles->row_keep[p.row_map[k]] : p.row_map[k];
     if (scalars) {
         scalars[0] = p.eta; scalars[1] = p.omega0; scalars[2] = p.norm_A;
         scalars[3] = p.obj_const; scalars[4] = p.q_inf; scalars[5] = p.c_inf; scalars[6] = p.norm_bound;
@@ -973,7 +1189,7 @@ int uc_get_raw_solution(const uc_result *res, double *x, double *y) {
 int uc_get_solution(const uc_result *res, double *p, double *u, double *v, double *theta,
                     double *f, double *shed, double *lmp, uc_stats *stats) {
     if (!res) { set_error("uc_get_solution: null result"); return UC_EINVAL; }
-    const RawLp &raw = *res->ps->raw;
+    const RawLp &raw = *res->ps->orig;
     std::vector<double> xr, yr;
     postsolve(*res->ps, res->x_ret.data(), res->y_ret.data(), xr, yr);
     const int G = raw.G, B = raw.B, L = raw.L;

@@ -51,9 +51,26 @@ struct RemovedRow {
     bool lo_from_s = false, hi_from_s = false;   // x_f's bound came from x_s's
 };
 
+// The bus angles substituted out of a raw LP along a spanning tree per period
+// (presolve option eliminate_angles): the angle-free LP's columns and rows are
+// raw columns (all but the angles) and raw rows (all but the tree lines' flow
+// rows); restore_angles maps its points back.
+struct AngleElim {
+    std::vector<int32_t> col_keep, row_keep;   // angle-free LP column / row -> raw
+    std::vector<int32_t> roots;                // per period: the reference angle column
+    struct Node { int32_t col, parent, fcol; double s, inv; };
+    std::vector<Node> tree;                    // each period's non-root buses, breadth-first
+    std::vector<int32_t> tree_row;             // raw n: removed flow row of a tree line's flow column, else -1
+};
+int eliminate_angles(const RawLp &raw, RawLp &out, AngleElim &E);
+
 // Everything the device solve and the postsolve need.
 struct PsData {
+    // the LP the reductions started from (the angle-free LP when the angles
+    // were eliminated), the LP as built, and what restores the angles
     std::shared_ptr<const RawLp> raw;
+    std::shared_ptr<const RawLp> orig;
+    std::shared_ptr<const AngleElim> angles;
     // reduced, scaled LP: A_s = diag(Dr) A diag(Dc)
     Csr A;            // m x n, FP64 scaled values
     Csr AT;           // n x m
@@ -67,8 +84,8 @@ struct PsData {
     std::vector<RemovedRow> removed;
     std::vector<double> raw_reduced_val;   // reduced matrix values before scaling
     double eta = 1.0, omega0 = 1.0, norm_A = 0.0, obj_const = 0.0;
-    double norm_bound = 0.0;
-    bool aggressive = false;               // presolve substituted doubleton equations               // max(certified upper bound, norm_A); eta = 0.998 / it
+    double norm_bound = 0.0;               // max(certified upper bound, norm_A); eta = 0.998 / it
+    bool aggressive = false;               // presolve substituted doubleton equations
     double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
     int value_bits = 64;
     int n() const { return A.cols; }

@@ -7,7 +7,7 @@ import pytest
 import ucgen
 from gpu_common import (ITERATE_RTOL, KKT_TOL, OBJ_GAP_TOL, golden_tiny, oracle_kkt_of_raw,
                         oracle_pipeline, oracle_solve, oracle_trace, raw_objective, rel_inf)
-from oracle import lp as olp, pdhg, simplex
+from oracle import kkt, lp as olp, pdhg, simplex
 
 pytestmark = pytest.mark.gpu
 
@@ -221,3 +221,38 @@ def test_aggressive_presolve_parity_and_gates(B, seed):
     assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6)
     opt = g["objective_by_seed"][str(seed)]
     assert abs(raw_objective(raw, xr) - opt) / max(1.0, abs(opt)) <= OBJ_GAP_TOL
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_angle_elimination_parity_and_gates(B, seed):
+    # the device solve of the angle-free LP (bus angles substituted out along a
+    # spanning tree) follows the oracle's PDHG on its own angle-free presolve,
+    # and after the postsolve puts the angles and the tree rows' duals back the
+    # point meets the gates on the LP as built
+    from oracle import presolve as ops
+    g = golden_tiny()
+    P = ucgen.tiny(seed)
+    raw = olp.build_lp(P)
+    ps_o = ops.presolve(raw, angles=True)
+    S = ops.scale(ps_o.lp)
+    ref = oracle_trace(S, [1, 64, 65, 200])
+    ps = B.uc_presolve(B.uc_build_lp(P), eliminate_angles=1)
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    assert (n, m) == (ps_o.lp.n, ps_o.lp.m)
+    for K in (1, 64, 65, 200):
+        x, y, st = _device_iterates(B, ps, n, m, K)
+        xo, yo, restarts, omega, _, _ = ref[K]
+        assert st["restarts"] == restarts
+        assert rel_inf(x, xo) <= ITERATE_RTOL and rel_inf(y, yo) <= ITERATE_RTOL, K
+    res, rc = B.uc_solve(ps, tol=KKT_TOL)
+    assert rc == B.UC_OK
+    r = oracle_solve(S, KKT_TOL)
+    assert B.uc_get_stats(res)["iters"] == r.iters
+    xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+    # the raw LP's own KKT (the angle-free LP's rows are raw rows or implied by them)
+    assert max(kkt.relative_kkt(raw, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+    assert max(oracle_kkt_of_raw(ps_o, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+    opt = g["objective_by_seed"][str(seed)]
+    assert abs(raw_objective(raw, xr) - opt) / max(1.0, abs(opt)) <= OBJ_GAP_TOL
+    sol = B.uc_get_solution(res, P.T, P.B, P.L, P.G)
+    assert np.all(sol["theta"][:, P.ref_bus] == 0.0)

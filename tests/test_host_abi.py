@@ -57,12 +57,13 @@ def test_builder_matches_oracle_exactly(B, P):
         np.testing.assert_array_equal(d[k], getattr(ref, k))
 
 
-@pytest.mark.parametrize("aggressive", [0, 1], ids=["default", "aggressive"])
+@pytest.mark.parametrize("aggressive,angles", [(0, 0), (1, 0), (0, 1), (1, 1)],
+                         ids=["default", "aggressive", "angles", "angles+aggressive"])
 @pytest.mark.parametrize("P", list(_problems()), ids=lambda P: P.name or "strict")
-def test_presolve_and_scaling_match_oracle(B, P, aggressive):
-    ps_o = ops.presolve(olp.build_lp(P), aggressive=bool(aggressive))
+def test_presolve_and_scaling_match_oracle(B, P, aggressive, angles):
+    ps_o = ops.presolve(olp.build_lp(P), aggressive=bool(aggressive), angles=bool(angles))
     S = ops.scale(ps_o.lp)
-    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P), aggressive=aggressive))
+    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P), aggressive=aggressive, eliminate_angles=angles))
     assert (d["n"], d["m"], d["m_eq"]) == (ps_o.lp.n, ps_o.lp.m, ps_o.lp.m_eq)
     np.testing.assert_array_equal(d["col_map"], ps_o.col_map)
     np.testing.assert_array_equal(d["row_map"], ps_o.row_map)
@@ -352,3 +353,38 @@ def test_aggressive_postsolve_matches_oracle(B):
     np.testing.assert_allclose(xr, xo, rtol=1e-9, atol=1e-9 * np.max(np.abs(xo)))
     np.testing.assert_allclose(yr, yo, rtol=1e-9, atol=1e-9 * np.max(np.abs(yo)))
     assert max(kkt.relative_kkt(raw, xr, yr)) <= 1e-8
+
+
+@pytest.mark.parametrize("aggressive", [0, 1], ids=["angles", "angles+aggressive"])
+def test_angle_postsolve_matches_oracle(B, aggressive):
+    # the host postsolve of the oracle simplex optimum of the angle-free 30-bus
+    # LP equals the oracle's: angles put back down the tree, tree lines' flow
+    # rows given their duals; the pair is KKT-optimal on the LP as built
+    from oracle import simplex
+    P = ucgen.tiny(0)
+    raw = olp.build_lp(P)
+    ps_o = ops.presolve(raw, aggressive=bool(aggressive), angles=True)
+    S = ops.scale(ps_o.lp)
+    r = simplex.solve_lp(ps_o.lp)
+    xo, yo = ops.postsolve(ps_o, r.x, r.y)
+    ps = B.uc_presolve(B.uc_build_lp(P), aggressive=aggressive, eliminate_angles=1)
+    res = B.uc_result_from_point(ps, r.x / S.Dc, r.y / S.Dr)
+    xr, yr = B.uc_get_raw_solution(res, raw.n, raw.m)
+    np.testing.assert_allclose(xr, xo, rtol=1e-9, atol=1e-9 * np.max(np.abs(xo)))
+    np.testing.assert_allclose(yr, yo, rtol=1e-9, atol=1e-9 * np.max(np.abs(yo)))
+    assert max(kkt.relative_kkt(raw, xr, yr)) <= 1e-8
+
+
+def test_angle_elimination_option_is_checked(B):
+    with pytest.raises(B.UCError, match="eliminate_angles"):
+        B.uc_presolve(B.uc_build_lp(ucgen.tiny(0)), eliminate_angles=2)
+
+
+def test_angle_elimination_reuse_equals_a_full_presolve(B):
+    base = ucgen.tiny(3)
+    ps0 = B.uc_presolve(B.uc_build_lp(base), eliminate_angles=1)
+    Q = ucgen.served_request(base, 1, 7)
+    full = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(Q), eliminate_angles=1))
+    re = B.uc_presolved_export(B.uc_presolve_reuse(ps0, B.uc_build_lp(Q)))
+    for k in ("rowptr", "colidx", "val", "q", "c", "l", "u", "Dr", "Dc", "col_map", "row_map"):
+        np.testing.assert_array_equal(re[k], full[k], err_msg=k)
