@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -209,13 +210,21 @@ constexpr int kPre = 3;   // row entries whose index and value are loaded before
 
 // A session of one LP has uniform tables: CTA c covers rows [c B, c B + B) of
 // B = BS * rpt rows, so its slice follows from blockIdx without loading the
-// table entry (n > 0 marks it; aux = first ">=" row for the dual kernel).
-struct Uniform { int n, aux, rpt; };
+// table entry (ntot > 0 marks it; aux = first ">=" row for the dual kernel).
+// Rows with more than kLongRow entries (the device layout puts them after all
+// others) get a warp each: their slices have rpt = 0 and BS / 32 rows, the
+// first cs CTAs covering the n shorter rows.
+constexpr int kLongRow = 32;
+struct Uniform { int n, aux, rpt, cs, ntot; };
 template <int BS>
 __device__ __forceinline__ Seg row_slice(const Seg *__restrict__ segs, const Uniform &u) {
-    if (u.n <= 0) return segs[blockIdx.x];
-    const int begin = (int)blockIdx.x * BS * u.rpt;
-    return Seg{0, begin, min(begin + BS * u.rpt, u.n), u.aux, u.rpt};
+    if (u.ntot <= 0) return segs[blockIdx.x];
+    if ((int)blockIdx.x < u.cs) {
+        const int begin = (int)blockIdx.x * BS * u.rpt;
+        return Seg{0, begin, min(begin + BS * u.rpt, u.n), u.aux, u.rpt};
+    }
+    const int begin = u.n + ((int)blockIdx.x - u.cs) * (BS / 32);
+    return Seg{0, begin, min(begin + BS / 32, u.ntot), u.aux, 0};
 }
 
 // Period-strided 16-row groups (SD = true).  In the entity-major device layout
@@ -278,10 +287,54 @@ __device__ __forceinline__ int row_head(const int *__restrict__ ci_arr, const VT
 // The loads of a row are issued before the LP's state is read (the addresses
 // are valid either way), so that read overlaps them instead of heading the
 // chain of dependent loads.  SD: strided groups read their slots (see above).
+// A long column (more than kLongRow entries) gets a warp: the lanes stride over
+// its entries, their partial sums are added in a fixed butterfly order, and
+// lane 0 adds -c and applies the column's update as the one-thread path does.
+template <typename VT, int ALGO>
+__device__ __forceinline__ void primal_long(const Seg &sg, const Bufs &b, int it, int src) {
+    const int lane = threadIdx.x & 31;
+    const int j = sg.begin + (int)(threadIdx.x >> 5);
+    if (j >= sg.end) return;                      // whole warps
+    const Scalars *S = b.S + sg.inst;
+    const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
+    const int k0 = __ldg(b.AT_rp + j), k1 = __ldg(b.AT_rp + j + 1);
+    const int k = S->k_base + it;
+    if (S->status != RUNNING || k >= S->max_iter) return;
+    const bool keep = (it == S->n_eval - 1 || k == S->max_iter - 1);
+    pdl_wait();
+    pdl_trigger();
+    const double *__restrict__ y = b.y[src];
+    double part = 0.0;
+    for (int e = k0 + lane; e < k1; e += 32) part = fma(widen(ld_stream(v + e)), y[ld_stream(b.AT_ci + e)], part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane != 0) return;
+    const double xin = ld_stream(b.x[src] + j);
+    const long long lk = ld_stream(b.lkey + j), uk = ld_stream(b.ukey + j);
+    const double aux = (ALGO == ALG_AVERAGE) ? b.xsum[j] : ld_stream(b.xa + j);
+    const double acc = neg_bits(ld_stream(b.c + j)) + part;
+    const double xv = clip_keys(fma(S->tau, acc, xin), lk, uk);
+    if (ALGO == ALG_AVERAGE) {
+        b.x[src ^ 1][j] = xv;
+        b.xsum[j] = aux + xv;
+    } else {
+        double w, w1;
+        halpern_weights(b, S, it, w, w1);
+        const double xb = fma(2.0, xv, -xin);
+        b.xsum[j] = xb;
+        b.x[src ^ 1][j] = fma(w, xb, w1 * aux);
+        if (keep) b.xret[j] = xv;
+    }
+}
+
 template <typename VT, int ALGO, int BS, bool SD>
 __global__ void __launch_bounds__(BS, 1536 / BS) k_primal(const Seg *__restrict__ segs, Bufs b, int it, int src,
                                                            Uniform u) {
     const Seg sg = row_slice<BS>(segs, u);
+    if (sg.rpt == 0) {   // a slice of long columns, one per warp
+        primal_long<VT, ALGO>(sg, b, it, src);
+        return;
+    }
     const Scalars *S = b.S + sg.inst;
     const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
     const SlotT<VT> *__restrict__ slots = static_cast<const SlotT<VT> *>(b.AT_sl);
@@ -1066,14 +1119,29 @@ __global__ void __launch_bounds__(kThreads) k_eval(const Seg *__restrict__ segs,
             }
         } else {
             const VT *__restrict__ v = static_cast<const VT *>(b.AT_v);
-            for (int j = sg.begin + threadIdx.x; j < sg.end; j += kThreads) {
+            // a slice of long columns (rpt = 0): a warp per column, lanes striding
+            // over its entries, lane 0 accumulating the column's terms
+            const bool lng = sg.rpt == 0;
+            const int wl = threadIdx.x & 31;
+            for (int j = lng ? sg.begin + (int)(threadIdx.x >> 5) : sg.begin + (int)threadIdx.x; j < sg.end;
+                 j += lng ? sg.end - j : kThreads) {
                 double t0 = 0.0, t1 = 0.0, tr = 0.0;
-                for (int k = b.AT_rp[j]; k < b.AT_rp[j + 1]; k++) {
+                const int e0 = b.AT_rp[j] + (lng ? wl : 0), e1 = b.AT_rp[j + 1], es = lng ? 32 : 1;
+                for (int k = e0; k < e1; k += es) {
                     const size_t i = at(b.AT_ci[k]);
                     const double a = widen(v[k]);
                     t0 += a * y[i];
                     if (avg) t1 += a * (yav[i] * inv_j);
                     if (ray) tr += a * (y[i] - b.y[1][i]);
+                }
+                if (lng) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                        if (avg) t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+                        if (ray) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+                    }
+                    if (wl != 0) break;
                 }
                 const size_t jj = at(j);
                 const double cj = b.c[jj], lj = b.l[jj], uj = b.u[jj], idc = b.inv_Dc[jj], xh = b.xa[jj];
@@ -1588,6 +1656,7 @@ struct uc_session {
     std::vector<int64_t> roff, coff, zoff;
     int64_t M = 0, N = 0, Z = 0;
     int n_sp = 0, n_sd = 0, n_se = 0, n_sa = 0;
+    int n_sac = 0;   // column blocks at the head of the apply table
     uc::dev::Layout L{};
     char *D = nullptr;
     size_t bytes = 0;
@@ -1666,7 +1735,9 @@ static void put(std::vector<char> &st, size_t off, const T *src, size_t count) {
 // windows of kOrderWindow rows of that order the rows are then sorted by
 // decreasing length (stable).  Columns get the same treatment with their A^T
 // row length.  Each row keeps its entries in their original order, so every
-// dot product sums in the same order as in the natural layout.
+// dot product sums in the same order as in the natural layout, except that the
+// columns with more than kLongRow entries go last and a warp sums each of them
+// (primal_long).
 constexpr int kOrderWindow = 1024;
 
 static void window_order(const std::vector<int32_t> &rp, const std::vector<int32_t> &base, std::vector<int32_t> &out) {
@@ -1756,6 +1827,18 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
               [&] { window_order(p.A.rowptr, entity_order(p.m_eq, m, p.row_map, R.row_kind, R.row_idx, R.row_t), prow_ge); },
               [&] { window_order(p.AT.rowptr, entity_order(0, n, p.col_map, R.col_kind, R.col_idx, R.col_t), pcol); });
     prow.insert(prow.end(), prow_ge.begin(), prow_ge.end());
+    // columns with more than kLongRow entries go last, in their order: the
+    // primal kernel gives each of them a warp
+    std::vector<int32_t> longc;
+    {
+        std::vector<int32_t> shortc;
+        shortc.reserve(n);
+        for (int32_t j : pcol) (p.AT.rowptr[j + 1] - p.AT.rowptr[j] > kLongRow ? longc : shortc).push_back(j);
+        if (!longc.empty()) {
+            pcol.swap(shortc);
+            pcol.insert(pcol.end(), longc.begin(), longc.end());
+        }
+    }
     std::vector<int32_t> irow(m), icol(n);
     for (int i = 0; i < m; i++) irow[prow[i]] = i;
     for (int j = 0; j < n; j++) icol[pcol[j]] = j;
@@ -1765,6 +1848,7 @@ static std::shared_ptr<const PsData> device_view(const std::shared_ptr<const PsD
     d->value_bits = p.value_bits;
     d->eta = p.eta; d->omega0 = p.omega0; d->norm_A = p.norm_A; d->norm_bound = p.norm_bound; d->obj_const = p.obj_const;
     d->q_inf = p.q_inf; d->c_inf = p.c_inf;
+    d->long_cols = (int)longc.size();
     auto permute_csr = [](const Csr &A, const std::vector<float> &v32, const std::vector<int32_t> &order,
                           const std::vector<int32_t> &inv_cols, Csr &out, std::vector<float> &o32) {
         out.rows = A.rows; out.cols = A.cols;
@@ -2049,10 +2133,12 @@ static cudaError_t launch_staged(const uc_session &X, cudaStream_t s, bool pdl, 
 template <typename VT, int ALGO, int BS, bool SD>
 static cudaError_t launch_rows(const uc_session &X, cudaStream_t s, bool pdl, int it, int src, bool primal) {
     if (primal) {
-        const Uniform u = X.k == 1 ? Uniform{(int)X.Nr, 0, X.rpt[0]} : Uniform{0, 0, 0};
+        const int ns = (int)X.Nr - (X.k == 1 ? X.Pd[0]->long_cols : 0);
+        const Uniform u = X.k == 1 ? Uniform{ns, 0, X.rpt[0], (ns + BS * X.rpt[0] - 1) / (BS * X.rpt[0]), (int)X.Nr}
+                                   : Uniform{0, 0, 0, 0, 0};
         return launch_k(k_primal<VT, ALGO, BS, SD>, X.n_sp, BS, s, pdl, X.dsp, X.b, it, src, u);
     }
-    const Uniform u = X.k == 1 ? Uniform{(int)X.Mr, X.m_eq[0], X.rpt[0]} : Uniform{0, 0, 0};
+    const Uniform u = X.k == 1 ? Uniform{(int)X.Mr, X.m_eq[0], X.rpt[0], INT_MAX, (int)X.Mr} : Uniform{0, 0, 0, 0, 0};
     return launch_k(k_dual<VT, ALGO, BS, SD>, X.n_sd, BS, s, pdl, X.dsd, X.b, it, src, u);
 }
 
@@ -2111,9 +2197,9 @@ static void launch_apply(uc_session &X, cudaStream_t s) {
         return;
     }
     switch (X.cta) {
-        case 128: k_apply<128, 1><<<X.n_sa, 128, 0, s>>>(X.dsa, X.n_sp, X.b); break;
-        case 512: k_apply<512, 1><<<X.n_sa, 512, 0, s>>>(X.dsa, X.n_sp, X.b); break;
-        default: k_apply<256, 1><<<X.n_sa, 256, 0, s>>>(X.dsa, X.n_sp, X.b); break;
+        case 128: k_apply<128, 1><<<X.n_sa, 128, 0, s>>>(X.dsa, X.n_sac, X.b); break;
+        case 512: k_apply<512, 1><<<X.n_sa, 512, 0, s>>>(X.dsa, X.n_sac, X.b); break;
+        default: k_apply<256, 1><<<X.n_sa, 256, 0, s>>>(X.dsa, X.n_sac, X.b); break;
     }
 }
 
@@ -2239,8 +2325,10 @@ static int staged_setup(uc_session &X) {
 // LPs outside the mask get no CTAs (and an empty evaluation range).
 static void build_tables(const uc_session &X, const std::vector<char> &mask, std::vector<Seg> &sp,
                          std::vector<Seg> &sd, std::vector<Seg> &se, std::vector<Seg> &sa,
-                         std::vector<InstRange> &ranges) {
+                         std::vector<InstRange> &ranges, int &n_sac) {
     sp.clear(); sd.clear(); se.clear(); sa.clear();
+    std::vector<Seg> sac;
+    n_sac = 0;
     ranges.assign(X.k, InstRange{0, 0});
     if (X.K > 1) {
         // lanes session: one structure; K/2 threads per row in the iteration
@@ -2254,6 +2342,7 @@ static void build_tables(const uc_session &X, const std::vector<char> &mask, std
         if (se.empty()) se.push_back({0, 0, 0, 0, 1});
         for (int i = 0; i < X.k; i++) ranges[i] = {i * (int)se.size(), (i + 1) * (int)se.size()};
         for (int64_t s = 0; s < X.Nr; s += X.cta) sa.push_back({0, (int)s, (int)std::min<int64_t>(s + X.cta, X.Nr), 0, 1});
+        n_sac = (int)sa.size();
         for (int64_t s = 0; s < X.Mr; s += X.cta) sa.push_back({0, (int)s, (int)std::min<int64_t>(s + X.cta, X.Mr), 0, 1});
         return;
     }
@@ -2262,16 +2351,23 @@ static void build_tables(const uc_session &X, const std::vector<char> &mask, std
         const int64_t c0 = X.coff[i], c1 = X.coff[i + 1], r0 = X.roff[i], r1 = X.roff[i + 1];
         const int rpt = X.rpt[i];
         const int cta = X.cta * rpt;
-        for (int64_t s = c0; s < c1; s += cta) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, c1), 0, rpt});
+        // the LP's long columns (last in its range) get one warp each (rpt = 0)
+        const int64_t cl = c1 - X.Pd[i]->long_cols;
+        for (int64_t s = c0; s < cl; s += cta) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, cl), 0, rpt});
+        for (int64_t s = cl; s < c1; s += X.cta / 32) sp.push_back({i, (int)s, (int)std::min<int64_t>(s + X.cta / 32, c1), 0, 0});
+        for (int64_t s = c0; s < c1; s += cta) sac.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, c1), 0, rpt});
         const int eq_end = (int)(r0 + X.m_eq[i]);
         for (int64_t s = r0; s < r1; s += cta) sd.push_back({i, (int)s, (int)std::min<int64_t>(s + cta, r1), eq_end, rpt});
         ranges[i].eval_begin = (int)se.size();
         for (int64_t s = r0; s < r1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, r1), eq_end << 1, 1});
-        for (int64_t s = c0; s < c1; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, c1), 1, 1});
+        for (int64_t s = c0; s < cl; s += kEvalRows) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kEvalRows, cl), 1, 1});
+        for (int64_t s = cl; s < c1; s += kThreads / 32) se.push_back({i, (int)s, (int)std::min<int64_t>(s + kThreads / 32, c1), 1, 0});
         if (se.size() == (size_t)ranges[i].eval_begin) se.push_back({i, 0, 0, 0, 1});
         ranges[i].eval_end = (int)se.size();
     }
-    sa = sp;
+    // the apply kernel covers columns and rows with one thread per element
+    n_sac = (int)sac.size();
+    sa = sac;
     sa.insert(sa.end(), sd.begin(), sd.end());
 }
 
@@ -2329,7 +2425,7 @@ static int capture(uc_session &X, int gi);
 static int retable(uc_session &X, const std::vector<char> &mask) {
     std::vector<Seg> sp, sd, se, sa;
     std::vector<InstRange> ranges;
-    build_tables(X, mask, sp, sd, se, sa, ranges);
+    build_tables(X, mask, sp, sd, se, sa, ranges, X.n_sac);
     const Layout &L = X.L;
     auto up = [&](size_t off, const void *src, size_t bytes) -> int {
         if (bytes) UC_CUDA(cudaMemcpyAsync(X.D + off, src, bytes, cudaMemcpyHostToDevice, X.s));
@@ -2497,7 +2593,7 @@ static int session_create(const PsData *const *Pp, const std::shared_ptr<const P
     std::vector<Seg> sp, sd, se, sa;
     std::vector<InstRange> ranges;
     std::vector<char> all(k, 1);
-    build_tables(*X, all, sp, sd, se, sa, ranges);
+    build_tables(*X, all, sp, sd, se, sa, ranges, X->n_sac);
     X->tabled = all;
     std::vector<Chunk> cp, cd;
     std::vector<int> gp, gd;

@@ -88,6 +88,7 @@ struct PsData {
     bool aggressive = false;               // presolve substituted doubleton equations
     double q_inf = 0.0, c_inf = 0.0;       // unscaled infinity norms (relative KKT)
     int value_bits = 64;
+    int long_cols = 0;   // device view: columns with more than kLongRow A^T entries, placed last
     int n() const { return A.cols; }
     int m() const { return A.rows; }
 };
