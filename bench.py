@@ -52,8 +52,8 @@ MAX_ITER = 100_000
 # strided-slot builder) and the launch shape (threads per CTA, rows per thread).
 NCU_TRAFFIC = {}
 NCU_TRAFFIC_RPT2 = {
-    ("paper", "halpern", "k_primal"): {"src": "e5a319d16b4d6fd1", "launch": (128, 2), "bytes": 36105216 + 4938496},
-    ("paper", "halpern", "k_dual"): {"src": "e5a319d16b4d6fd1", "launch": (128, 2), "bytes": 16612949 + 2451627},
+    ("paper", "halpern", "k_primal"): {"src": "2332a82d9f753da8", "launch": (128, 2), "bytes": 36162645 + 4488107},
+    ("paper", "halpern", "k_dual"): {"src": "2332a82d9f753da8", "launch": (128, 2), "bytes": 16699563 + 2484651},
 }
 
 
