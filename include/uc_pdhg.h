@@ -198,8 +198,11 @@ typedef struct {
                                     restart point: a decrease is dropped when rel_primal > kappa *
                                     rel_dual, an increase when rel_dual > kappa * rel_primal (a larger
                                     omega is a larger dual step, which works on primal
-                                    infeasibility).  Halpern variant.  UC_EINVAL for a negative,
-                                    non-finite or (0, 1) value */
+                                    infeasibility).  Halpern variant.  An LP without free columns
+                                    (e.g. presolved with eliminate_angles) keeps its dual residual
+                                    at rounding level, so the guard then blocks every decrease and
+                                    should stay off.  UC_EINVAL for a negative, non-finite or (0, 1)
+                                    value */
 } uc_solve_opts;
 
 typedef struct {
