@@ -295,3 +295,21 @@ def test_long_columns_parity_batch_and_kernels(B):
     np.testing.assert_array_equal(yb, ys)
     xr, yr = B.uc_get_raw_solution(single, raw.n, raw.m)
     assert max(kkt.relative_kkt(raw, xr, yr)) <= KKT_TOL * (1 + 1e-6)
+
+
+def test_long_columns_averaging_parity(B):
+    # the averaging variant through the warp-per-column paths (primal kernel
+    # and both candidates of the evaluation kernel) against the oracle
+    from oracle import presolve as ops
+    P = ucgen.batch_member(24)
+    ps_o = ops.presolve(olp.build_lp(P), angles=True)
+    S = ops.scale(ps_o.lp)
+    Ks = [1, 64, 65, 200]
+    ref = oracle_trace(S, Ks, variant="average")
+    ps = B.uc_presolve(B.uc_build_lp(P), eliminate_angles=1)
+    n, m, _, _ = B.uc_presolved_dims(ps)
+    for K in Ks:
+        x, y, st = _device_iterates(B, ps, n, m, K, algorithm="average")
+        xo, yo, restarts, omega, _, _ = ref[K]
+        assert st["restarts"] == restarts
+        assert rel_inf(x, xo) <= ITERATE_RTOL and rel_inf(y, yo) <= ITERATE_RTOL, K

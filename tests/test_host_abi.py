@@ -388,3 +388,20 @@ def test_angle_elimination_reuse_equals_a_full_presolve(B):
     re = B.uc_presolved_export(B.uc_presolve_reuse(ps0, B.uc_build_lp(Q)))
     for k in ("rowptr", "colidx", "val", "q", "c", "l", "u", "Dr", "Dc", "col_map", "row_map"):
         np.testing.assert_array_equal(re[k], full[k], err_msg=k)
+
+
+def test_device_order_puts_long_columns_last(B):
+    # on an angle-free LP the columns with more than 32 entries follow all
+    # others (a warp each in the primal kernel), keeping their relative order
+    P = ucgen.batch_member(24)
+    ps = B.uc_presolve(B.uc_build_lp(P), eliminate_angles=1)
+    d = B.uc_presolved_export(ps)
+    n = d["n"]
+    lc = np.bincount(d["colidx"].astype(np.int64), minlength=n)
+    prow, pcol = B.uc_presolved_device_order(ps)
+    np.testing.assert_array_equal(np.sort(pcol), np.arange(n))
+    longv = lc[pcol] > 32
+    k = int(longv.sum())
+    assert k > 0 and longv[n - k:].all() and not longv[:n - k].any()
+    # the default LP has no such column: its kernels keep the one-thread path
+    assert not (np.bincount(B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P)))["colidx"]) > 32).any()
