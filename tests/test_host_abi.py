@@ -405,3 +405,22 @@ def test_device_order_puts_long_columns_last(B):
     assert k > 0 and longv[n - k:].all() and not longv[:n - k].any()
     # the default LP has no such column: its kernels keep the one-thread path
     assert not (np.bincount(B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P)))["colidx"]) > 32).any()
+
+
+def test_angle_elimination_with_parallel_lines_matches_oracle(B):
+    # a grid with two lines between the same buses (a 2-entry cycle) and a
+    # 4-bus ring: the host's angle-free presolve equals the oracle's
+    P = ucgen.micro(1, B=4, L=5, G=2, T=3)
+    P.ref_bus = 0
+    P.line_from = np.array([0, 1, 2, 3, 0], np.int32)
+    P.line_to = np.array([1, 2, 3, 0, 1], np.int32)
+    P.x_pu = np.array([0.1, 0.2, 0.05, 0.15, 0.3])
+    P.fmax = np.full(5, 500.0)
+    ps_o = ops.presolve(olp.build_lp(P), angles=True)
+    S = ops.scale(ps_o.lp)
+    d = B.uc_presolved_export(B.uc_presolve(B.uc_build_lp(P), eliminate_angles=1))
+    np.testing.assert_array_equal(d["col_map"], ps_o.col_map)
+    np.testing.assert_array_equal(d["row_map"], ps_o.row_map)
+    np.testing.assert_array_equal(d["rowptr"], S.A.indptr)
+    np.testing.assert_array_equal(d["colidx"], S.A.indices)
+    np.testing.assert_allclose(d["val"], S.A.data, rtol=1e-13)

@@ -133,3 +133,41 @@ def test_each_planted_mistake_fails_a_pin(name):
         except (AssertionError, KeyError, ValueError):
             failed.append(pin.__name__)
     assert failed, f"no pin caught the planted mistake: {name}"
+
+
+def test_parallel_lines_form_a_two_entry_cycle():
+    # two lines between the same buses form a 2-entry cycle: the second line's
+    # row becomes f_1 - (x_0 / x_1) f_0 = 0; the host builds the same LP
+    P = _triangle()
+    P.line_from = np.array([0, 0, 1], np.int32)
+    P.line_to = np.array([1, 1, 2], np.int32)
+    P.x_pu = np.array([0.1, 0.4, 0.5])
+    raw = olp.build_lp(P)
+    E = ops.eliminate_angles(raw)
+    fcol = {int(raw.col_idx[j]): k for k, j in enumerate(E.col_keep) if raw.col_kind[j] == olp.COL_F}
+    kept = [i for i in np.flatnonzero(raw.row_kind == olp.ROW_FLOW) if i in set(E.row_keep.tolist())]
+    assert [int(raw.row_idx[i]) for i in kept] == [1]
+    r = int(np.flatnonzero(E.row_keep == kept[0])[0])
+    A = E.lp.A.tocsr()
+    row = {int(A.indices[k]): float(A.data[k]) for k in range(A.indptr[r], A.indptr[r + 1])}
+    # theta_0 - theta_1 = x0 f0 (tree line 0 from the reference bus), so
+    # f1 - (theta_0 - theta_1) / x1 = f1 - (x0 / x1) f0 = f1 - 0.25 f0
+    assert row == pytest.approx({fcol[1]: 1.0, fcol[0]: -0.25}, rel=1e-15)
+    _check_kvl_on(raw, E)
+
+
+def _check_kvl_on(raw, E):
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1.0, 1.0, raw.n)
+    th = raw.col_kind == olp.COL_TH
+    x[th & (raw.l == 0.0) & (raw.u == 0.0)] = 0.0
+    A = raw.A.tocsr()
+    for i in np.flatnonzero(raw.row_kind == olp.ROW_FLOW):
+        ents = range(A.indptr[i], A.indptr[i + 1])
+        fc = [A.indices[k] for k in ents if raw.col_kind[A.indices[k]] == olp.COL_F][0]
+        x[fc] = -sum(A.data[k] * x[A.indices[k]] for k in ents if A.indices[k] != fc)
+    xk = x[E.col_keep]
+    res = E.lp.A @ xk
+    assert np.max(np.abs(res[E.lp.row_kind == olp.ROW_FLOW])) <= 1e-12 * np.max(np.abs(xk))
+    xr, _ = ops.restore_angles(E, raw, xk)
+    np.testing.assert_allclose(xr, x, rtol=0, atol=1e-12)
