@@ -137,7 +137,7 @@ def test_each_planted_mistake_fails_a_pin(name):
 
 def test_parallel_lines_form_a_two_entry_cycle():
     # two lines between the same buses form a 2-entry cycle: the second line's
-    # row becomes f_1 - (x_0 / x_1) f_0 = 0; the host builds the same LP
+    # row becomes f_1 - (x_0 / x_1) f_0 = 0
     P = _triangle()
     P.line_from = np.array([0, 0, 1], np.int32)
     P.line_to = np.array([1, 1, 2], np.int32)
