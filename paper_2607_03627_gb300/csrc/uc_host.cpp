@@ -637,13 +637,20 @@ static int presolve_reduce(const RawLp &raw, PsData &ps, Csr &Ared, std::vector<
         }
     }
     std::vector<int32_t> newcol(n, -1);
+    ps.col_map.reserve(n);
+    ps.row_map.reserve(m);
     for (int j = 0; j < n; j++)
         if (col_on[j]) { newcol[j] = (int32_t)ps.col_map.size(); ps.col_map.push_back(j); }
     for (int i = 0; i < m; i++)
         if (row_on[i]) ps.row_map.push_back(i);
     Ared.rows = (int)ps.row_map.size();
     Ared.cols = (int)ps.col_map.size();
+    Ared.rowptr.reserve(ps.row_map.size() + 1);
     Ared.rowptr.assign(1, 0);
+    Ared.colidx.reserve(A.colidx.size());
+    Ared.val.reserve(A.val.size());
+    qr.reserve(ps.row_map.size());
+    cr.reserve(ps.col_map.size()); lr.reserve(ps.col_map.size()); ur.reserve(ps.col_map.size());
     for (int32_t i : ps.row_map) {
         for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; k++)
             if (col_on[A.colidx[k]]) { Ared.colidx.push_back(newcol[A.colidx[k]]); Ared.val.push_back(A.val[k]); }
