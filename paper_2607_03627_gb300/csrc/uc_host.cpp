@@ -372,6 +372,9 @@ int eliminate_angles(const RawLp &raw, RawLp &out, AngleElim &E) {
     std::vector<char> has_new(m, 0);
     E.roots.clear();
     E.tree.clear();
+    size_t n_angles = 0;
+    for (const auto &nodes : th_of) n_angles += nodes.size();
+    E.tree.reserve(n_angles);
     E.tree_row.assign(n, -1);
     std::vector<int> local(n, -1);
     for (size_t p = 0; p < periods.size(); p++) {
@@ -431,6 +434,7 @@ int eliminate_angles(const RawLp &raw, RawLp &out, AngleElim &E) {
             up(local[L.b], pb);
             while (!pa.empty() && !pb.empty() && pa.back() == pb.back()) { pa.pop_back(); pb.pop_back(); }
             auto &row = new_row[L.row];
+            row.reserve(1 + pa.size() + pb.size());
             row.push_back({L.fc, 1.0});
             for (auto &gs : pa) row.push_back({edges[gs.first].fc, -gs.second * L.inv / edges[gs.first].inv});
             for (auto &gs : pb) row.push_back({edges[gs.first].fc, gs.second * L.inv / edges[gs.first].inv});
@@ -456,7 +460,16 @@ int eliminate_angles(const RawLp &raw, RawLp &out, AngleElim &E) {
     const int nk = (int)E.col_keep.size(), mk = (int)E.row_keep.size();
     out.A.rows = mk;
     out.A.cols = nk;
+    int64_t nnz_new = 0;
+    for (int i = 0; i < m; i++) nnz_new += has_new[i] ? (int64_t)new_row[i].size() : 0;
+    out.A.rowptr.reserve((size_t)mk + 1);
     out.A.rowptr.assign(1, 0);
+    out.A.colidx.reserve((size_t)(A.nnz() + nnz_new));
+    out.A.val.reserve((size_t)(A.nnz() + nnz_new));
+    for (auto *v : {&out.q}) v->reserve(mk);
+    out.row_kind.reserve(mk); out.row_t.reserve(mk); out.row_idx.reserve(mk);
+    out.c.reserve(nk); out.l.reserve(nk); out.u.reserve(nk);
+    out.col_kind.reserve(nk); out.col_t.reserve(nk); out.col_idx.reserve(nk);
     std::vector<std::pair<int, double>> ents;
     for (int r = 0; r < mk; r++) {
         const int i = E.row_keep[r];
